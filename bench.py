@@ -1,0 +1,378 @@
+"""Benchmark of the Monte-Carlo line-by-line hot path on GB300.
+
+One step = one pass of the whole path over the 32^3-box workload (20k Voigt
+lines, 64 temperature nodes x 100k wavenumbers, 1e7 rays): rt_build_kappa
+(line geometry, Eq. S prefactors, Eq. tau table) -> rt_tally_zero -> rt_trace
+(cell prep, walk) -> rt_tally (binary64 reduction, energy balance).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded ray/column sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+FP32_LANES_PER_SM = 128
+# algorithmic binary32 flops of one profile evaluation (FMA = 2): far-wing
+# Voigt (five-term asymptotic series) and Lorentz, each with the Kahan update
+FLOPS_PER_EVAL = {"voigt": 46, "lorentz": 11}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def ray_range(rank: int, world: int, rays_per_rank: int):
+    """Weak scaling: rank r traces rays [r * R, (r + 1) * R) of an N*R-ray estimate."""
+    return rank * rays_per_rank, rays_per_rank, world * rays_per_rank
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=open(path, "w"), stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def _clock_summary(path, dev_index):
+    rows = []
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(dev_index):
+                continue
+            rows.append(f)
+    except OSError:
+        return None
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    reasons = set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        for n, v in zip(names, r[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import paper_cs_0703028_gb300 as rt
+
+    world, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    case = synth.config(1)
+    spec, lines, grid = case.spec, case.lines, case.grid
+    ray_begin, n_rays, n_total = ray_range(rank, world, case.n_rays)
+
+    stream = torch.cuda.current_stream()
+    # inputs resident in HBM
+    lines_dev, keep_lines = rt.make_lines(lines, memory="device")
+    gs, keep_grid = rt.make_grid(grid)
+    S = rt.make_spectral(spec)
+    kappa = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    evals = torch.zeros(1, dtype=torch.int64, device="cuda")
+    bstatus = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tally = rt.Tally(grid.ncells)
+    L = rt.lib()
+    import ctypes as ct
+    sp = ct.c_void_p(stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2
+    host_sc = np.zeros(4, dtype=np.float64)
+
+    kb0 = torch.cuda.Event(enable_timing=True)
+    kb1 = torch.cuda.Event(enable_timing=True)
+    kt0 = torch.cuda.Event(enable_timing=True)
+    kt1 = torch.cuda.Event(enable_timing=True)
+
+    def step(timers=None):
+        if timers:
+            timers[0].record(stream)
+        st = L.rt_build_kappa(ct.byref(lines_dev), ct.byref(S), ct.c_void_p(kappa.data_ptr()),
+                              ct.c_void_p(evals.data_ptr()), ct.c_void_p(bstatus.data_ptr()), sp)
+        if st:
+            raise rt.RtError(st, "rt_build_kappa", L.rt_last_error().decode())
+        if timers:
+            timers[1].record(stream)
+        st = L.rt_tally_zero(ct.byref(tally.buf), grid.ncells, sp)
+        if timers:
+            timers[2].record(stream)
+        st |= L.rt_trace(ct.byref(gs), ct.c_void_p(kappa.data_ptr()), ct.byref(S), ray_begin, n_rays,
+                         n_total, case.seed, 0, 0, ct.byref(tally.buf), None, sp)
+        if timers:
+            timers[3].record(stream)
+        if st:
+            raise rt.RtError(st, "rt_trace", L.rt_last_error().decode())
+        st = L.rt_tally(ct.byref(tally.buf), grid.ncells, None, host_sc.ctypes.data, sp)
+        if st:
+            raise rt.RtError(st, "rt_tally", L.rt_last_error().decode())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evals.zero_()
+    evals_per_step = None
+    steps_per_step = int(tally.steps.item())
+
+    clk_path = os.path.join(tempfile.gettempdir(), f"rt_clocks_{os.getpid()}.csv")
+    sampler = _clock_sampler(clk_path) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    s0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    s1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))          # evict the previous step's data from L2 (untimed)
+        s0[i].record(stream)
+        step(ev[i])
+        s1[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    ms_total = sum(a.elapsed_time(b) for a, b in zip(s0, s1))
+    ms_build = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    ms_trace = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
+    evals_per_step = int(evals.item()) // args.steps
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = steps_per_step * world / (ms_step * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned)
+    lines_host = [torch.from_numpy(np.ascontiguousarray(getattr(lines, k))).pin_memory()
+                  for k in ("nu0", "S_ref", "gamma_ref", "E_lower")]
+    Lh = rt.rt_lines(lines.n, *[t.data_ptr() for t in lines_host], lines.T_ref, lines.n_T,
+                     lines.q_exp, lines.mass_amu, rt.RT_MEM_HOST, 0)
+    T_host = torch.from_numpy(grid.T).pin_memory()
+    p_host = torch.from_numpy(grid.p_atm).pin_memory()
+    x_host = torch.from_numpy(grid.x).pin_memory()
+    T_dev, p_dev, x_dev = keep_grid
+    ab_host = torch.zeros(grid.ncells, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in lines_host + [T_host, p_host, x_host])
+    d2h = ab_host.numel() * 8 + 4 * 8
+
+    def e2e_step():
+        T_dev.copy_(T_host, non_blocking=True)
+        p_dev.copy_(p_host, non_blocking=True)
+        x_dev.copy_(x_host, non_blocking=True)
+        st = L.rt_build_kappa(ct.byref(Lh), ct.byref(S), ct.c_void_p(kappa.data_ptr()), None, None, sp)
+        st |= L.rt_tally_zero(ct.byref(tally.buf), grid.ncells, sp)
+        st |= L.rt_trace(ct.byref(gs), ct.c_void_p(kappa.data_ptr()), ct.byref(S), ray_begin, n_rays,
+                         n_total, case.seed, 0, 0, ct.byref(tally.buf), None, sp)
+        st |= L.rt_tally(ct.byref(tally.buf), grid.ncells, ab_host.data_ptr(), host_sc.ctypes.data, sp)
+        if st:
+            raise RuntimeError("e2e step failed: " + L.rt_last_error().decode())
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms += e0.elapsed_time(e1)
+    e2e_value = steps_per_step * world / (e_ms / args.steps * 1e-3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    clocks = _clock_summary(clk_path, local) if sampler else None
+    sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    props = torch.cuda.get_device_properties(local)
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_clock_mhz * 1e6 / 1e12
+    flops = evals_per_step * FLOPS_PER_EVAL[spec.profile]
+    achieved = flops / (ms_build * 1e-3) / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "k_kappa_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get("bytes_per_launch")
+        except ValueError:
+            traffic = None
+    out = {
+        "metric": "ray-cell steps/s + line-profile evals/s; surrogate vs plain at <=1% tally err",
+        "value": value,
+        "unit": "ray-cell steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded line list, Gaussian hot-spot field; no HITRAN data)",
+        "config": {"workload": "box32_voigt20k: 32^3 cells 1 m^3, 20k Voigt lines 2000-3000 cm^-1, "
+                               "64 T x 100k nu table, 1e7 rays per GPU",
+                   "ncells": grid.ncells, "n_lines": lines.n, "n_nu": spec.n_nu, "nT": spec.nT,
+                   "rays_per_gpu": n_rays, "l2": "flushed between steps (256 MB write, untimed)"},
+        "line_profile_evals_per_s": evals_per_step * world / (ms_step * 1e-3),
+        "ray_cell_steps_per_step": steps_per_step,
+        "profile_evals_per_step": evals_per_step,
+        "kernels_ms": {"rt_build_kappa": ms_build, "rt_trace": ms_trace},
+        "energy_residual": float(host_sc[3]),
+        "gpu_launches": 7 * args.steps,
+        "roofline": {"kernel": "k_kappa (rt_build_kappa)", "bound": "alu", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic,
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                    f"{sm_clock_mhz:.0f} MHz",
+                     "flops_per_eval": FLOPS_PER_EVAL[spec.profile]},
+        "e2e": {"value": e2e_value, "unit": "ray-cell steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(case, evals_per_step, steps_per_step, budget_s=args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(case, evals_full, steps_full, budget_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded ray sample of the same step:
+    the kappa columns those rays use (all 64 T) and the walk of those rays;
+    throughput extrapolated to the full step."""
+    from oracle import kappa as okappa
+    from oracle import trace as otrace
+    threads = otrace.default_threads()
+    n = 64
+    t_k = t_w = 0.0
+    ev = st = rays = 0
+    rb = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        _, j = otrace.emission_indices(case.grid.ncells, case.spec.n_nu, case.seed, rb, n)
+        cols = np.unique(j)
+        a = time.perf_counter()
+        K = okappa.kappa_columns(case.lines, case.spec, cols)
+        b = time.perf_counter()
+        lo, hi = okappa.line_ranges(case.lines, case.spec)
+        nu = okappa.grid_nu(case.spec, cols)
+        col_evals = np.searchsorted(case.lines.nu0, nu + case.spec.cutoff, "right") - \
+            np.searchsorted(case.lines.nu0, nu - case.spec.cutoff, "left")
+        r = otrace.trace(case.grid, case.spec, K, seed=case.seed, ray_begin=rb, n_rays=n,
+                         n_total=case.n_rays, columns=cols, threads=threads)
+        c = time.perf_counter()
+        t_k += b - a
+        t_w += c - b
+        ev += int(col_evals.sum()) * case.spec.nT
+        st += r.steps
+        rays += n
+        rb += n
+    evals_per_s = ev / t_k
+    steps_per_s = st / t_w
+    t_full = evals_full / evals_per_s + steps_full / steps_per_s
+    return {"value": steps_full / t_full, "unit": "ray-cell steps/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"rays [0, {rays}) of the 1e7-ray step and the {ev // case.spec.nT} (line, nu) "
+                      f"pairs of their columns at all 64 T; kappa oracle numpy/scipy on 1 core, walk "
+                      f"oracle C on {threads} threads; full-step time extrapolated from "
+                      f"{evals_per_s:.3g} evals/s and {steps_per_s:.3g} steps/s",
+            "line_profile_evals_per_s": evals_per_s, "ray_cell_steps_per_s": steps_per_s}
+
+
+def run_reference(args):
+    world, rank = _dist()
+    if rank != 0:
+        return
+    case = synth.config(1)
+    from oracle import kappa as okappa
+    # full-step work (exact profile-evaluation count, ray-cell steps from a ray sample)
+    evals_full = okappa.profile_evals(case.lines, case.spec)
+    from oracle import trace as otrace
+    K1 = np.full((case.spec.nT, case.spec.n_nu), 1e-3)
+    probe = otrace.trace(case.grid, case.spec, K1, seed=case.seed, n_rays=20000, n_total=case.n_rays)
+    steps_full = int(probe.steps * (case.n_rays / 20000))
+    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(case, evals_full, steps_full, budget_s=per)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(case, evals_full, steps_full, budget_s=per))
+    el = time.perf_counter() - t0
+    v = statistics.median([x["value"] for x in vals])
+    ms_step = steps_full / v * 1e3
+    cb = dict(vals[-1])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": "ray-cell steps/s + line-profile evals/s; surrogate vs plain at "
+                                          "<=1% tally err",
+           "value": v, "unit": "ray-cell steps/s", "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "box32_voigt20k: 32^3 cells 1 m^3, 20k Voigt lines 2000-3000 cm^-1, "
+                                  "64 T x 100k nu table, 1e7 rays per GPU"},
+           "cpu_baseline": cb, "wall_s": el,
+           "e2e": {"value": v, "unit": "ray-cell steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * rt.h -- C ABI of the GB300 Monte-Carlo line-by-line radiative-transfer library.
+ *
+ * The library computes the hot path of the method of Collange, Daumas and Defour,
+ * "Graphic processors to speed-up simulations for the design of high performance
+ * solar receptors" (Section 3): the absorption coefficient kappa(nu, T) of a gas
+ * from a spectral line list (Eqs. S and tau), and Monte-Carlo rays traced cell by
+ * cell through a grid of isothermal homogeneous finite volumes with Beer-Lambert
+ * attenuation (Eq. I, first term), emitted according to the Planck function
+ * (Eq. planck), with the absorbed power tallied per cell (the parallel reduction
+ * of Section 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Memory: the caller owns every buffer.  "host" pointers are ordinary CPU
+ *    memory, "device" pointers are CUDA device memory of the current device.
+ *    The library allocates only temporary scratch, stream-ordered on the given
+ *    stream (cudaMallocAsync / cudaFreeAsync), and releases it before the
+ *    call's work completes.
+ *  - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *    Calls are asynchronous on that stream unless stated otherwise.
+ *  - Errors: every call returns an rt_status and never aborts the process.
+ *    Arguments are validated on the host before any launch.  Conditions only the
+ *    device can see (a non-finite temperature in a device field, a ray over its
+ *    step cap, a bounded wait that ran out) are OR-ed into a caller-provided
+ *    device status word; rt_tally() and rt_status_read() report them.
+ *    rt_last_error() returns a thread-local message for the last failure.
+ *  - Units: wavenumbers in cm^-1, lengths in m, temperatures in K, pressures in
+ *    atm, absorption coefficients in cm^-1, powers in W.
+ *  - Arithmetic: the line sum and the ray walk run in binary32 with compensated
+ *    (Kahan) sums; binary64 is used on the device for the per-cell tally, the
+ *    energy balance, and the exact conversion of the caller's binary64 line
+ *    positions into grid coordinates.
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_E_INVAL = 1,      /* bad argument: NULL pointer, size or range */
+  RT_E_NOMEM = 2,      /* scratch allocation failed */
+  RT_E_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  RT_E_STEPCAP = 4,    /* a ray exceeded nx+ny+nz+4 cell visits (device-reported) */
+  RT_E_TIMEOUT = 5,    /* a bounded device wait ran out (device-reported) */
+  RT_E_UNSORTED = 6,   /* line list not sorted by ascending centre */
+  RT_E_NONFINITE = 7   /* NaN / Inf / non-positive value where a positive finite one is needed */
+} rt_status;
+
+/* Device status word bits (OR-ed by kernels into rt_tally_buf.status etc.). */
+#define RT_DEV_STEPCAP   (1u << 0)
+#define RT_DEV_TIMEOUT   (1u << 1)
+#define RT_DEV_NONFINITE (1u << 2)
+#define RT_DEV_UNSORTED  (1u << 3)
+#define RT_DEV_COLUMN    (1u << 4)
+
+enum { RT_PROFILE_LORENTZ = 0, RT_PROFILE_VOIGT = 1 };
+enum { RT_MEM_HOST = 0, RT_MEM_DEVICE = 1 };
+
+/* rt_trace flags */
+#define RT_SRC_EMIT   0        /* thermal emission sampled over cells and wavenumbers */
+#define RT_SRC_BEAM   1        /* collimated unit beams: ray r enters face x=0 at nu_(r mod n_nu) */
+#define RT_TAU_CUT    (1 << 4) /* stop a ray once its optical depth exceeds 100 (lost < 4e-44) */
+
+/*
+ * Spectral line list (Section 3, Eq. S: S(T_ref), nu, E_eta; Eq. tau: lines of one
+ * absorbing gas).  Arrays hold n binary64 values, sorted by ascending nu0, in host
+ * memory (memory = RT_MEM_HOST; validated on the host: RT_E_UNSORTED,
+ * RT_E_NONFINITE) or device memory (memory = RT_MEM_DEVICE; validated on the
+ * device into the status word given to rt_build_kappa).
+ */
+typedef struct {
+  int64_t n;               /* number of lines, >= 0 */
+  const double *nu0;       /* line centre, cm^-1, ascending */
+  const double *S_ref;     /* intensity at T_ref, cm/molecule, > 0 */
+  const double *gamma_ref; /* Lorentz half-width at T_ref and 1 atm, cm^-1, > 0 */
+  const double *E_lower;   /* lower-state energy, cm^-1, >= 0 */
+  double T_ref;            /* reference temperature, K (296 for HITRAN-style lists) */
+  double n_T;              /* gamma(T) = gamma_ref (p / 1 atm) (T_ref / T)^n_T */
+  double q_exp;            /* partition function Q(T) ~ T^q_exp */
+  double mass_amu;         /* molecular mass, u (Doppler width) */
+  int32_t memory;          /* RT_MEM_HOST or RT_MEM_DEVICE */
+  int32_t pad;
+} rt_lines;
+
+/*
+ * Spectral window and temperature grid of the kappa table (Section 3, Eq. tau).
+ * Spectral samples nu_j = nu_min + j * dnu, j = 0 .. n_nu-1 (binary64).
+ * Temperature nodes T_k = T_min + k (T_max - T_min) / (nT - 1), k = 0 .. nT-1;
+ * nT = 1 is a single isothermal row at T_min.  Lines contribute at nu_j when
+ * |nu_j - nu0| <= cutoff (binary64, inclusive), with no renormalisation.
+ */
+typedef struct {
+  double nu_min;           /* cm^-1 */
+  double dnu;              /* cm^-1, > 0 */
+  int64_t n_nu;            /* number of spectral samples, >= 1 */
+  double cutoff;           /* line-wing cutoff, cm^-1, >= 0 */
+  int32_t profile;         /* RT_PROFILE_LORENTZ or RT_PROFILE_VOIGT */
+  int32_t nT;              /* number of temperature nodes, >= 1 */
+  double T_min, T_max;     /* K, 0 < T_min <= T_max (T_min < T_max when nT > 1) */
+  double p_ref_atm;        /* pressure of the table, atm, > 0 */
+  double x_ref;            /* absorber mole fraction of the table, > 0 */
+} rt_spectral;
+
+/*
+ * Finite-volume grid (Section 3, Fig. ray: isothermal homogeneous finite volumes
+ * with temperature, pressure and absorber density).  Cell (ix, iy, iz) has flat
+ * index ix + nx (iy + ny iz) and spans [ix hx, (ix+1) hx) etc.  An infinite cell
+ * size makes that axis unbounded (hy = hz = INFINITY gives a plane-parallel slab;
+ * the cell volume then counts 1 m per unbounded axis).  Fields are binary32
+ * device arrays of nx*ny*nz values.  p_atm and x may be NULL (the table's
+ * p_ref and x_ref); otherwise kappa of a cell is scaled by (p x)/(p_ref x_ref).
+ */
+typedef struct {
+  int32_t nx, ny, nz, pad;
+  double hx, hy, hz;       /* m, > 0 (or +INFINITY) */
+  const float *T;          /* device [ncells], K, finite > 0 */
+  const float *p_atm;      /* device [ncells] or NULL */
+  const float *x;          /* device [ncells] or NULL */
+} rt_grid;
+
+/*
+ * Tally buffers (device, caller-owned).  rt_trace ADDS into them, so several
+ * calls (ray ranges, enclosures) can accumulate; zero them with rt_tally_zero().
+ *   absorbed[ncells]  absorbed power per cell, W (binary64)
+ *   scalars[4]        [0] emitted power, [1] total absorbed (set by rt_tally),
+ *                     [2] power absorbed by the cold black walls, [3] relative
+ *                     energy residual |emitted - absorbed - walls| / emitted
+ *                     (set by rt_tally)
+ *   steps[1]          number of ray-cell steps processed
+ *   status[1]         sticky RT_DEV_* bits
+ */
+typedef struct {
+  double *absorbed;
+  double *scalars;
+  unsigned long long *steps;
+  uint32_t *status;
+} rt_tally_buf;
+
+/*
+ * Optional per-ray record (device buffers) of rays [ray_begin, ray_begin + n_rays)
+ * of a trace call: the visited cells and segment lengths (m) in walk order, the
+ * number of visits, the emitted power and the power that reached a wall.
+ */
+typedef struct {
+  int64_t n_rays;
+  int32_t max_visits;      /* row length of cells/ds, >= nx+ny+nz+4 for complete rows */
+  int32_t pad;
+  int32_t *cells;          /* [n_rays * max_visits] */
+  float *ds;               /* [n_rays * max_visits] */
+  int32_t *n_visits;       /* [n_rays] */
+  float *weight;           /* [n_rays] */
+  float *escaped;          /* [n_rays] */
+} rt_record;
+
+/* Library version string. */
+const char *rt_version(void);
+
+/* Thread-local message describing the last non-RT_OK status of this thread. */
+const char *rt_last_error(void);
+
+/* Number of binary32 elements of the kappa table: nT * n_nu (0 on bad input). */
+size_t rt_kappa_table_elems(const rt_spectral *spec);
+
+/*
+ * rt_build_kappa -- Eqs. (S) and (tau) of Section 3 on a temperature grid:
+ *   kappa[k * n_nu + j] = u(T_k) * sum_{l : |nu_j - nu0_l| <= cutoff} S_l(T_k) f_l(nu_j - nu0_l; T_k)
+ * with u = x_ref p_ref / (k_B T) the absorber number density [cm^-3], S_l(T) by
+ * Eq. (S) with Q(T_ref)/Q(T) = (T_ref/T)^q_exp, and f the Lorentz profile (half-width
+ * gamma = gamma_ref p_ref (T_ref/T)^n_T) or the Voigt profile (that Lorentz width and
+ * the Doppler half-width nu0/c sqrt(2 ln2 k_B T / m)).  Binary32 with a Kahan sum
+ * over lines in ascending nu0.
+ *   kappa      device [nT * n_nu] binary32, cm^-1, written (T-major: row k is the
+ *              spectrum at T_k).
+ *   evals_out  optional device counter: adds the number of (T_k, line, nu_j)
+ *              profile evaluations.
+ *   status     device status word; required when lines->memory == RT_MEM_DEVICE
+ *              (receives RT_DEV_UNSORTED / RT_DEV_NONFINITE), may be NULL otherwise.
+ * Returns RT_E_INVAL / RT_E_UNSORTED / RT_E_NONFINITE before any launch on bad
+ * host-visible input, RT_E_NOMEM / RT_E_CUDA on runtime failures.
+ */
+rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                         unsigned long long *evals_out, uint32_t *status, void *stream);
+
+/*
+ * rt_trace -- the Monte-Carlo ray-tracing estimator of Section 3 (Fig. ray).
+ * Rays r in [ray_begin, ray_begin + n_rays) of an estimate over n_rays_total rays:
+ *   RT_SRC_EMIT: Philox4x32-10 (key = seed, counter = (r_lo, r_hi, call, enclosure))
+ *     draws the emission cell c and wavenumber index j uniformly, a uniform point in
+ *     the cell and an isotropic direction (Marsaglia 1972).  The ray carries
+ *       w = 4 pi V kappa_c(nu_j) I_b(nu_j, T_c) dnu * ncells n_nu / n_rays_total
+ *     with I_b the Planck function of Eq. (planck) in wavenumber form.
+ *   RT_SRC_BEAM: ray r enters the x = 0 face at the centre of cell (0, ny/2, nz/2)
+ *     along +x with w = 1 at nu_(r mod n_nu).
+ * The ray is walked cell by cell (Amanatides-Woo traversal, specified in binary32
+ * round-to-nearest without contraction); in a cell crossed over length ds it leaves
+ *   w exp(-tau) (1 - exp(-kappa_cell 100 ds))     (Eq. I, first term)
+ * where tau is its (Kahan-summed) optical depth so far and kappa_cell is the table
+ * interpolated linearly in T between the cell's bracketing nodes (clamped to the
+ * table range) times the density scale.  What reaches a wall is absorbed there.
+ *   kappa      device [nT * n_nu] table from rt_build_kappa for the same spec.
+ *   tally      accumulated (see rt_tally_buf).
+ *   record     optional (NULL = none).
+ *   flags      RT_SRC_EMIT or RT_SRC_BEAM, optionally | RT_TAU_CUT.
+ */
+rt_status rt_trace(const rt_grid *grid, const float *kappa, const rt_spectral *spec,
+                   uint64_t ray_begin, uint64_t n_rays, uint64_t n_rays_total,
+                   uint64_t seed, uint32_t enclosure, int32_t flags,
+                   const rt_tally_buf *tally, const rt_record *record, void *stream);
+
+/* Zero a tally buffer of ncells cells (asynchronous). */
+rt_status rt_tally_zero(const rt_tally_buf *tally, int64_t ncells, void *stream);
+
+/*
+ * rt_tally -- final reduction of Section 3 (sum of the absorbed power over all
+ * cells, binary64) and the energy balance.  Sets tally->scalars[1] and [3] on the
+ * device, then copies scalars[0..3] into host_scalars (required) and, if
+ * host_absorbed is not NULL, absorbed[0..ncells) into it.  SYNCHRONISES the stream.
+ * Returns the device status bits as a status: RT_E_NONFINITE, RT_E_STEPCAP,
+ * RT_E_TIMEOUT, RT_E_UNSORTED, RT_E_INVAL (missing table column), else RT_OK.
+ */
+rt_status rt_tally(const rt_tally_buf *tally, int64_t ncells, double *host_absorbed,
+                   double host_scalars[4], void *stream);
+
+/* Synchronise the stream and translate a device status word into an rt_status. */
+rt_status rt_status_read(const uint32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RT_H */

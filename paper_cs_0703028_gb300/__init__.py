@@ -1,0 +1,245 @@
+"""GB300 (sm_103a) Monte-Carlo line-by-line radiative transfer.
+
+Thin Python binding of the C ABI declared in ``include/rt.h``: the functions
+``rt_build_kappa``, ``rt_trace``, ``rt_tally``, ``rt_tally_zero``,
+``rt_status_read``, ``rt_last_error``, ``rt_version`` and
+``rt_kappa_table_elems`` are the library's own entry points (ctypes), and the
+helpers below only marshal arguments: every step of the computation runs in
+the library's CUDA kernels.  PyTorch supplies device memory and streams.
+
+The method follows Section 3 of Collange, Daumas and Defour, "Graphic
+processors to speed-up simulations for the design of high performance solar
+receptors": the absorption coefficient of a gas from its line list (Eqs. S,
+tau) and Monte-Carlo rays traced through finite volumes with Beer-Lambert
+attenuation (Eq. I) and Planck emission (Eq. planck).
+
+There is no CPU fallback: if the CUDA library cannot be loaded, importing
+this package raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+import os
+
+from . import _build
+
+__all__ = ["RtError", "lib", "rt_lines", "rt_spectral", "rt_grid", "rt_tally_buf", "rt_record",
+           "make_lines", "make_spectral", "make_grid", "Tally", "Record", "build_kappa", "trace",
+           "PROFILE", "RT_SRC_EMIT", "RT_SRC_BEAM", "RT_TAU_CUT", "RT_MEM_HOST", "RT_MEM_DEVICE"]
+
+RT_OK, RT_E_INVAL, RT_E_NOMEM, RT_E_CUDA, RT_E_STEPCAP, RT_E_TIMEOUT, RT_E_UNSORTED, RT_E_NONFINITE = range(8)
+STATUS_NAMES = {0: "RT_OK", 1: "RT_E_INVAL", 2: "RT_E_NOMEM", 3: "RT_E_CUDA", 4: "RT_E_STEPCAP",
+                5: "RT_E_TIMEOUT", 6: "RT_E_UNSORTED", 7: "RT_E_NONFINITE"}
+PROFILE = {"lorentz": 0, "voigt": 1}
+RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
+RT_SRC_EMIT, RT_SRC_BEAM, RT_TAU_CUT = 0, 1, 1 << 4
+
+
+class RtError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class rt_lines(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("nu0", ct.c_void_p), ("S_ref", ct.c_void_p),
+                ("gamma_ref", ct.c_void_p), ("E_lower", ct.c_void_p), ("T_ref", ct.c_double),
+                ("n_T", ct.c_double), ("q_exp", ct.c_double), ("mass_amu", ct.c_double),
+                ("memory", ct.c_int32), ("pad", ct.c_int32)]
+
+
+class rt_spectral(ct.Structure):
+    _fields_ = [("nu_min", ct.c_double), ("dnu", ct.c_double), ("n_nu", ct.c_int64),
+                ("cutoff", ct.c_double), ("profile", ct.c_int32), ("nT", ct.c_int32),
+                ("T_min", ct.c_double), ("T_max", ct.c_double), ("p_ref_atm", ct.c_double),
+                ("x_ref", ct.c_double)]
+
+
+class rt_grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("nz", ct.c_int32), ("pad", ct.c_int32),
+                ("hx", ct.c_double), ("hy", ct.c_double), ("hz", ct.c_double),
+                ("T", ct.c_void_p), ("p_atm", ct.c_void_p), ("x", ct.c_void_p)]
+
+
+class rt_tally_buf(ct.Structure):
+    _fields_ = [("absorbed", ct.c_void_p), ("scalars", ct.c_void_p), ("steps", ct.c_void_p),
+                ("status", ct.c_void_p)]
+
+
+class rt_record(ct.Structure):
+    _fields_ = [("n_rays", ct.c_int64), ("max_visits", ct.c_int32), ("pad", ct.c_int32),
+                ("cells", ct.c_void_p), ("ds", ct.c_void_p), ("n_visits", ct.c_void_p),
+                ("weight", ct.c_void_p), ("escaped", ct.c_void_p)]
+
+
+_P = ct.c_void_p
+_SIGNATURES = {
+    "rt_version": ([], ct.c_char_p),
+    "rt_last_error": ([], ct.c_char_p),
+    "rt_kappa_table_elems": ([_P], ct.c_size_t),
+    "rt_build_kappa": ([_P, _P, _P, _P, _P, _P], ct.c_int),
+    "rt_trace": ([_P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
+                  ct.c_int32, _P, _P, _P], ct.c_int),
+    "rt_tally_zero": ([_P, ct.c_int64, _P], ct.c_int),
+    "rt_tally": ([_P, ct.c_int64, _P, _P, _P], ct.c_int),
+    "rt_status_read": ([_P, _P], ct.c_int),
+}
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path) or os.environ.get("RT_GB300_AUTOBUILD", "1") == "1":
+            path = _build.build()
+        L = ct.CDLL(path)
+        for name, (args, res) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != RT_OK:
+        raise RtError(st, where, lib().rt_last_error().decode())
+
+
+def __getattr__(name):  # rt_* entry points by their C names
+    if name in _SIGNATURES:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- marshalling
+def make_lines(lines, memory: str = "host"):
+    """rt_lines from an object with nu0, S_ref, gamma_ref, E_lower (float64 arrays)
+    and T_ref, n_T, q_exp, mass_amu.  memory='host' keeps numpy arrays;
+    'device' copies them to CUDA tensors.  Returns (struct, keepalive)."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(getattr(lines, k), dtype=np.float64)
+            for k in ("nu0", "S_ref", "gamma_ref", "E_lower")]
+    n = int(arrs[0].shape[0])
+    if memory == "device":
+        import torch
+        keep = [torch.from_numpy(a).cuda() for a in arrs]
+        ptrs = [k.data_ptr() if n else None for k in keep]
+        mem = RT_MEM_DEVICE
+    else:
+        keep = arrs
+        ptrs = [a.ctypes.data if n else None for a in arrs]
+        mem = RT_MEM_HOST
+    s = rt_lines(n, *ptrs, float(lines.T_ref), float(lines.n_T), float(lines.q_exp),
+                 float(lines.mass_amu), mem, 0)
+    return s, keep
+
+
+def make_spectral(spec) -> rt_spectral:
+    return rt_spectral(float(spec.nu_min), float(spec.dnu), int(spec.n_nu), float(spec.cutoff),
+                       PROFILE[spec.profile] if isinstance(spec.profile, str) else int(spec.profile),
+                       int(spec.nT), float(spec.T_min), float(spec.T_max), float(spec.p_ref_atm),
+                       float(spec.x_ref))
+
+
+def make_grid(grid, device="cuda"):
+    """rt_grid with the fields copied to CUDA float32 tensors. Returns (struct, keepalive)."""
+    import torch
+
+    def dev(a):
+        if a is None:
+            return None
+        t = a if isinstance(a, torch.Tensor) else torch.from_numpy(a)
+        return t.to(device=device, dtype=torch.float32).contiguous()
+
+    T, p, x = dev(grid.T), dev(grid.p_atm), dev(grid.x)
+    s = rt_grid(int(grid.nx), int(grid.ny), int(grid.nz), 0, float(grid.hx), float(grid.hy),
+                float(grid.hz), T.data_ptr(), None if p is None else p.data_ptr(),
+                None if x is None else x.data_ptr())
+    return s, (T, p, x)
+
+
+class Tally:
+    """Device tally buffers (caller-owned torch tensors) of a grid of ncells cells."""
+
+    def __init__(self, ncells: int, device="cuda"):
+        import torch
+        self.ncells = int(ncells)
+        self.absorbed = torch.zeros(self.ncells, dtype=torch.float64, device=device)
+        self.scalars = torch.zeros(4, dtype=torch.float64, device=device)
+        self.steps = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.buf = rt_tally_buf(self.absorbed.data_ptr(), self.scalars.data_ptr(),
+                                self.steps.data_ptr(), self.status.data_ptr())
+
+    def zero(self, stream=None):
+        _check(lib().rt_tally_zero(ct.byref(self.buf), self.ncells, _stream_ptr(stream)), "rt_tally_zero")
+
+    def read(self, stream=None, absorbed=True, check=True):
+        """rt_tally: returns (absorbed float64 numpy or None, scalars[4], status)."""
+        import numpy as np
+        sc = np.zeros(4, dtype=np.float64)
+        ab = np.zeros(self.ncells, dtype=np.float64) if absorbed else None
+        st = lib().rt_tally(ct.byref(self.buf), self.ncells,
+                            None if ab is None else ab.ctypes.data, sc.ctypes.data, _stream_ptr(stream))
+        if check:
+            _check(st, "rt_tally")
+        return ab, sc, st
+
+
+class Record:
+    """Optional per-ray record buffers for the first n rays of a trace call."""
+
+    def __init__(self, n: int, max_visits: int, device="cuda"):
+        import torch
+        self.n, self.max_visits = int(n), int(max_visits)
+        self.cells = torch.full((self.n, self.max_visits), -1, dtype=torch.int32, device=device)
+        self.ds = torch.zeros((self.n, self.max_visits), dtype=torch.float32, device=device)
+        self.n_visits = torch.zeros(self.n, dtype=torch.int32, device=device)
+        self.weight = torch.zeros(self.n, dtype=torch.float32, device=device)
+        self.escaped = torch.zeros(self.n, dtype=torch.float32, device=device)
+        self.buf = rt_record(self.n, self.max_visits, 0, self.cells.data_ptr(), self.ds.data_ptr(),
+                             self.n_visits.data_ptr(), self.weight.data_ptr(), self.escaped.data_ptr())
+
+
+def build_kappa(lines, spec, out=None, stream=None, memory="host", evals=None, status=None):
+    """Run rt_build_kappa; returns the (nT, n_nu) float32 CUDA tensor."""
+    import torch
+    S = make_spectral(spec)
+    L, keep = make_lines(lines, memory)
+    if out is None:
+        out = torch.empty((int(spec.nT), int(spec.n_nu)), dtype=torch.float32, device="cuda")
+    st = lib().rt_build_kappa(ct.byref(L), ct.byref(S), _ptr(out), _ptr(evals), _ptr(status),
+                              _stream_ptr(stream))
+    _check(st, "rt_build_kappa")
+    if memory == "host":
+        # host arrays are read by the call's copies before it returns
+        pass
+    out._rt_keep = keep
+    return out
+
+
+def trace(grid_struct, kappa, spec, tally: Tally, n_rays: int, ray_begin: int = 0,
+          n_rays_total: int | None = None, seed: int = 0, enclosure: int = 0, flags: int = 0,
+          record: Record | None = None, stream=None):
+    """Run rt_trace (asynchronous); accumulates into ``tally``."""
+    S = make_spectral(spec)
+    st = lib().rt_trace(ct.byref(grid_struct), _ptr(kappa), ct.byref(S), int(ray_begin), int(n_rays),
+                        int(n_rays_total if n_rays_total is not None else n_rays), int(seed),
+                        int(enclosure), int(flags), ct.byref(tally.buf),
+                        None if record is None else ct.byref(record.buf), _stream_ptr(stream))
+    _check(st, "rt_trace")

@@ -1,0 +1,431 @@
+// Absorption-coefficient table on a temperature grid: Eqs. (S) and (tau) of
+// Section 3, for one absorbing gas, with Lorentz or Voigt line shapes and a
+// wing cutoff.  Three kernels:
+//   k_line_geometry : per line, the binary64 grid decisions (cutoff window
+//                     [j_lo, j_hi], nearest grid index j_c and offset) and the
+//                     profile-evaluation count; validates device-resident lists.
+//   k_prefactor     : per (T node, line), Eq. (S) times the number density and
+//                     the width parameters, in binary32 with double-float
+//                     arithmetic for the Boltzmann exponent.
+//   k_kappa         : per (1024-point wavenumber tile, T node), the line sum.
+//                     The tile's lines are staged in shared memory by bulk
+//                     asynchronous copies (cp.async.bulk + mbarrier), double
+//                     buffered; each thread owns 4 consecutive points (one
+//                     float4 store) and Kahan-sums over lines in ascending nu0.
+#include <cmath>
+#include <mutex>
+
+#include "rt_common.cuh"
+
+namespace rt {
+namespace {
+
+constexpr int kTileThreads = 256;
+constexpr int kPtsPerThread = 4;
+constexpr int kTilePts = kTileThreads * kPtsPerThread;  // 1024 wavenumbers per block
+constexpr int kChunk = 512;                              // lines per staged chunk
+constexpr unsigned kWaitLimit = 1u << 22;                // bounded mbarrier waits
+
+// CODATA 2018 (SI); derived quantities are formed on the host in binary64.
+constexpr double kH = 6.62607015e-34, kC = 299792458.0, kKB = 1.380649e-23;
+constexpr double kAmu = 1.66053906660e-27, kAtm = 101325.0;
+constexpr double kPi = 3.14159265358979323846;
+
+struct GeomParams {
+  double nu_min, dnu, cutoff;
+  long long n_nu, n_lines;
+  int nT, check;
+};
+
+struct PrefParams {
+  double T_min, T_max, T_ref;  // exact inputs, split into double-float in the kernel
+  df c2;                       // second radiation constant h c / k_B, cm K
+  float u_coef;                // x_ref p_ref atm / k_B * 1e-6  [cm^-3 K]
+  float p_ref, n_T, q_exp;
+  float doppler;               // sqrt(2 ln2 k_B / (m amu)) / c  [K^-1/2]
+  float inv_dnu, dnu;
+  long long n_lines;
+  int nT, profile;
+};
+
+__device__ __forceinline__ double grid_nu(double nu_min, long long j, double dnu) {
+  return __dadd_rn(nu_min, __dmul_rn((double)j, dnu));
+}
+
+__global__ void k_line_geometry(const double *__restrict__ nu0, const double *__restrict__ S,
+                                const double *__restrict__ g, const double *__restrict__ E,
+                                GeomParams P, int4 *__restrict__ R,
+                                unsigned long long *evals, uint32_t *status) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long cnt = 0;
+  if (l < P.n_lines) {
+    const double v = nu0[l];
+    if (P.check) {
+      const double s = S[l], gg = g[l], e = E[l];
+      if (!isfinite(v) || !isfinite(s) || !(s > 0.0) || !isfinite(gg) || !(gg > 0.0) ||
+          !isfinite(e) || !(e >= 0.0))
+        status_or(status, RT_DEV_NONFINITE);
+      if (l > 0 && !(nu0[l - 1] <= v)) status_or(status, RT_DEV_UNSORTED);
+    }
+    // nearest grid index: the origin of the line's local coordinate
+    double fc = (v - P.nu_min) / P.dnu;
+    fc = fmin(fmax(isfinite(fc) ? fc : 0.0, -536870912.0), 536870912.0);
+    const long long jc = llrint(fc);
+    const double dc = __dsub_rn(grid_nu(P.nu_min, jc, P.dnu), v);  // nu_jc - nu0
+    const float dg = __double2float_rn(dc / P.dnu);                 // grid units
+    // inclusive cutoff window: -cutoff <= nu_j - nu0 <= cutoff, in binary64
+    double flo = floor((v - P.cutoff - P.nu_min) / P.dnu) - 1.0;
+    double fhi = ceil((v + P.cutoff - P.nu_min) / P.dnu) + 1.0;
+    flo = fmin(fmax(isfinite(flo) ? flo : 0.0, -1.0), (double)P.n_nu + 1.0);
+    fhi = fmin(fmax(isfinite(fhi) ? fhi : 0.0, -2.0), (double)P.n_nu + 1.0);
+    long long lo = (long long)flo, hi = (long long)fhi;
+    if (lo < 0) lo = 0;
+    if (hi > P.n_nu - 1) hi = P.n_nu - 1;
+#pragma unroll 1
+    for (int it = 0; it < 6 && lo < P.n_nu; ++it)
+      if (__dsub_rn(grid_nu(P.nu_min, lo, P.dnu), v) < -P.cutoff) ++lo;
+#pragma unroll 1
+    for (int it = 0; it < 6 && hi >= 0; ++it)
+      if (__dsub_rn(grid_nu(P.nu_min, hi, P.dnu), v) > P.cutoff) --hi;
+    R[l] = make_int4((int)lo, (int)hi, (int)jc, __float_as_int(dg));
+    if (hi >= lo) cnt = (unsigned long long)(hi - lo + 1) * (unsigned long long)P.nT;
+  }
+  if (evals) {
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(evals, cnt);
+  }
+}
+
+__global__ void k_prefactor(const double *__restrict__ nu0, const double *__restrict__ S,
+                            const double *__restrict__ g, const double *__restrict__ E,
+                            PrefParams Q, float4 *__restrict__ Pout) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (l >= Q.n_lines) return;
+  // T_k = T_min + k (T_max - T_min) / (nT - 1) and 1/T_k in double-float
+  df Tk = df_from_double(Q.T_min);
+  if (Q.nT > 1) {
+    const df span = df_add(df_from_double(Q.T_max), df_neg(Tk));
+    const df step = df_mul(span, df_recip(df{(float)(Q.nT - 1), 0.0f}));
+    Tk = df_add(Tk, df_mul(step, df{(float)k, 0.0f}));
+  }
+  const df iT = df_recip(Tk);
+  const df Tref = df_from_double(Q.T_ref);
+  const df iTref = df_recip(Tref);
+  const float iTf = iT.hi;
+  const float tr = Tref.hi * iTf;  // T_ref / T
+  // Eq. (S): Q ratio, Boltzmann ratio (exponent in double-float), stimulated emission
+  const float qratio = powf(tr, Q.q_exp);
+  const df arg = df_mul(df_mul(Q.c2, df_from_double(E[l])), df_add(iTref, df_neg(iT)));
+  const float boltz = expf(arg.hi) * (1.0f + arg.lo);
+  const float nu0f = __double2float_rn(nu0[l]);
+  const float c2nu = Q.c2.hi * nu0f;
+  const float stim = expm1f(-c2nu * iTf) / expm1f(-c2nu * iTref.hi);
+  const float S_T = __double2float_rn(S[l]) * qratio * boltz * stim;
+  const float A = (Q.u_coef * iTf) * S_T;  // u(T) S(T), cm^-1 per unit profile
+  const float gam = __double2float_rn(g[l]) * Q.p_ref * powf(tr, Q.n_T);
+  float4 out;
+  if (Q.profile == RT_PROFILE_LORENTZ) {
+    const float gg = gam * Q.inv_dnu;  // half-width in grid units
+    out = make_float4(A * gg * (float)(1.0 / kPi) * Q.inv_dnu, gg * gg, 0.0f, 0.0f);
+  } else {
+    const float alpha = nu0f * sqrtf(Tk.hi) * Q.doppler;  // Doppler HWHM, cm^-1
+    const float s = 0.83255461f / alpha;                  // sqrt(ln 2) / alpha
+    const float y = s * gam;
+    out = make_float4(A * s * (float)(1.0 / kPi), y, s * Q.dnu, y * y);
+  }
+  Pout[(long long)k * Q.n_lines + l] = out;
+}
+
+// ---- bulk asynchronous copies global -> shared, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ long long lower_bound_hi(const int4 *R, long long n, int j) {
+  long long a = 0, b = n;  // first l with R[l].y >= j
+  while (a < b) {
+    long long m = (a + b) >> 1;
+    if (R[m].y < j) a = m + 1; else b = m;
+  }
+  return a;
+}
+__device__ __forceinline__ long long lower_bound_lo(const int4 *R, long long n, int j) {
+  long long a = 0, b = n;  // first l with R[l].x >= j
+  while (a < b) {
+    long long m = (a + b) >> 1;
+    if (R[m].x < j) a = m + 1; else b = m;
+  }
+  return a;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
+  const float y = __fsub_rn(v, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+template <int PROFILE>
+__global__ void __launch_bounds__(kTileThreads)
+k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_lines,
+        long long n_nu, WeidCoef wc, int vec_ok, float *__restrict__ kappa, uint32_t *status) {
+  __shared__ __align__(16) float4 sP[2][kChunk];
+  __shared__ __align__(16) int4 sR[2][kChunk];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ long long s_lb, s_ub;
+  __shared__ int s_abort;
+
+  const int k = blockIdx.y;
+  const long long j0 = (long long)blockIdx.x * kTilePts;
+  const long long jend = min(j0 + (long long)kTilePts, n_nu);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int jw0 = (int)(j0 + warp * 32 * kPtsPerThread);
+  const int jw1 = jw0 + 32 * kPtsPerThread - 1;
+  const int jt = jw0 + lane * kPtsPerThread;
+
+  if (threadIdx.x == 0) {
+    s_lb = lower_bound_hi(R, n_lines, (int)j0);
+    s_ub = max(s_lb, lower_bound_lo(R, n_lines, (int)jend));
+    s_abort = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long long lb = s_lb, ub = s_ub;
+  const int nchunks = (int)((ub - lb + kChunk - 1) / kChunk);
+  const float4 *Pk = P + (long long)k * n_lines;
+
+  auto issue = [&](int c) {
+    const long long l0 = lb + (long long)c * kChunk;
+    const uint32_t cnt = (uint32_t)min((long long)kChunk, ub - l0);
+    const int b = c & 1;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive_expect_tx(&bars[b], cnt * 32u);
+    bulk_g2s(&sP[b][0], Pk + l0, cnt * 16u, &bars[b]);
+    bulk_g2s(&sR[b][0], R + l0, cnt * 16u, &bars[b]);
+  };
+
+  float acc[kPtsPerThread], cmp[kPtsPerThread];
+#pragma unroll
+  for (int q = 0; q < kPtsPerThread; ++q) acc[q] = cmp[q] = 0.0f;
+
+  if (threadIdx.x == 0) {
+    if (nchunks > 0) issue(0);
+    if (nchunks > 1) issue(1);
+  }
+  for (int c = 0; c < nchunks; ++c) {
+    const int b = c & 1;
+    const uint32_t parity = (uint32_t)((c >> 1) & 1);
+    unsigned spins = 0;
+    int timed_out = 0;
+    while (!mbar_try_wait(&bars[b], parity)) {
+      if (++spins > kWaitLimit) {
+        timed_out = 1;
+        break;
+      }
+    }
+    if (__syncthreads_or(timed_out)) {  // the block leaves together
+      if (threadIdx.x == 0) {
+        s_abort = 1;
+        status_or(status, RT_DEV_TIMEOUT);
+      }
+      break;
+    }
+    const long long l0 = lb + (long long)c * kChunk;
+    const int cnt = (int)min((long long)kChunk, ub - l0);
+#pragma unroll 1
+    for (int i = 0; i < cnt; ++i) {
+      const int4 r = sR[b][i];
+      if (r.y < jw0 || r.x > jw1) continue;  // warp-uniform: no overlap with this warp
+      const float4 p = sP[b][i];
+      const float u0 = (float)(jt - r.z) + __int_as_float(r.w);
+#pragma unroll
+      for (int q = 0; q < kPtsPerThread; ++q) {
+        const int j = jt + q;
+        if (j < r.x || j > r.y) continue;
+        const float u = u0 + (float)q;
+        float v;
+        if (PROFILE == RT_PROFILE_LORENTZ) {
+          v = __fdividef(p.x, __fmaf_rn(u, u, p.y));
+        } else {
+          v = p.x * faddeeva_re(p.z * u, p.y, wc);
+        }
+        kahan_add(acc[q], cmp[q], v);
+      }
+    }
+    __syncthreads();  // every thread is done with buffer b
+    if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
+  }
+  __syncthreads();
+  if (s_abort) return;
+
+  float *row = kappa + (long long)k * n_nu;
+  float out[kPtsPerThread];
+#pragma unroll
+  for (int q = 0; q < kPtsPerThread; ++q) out[q] = __fsub_rn(acc[q], cmp[q]);
+  if ((long long)jt + kPtsPerThread <= jend && vec_ok) {
+    *reinterpret_cast<float4 *>(row + jt) = make_float4(out[0], out[1], out[2], out[3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < kPtsPerThread; ++q)
+      if ((long long)jt + q < jend) row[jt + q] = out[q];
+  }
+}
+
+}  // namespace
+
+rt_status validate_spec(const rt_spectral *s) {
+  if (!s) return fail(RT_E_INVAL, "spec is NULL");
+  if (!(s->n_nu >= 1) || s->n_nu > (1LL << 30))
+    return fail(RT_E_INVAL, "spec.n_nu must be in [1, 2^30]");
+  if (!std::isfinite(s->nu_min) || !std::isfinite(s->dnu) || !(s->dnu > 0))
+    return fail(RT_E_INVAL, "spec.nu_min / dnu must be finite, dnu > 0");
+  if (!std::isfinite(s->cutoff) || s->cutoff < 0 || s->cutoff / s->dnu > (double)(1 << 28))
+    return fail(RT_E_INVAL, "spec.cutoff must be finite, >= 0 and < 2^28 dnu");
+  if (s->profile != RT_PROFILE_LORENTZ && s->profile != RT_PROFILE_VOIGT)
+    return fail(RT_E_INVAL, "spec.profile must be RT_PROFILE_LORENTZ or RT_PROFILE_VOIGT");
+  if (s->nT < 1 || s->nT > 65535) return fail(RT_E_INVAL, "spec.nT must be in [1, 65535]");
+  if (!std::isfinite(s->T_min) || !std::isfinite(s->T_max) || !(s->T_min > 0) ||
+      s->T_max < s->T_min || (s->nT > 1 && !(s->T_max > s->T_min)))
+    return fail(RT_E_INVAL, "spec temperatures must satisfy 0 < T_min <= T_max (< when nT > 1)");
+  if (!std::isfinite(s->p_ref_atm) || !(s->p_ref_atm > 0) || !std::isfinite(s->x_ref) ||
+      !(s->x_ref > 0))
+    return fail(RT_E_INVAL, "spec.p_ref_atm and spec.x_ref must be finite and > 0");
+  return RT_OK;
+}
+
+namespace {
+
+rt_status validate_host_lines(const rt_lines *L, const rt_spectral *s) {
+  const double lim = 536870912.0 * s->dnu;  // 2^29 grid steps
+  for (int64_t l = 0; l < L->n; ++l) {
+    const double v = L->nu0[l], S = L->S_ref[l], g = L->gamma_ref[l], E = L->E_lower[l];
+    if (!std::isfinite(v) || !std::isfinite(S) || !(S > 0) || !std::isfinite(g) || !(g > 0) ||
+        !std::isfinite(E) || !(E >= 0))
+      return fail(RT_E_NONFINITE, "line %lld: non-finite or non-positive parameter", (long long)l);
+    if (!(std::fabs(v - s->nu_min) <= lim))
+      return fail(RT_E_INVAL, "line %lld: centre too far from the spectral grid", (long long)l);
+    if (l > 0 && !(L->nu0[l - 1] <= v))
+      return fail(RT_E_UNSORTED, "line %lld: centres not in ascending order", (long long)l);
+  }
+  return RT_OK;
+}
+
+}  // namespace
+
+rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                           unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
+  rt_status v = validate_spec(spec);
+  if (v != RT_OK) return v;
+  if (!lines || !kappa) return fail(RT_E_INVAL, "rt_build_kappa: lines or kappa is NULL");
+  if (lines->n < 0 || lines->n > (1LL << 31) - 1) return fail(RT_E_INVAL, "lines.n out of range");
+  if (lines->memory != RT_MEM_HOST && lines->memory != RT_MEM_DEVICE)
+    return fail(RT_E_INVAL, "lines.memory must be RT_MEM_HOST or RT_MEM_DEVICE");
+  if (!std::isfinite(lines->T_ref) || !(lines->T_ref > 0) || !std::isfinite(lines->n_T) ||
+      !std::isfinite(lines->q_exp) || !std::isfinite(lines->mass_amu) || !(lines->mass_amu > 0))
+    return fail(RT_E_INVAL, "lines: T_ref, n_T, q_exp, mass_amu must be finite (T_ref, mass > 0)");
+  const long long n = lines->n;
+  if (n > 0 && (!lines->nu0 || !lines->S_ref || !lines->gamma_ref || !lines->E_lower))
+    return fail(RT_E_INVAL, "lines: NULL array");
+  if (lines->memory == RT_MEM_DEVICE && !status)
+    return fail(RT_E_INVAL, "device-resident lines need a device status word");
+  if (lines->memory == RT_MEM_HOST && n > 0) {
+    v = validate_host_lines(lines, spec);
+    if (v != RT_OK) return v;
+  }
+  const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
+  if (n == 0) {
+    RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
+    return RT_OK;
+  }
+
+  // scratch: [line arrays if host-resident][R: n int4][P: nT*n float4]
+  const size_t bytes_lines = (lines->memory == RT_MEM_HOST) ? 4 * n * sizeof(double) : 0;
+  const size_t off_R = (bytes_lines + 255) & ~size_t(255);
+  const size_t off_P = (off_R + n * sizeof(int4) + 255) & ~size_t(255);
+  const size_t total = off_P + (size_t)spec->nT * n * sizeof(float4);
+  Scratch scr;
+  v = scr.alloc(total, st);
+  if (v != RT_OK) return v;
+  char *base = scr.as<char>();
+  const double *d_nu0 = lines->nu0, *d_S = lines->S_ref, *d_g = lines->gamma_ref, *d_E = lines->E_lower;
+  if (lines->memory == RT_MEM_HOST) {
+    double *d = reinterpret_cast<double *>(base);
+    RT_CUDA_TRY(cudaMemcpyAsync(d, lines->nu0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(d + n, lines->S_ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(d + 2 * n, lines->gamma_ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(d + 3 * n, lines->E_lower, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    d_nu0 = d; d_S = d + n; d_g = d + 2 * n; d_E = d + 3 * n;
+  }
+  int4 *R = reinterpret_cast<int4 *>(base + off_R);
+  float4 *P = reinterpret_cast<float4 *>(base + off_P);
+
+  GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
+               lines->memory == RT_MEM_DEVICE ? 1 : 0};
+  const int tb = 256;
+  k_line_geometry<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d_nu0, d_S, d_g, d_E, G, R,
+                                                                evals_out, status);
+  RT_CUDA_TRY(cudaGetLastError());
+
+  PrefParams Q;
+  Q.T_min = spec->T_min;
+  Q.T_max = spec->T_max;
+  Q.T_ref = lines->T_ref;
+  const double c2 = 100.0 * kH * kC / kKB;
+  Q.c2.hi = (float)c2;
+  Q.c2.lo = (float)(c2 - (double)Q.c2.hi);
+  Q.u_coef = (float)(spec->x_ref * spec->p_ref_atm * kAtm / kKB * 1e-6);
+  Q.p_ref = (float)spec->p_ref_atm;
+  Q.n_T = (float)lines->n_T;
+  Q.q_exp = (float)lines->q_exp;
+  Q.doppler = (float)(std::sqrt(2.0 * std::log(2.0) * kKB / (lines->mass_amu * kAmu)) / kC);
+  Q.inv_dnu = (float)(1.0 / spec->dnu);
+  Q.dnu = (float)spec->dnu;
+  Q.n_lines = n;
+  Q.nT = spec->nT;
+  Q.profile = spec->profile;
+  dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
+  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P);
+  RT_CUDA_TRY(cudaGetLastError());
+
+  static WeidCoef wc;
+  static std::once_flag wc_once;
+  std::call_once(wc_once, [] { weideman_coefficients(&wc); });
+  const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
+  dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)spec->nT);
+  if (spec->profile == RT_PROFILE_LORENTZ)
+    k_kappa<RT_PROFILE_LORENTZ><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc, vec_ok, kappa, status);
+  else
+    k_kappa<RT_PROFILE_VOIGT><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc, vec_ok, kappa, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
+}  // namespace rt
+
+extern "C" rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                                    unsigned long long *evals_out, uint32_t *status, void *stream) {
+  return rt::build_kappa_impl(lines, spec, kappa, evals_out, status, (cudaStream_t)stream);
+}

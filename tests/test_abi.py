@@ -1,0 +1,105 @@
+"""The C-ABI library loads, exports every entry point include/rt.h declares,
+and rejects bad arguments on the host before any launch (no GPU needed)."""
+import ctypes as ct
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_cs_0703028_gb300 as rt
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "rt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rt_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("rt_build_kappa", "rt_trace", "rt_tally", "rt_tally_zero", "rt_status_read",
+              "rt_last_error", "rt_version", "rt_kappa_table_elems"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = rt.lib()
+    for n in _declared():
+        assert hasattr(L, n), n
+        assert n in rt._SIGNATURES, f"binding misses {n}"
+
+
+def test_version_and_table_size():
+    assert b"sm_103a" in rt.lib().rt_version()
+    s = rt.make_spectral(synth.config(1).spec)
+    assert rt.lib().rt_kappa_table_elems(ct.byref(s)) == 64 * 100000
+    assert rt.lib().rt_kappa_table_elems(None) == 0
+
+
+def _status(call):
+    st = call()
+    return st, rt.lib().rt_last_error().decode()
+
+
+def test_build_kappa_rejects_bad_input_on_host():
+    L = rt.lib()
+    case = synth.config(0)
+    spec = rt.make_spectral(case.spec)
+    lines, keep = rt.make_lines(case.lines)
+    dummy = ct.c_void_p(16)   # never dereferenced: validation fails first
+    st, msg = _status(lambda: L.rt_build_kappa(None, ct.byref(spec), dummy, None, None, None))
+    assert st == rt.RT_E_INVAL
+    bad = rt.make_spectral(case.spec)
+    bad.dnu = 0.0
+    assert L.rt_build_kappa(ct.byref(lines), ct.byref(bad), dummy, None, None, None) == rt.RT_E_INVAL
+    bad = rt.make_spectral(case.spec)
+    bad.profile = 7
+    assert L.rt_build_kappa(ct.byref(lines), ct.byref(bad), dummy, None, None, None) == rt.RT_E_INVAL
+    bad = rt.make_spectral(case.spec)
+    bad.nT, bad.T_max = 4, bad.T_min
+    assert L.rt_build_kappa(ct.byref(lines), ct.byref(bad), dummy, None, None, None) == rt.RT_E_INVAL
+    # unsorted and non-finite line lists
+    ul = case.lines.subset(np.arange(case.lines.n)[::-1])
+    ls, keep2 = rt.make_lines(ul)
+    st, msg = _status(lambda: L.rt_build_kappa(ct.byref(ls), ct.byref(spec), dummy, None, None, None))
+    assert st == rt.RT_E_UNSORTED and "ascending" in msg
+    nl = case.lines.subset(np.arange(case.lines.n))
+    nl.S_ref[3] = math.nan
+    ls, keep3 = rt.make_lines(nl)
+    assert L.rt_build_kappa(ct.byref(ls), ct.byref(spec), dummy, None, None, None) == rt.RT_E_NONFINITE
+    nl = case.lines.subset(np.arange(case.lines.n))
+    nl.gamma_ref[0] = -1.0
+    ls, keep4 = rt.make_lines(nl)
+    assert L.rt_build_kappa(ct.byref(ls), ct.byref(spec), dummy, None, None, None) == rt.RT_E_NONFINITE
+    # device-resident lines need a status word
+    dl = rt.rt_lines(case.lines.n, 16, 16, 16, 16, 296.0, 0.75, 1.0, 44.0, rt.RT_MEM_DEVICE, 0)
+    assert L.rt_build_kappa(ct.byref(dl), ct.byref(spec), dummy, None, None, None) == rt.RT_E_INVAL
+
+
+def test_trace_rejects_bad_input_on_host():
+    L = rt.lib()
+    case = synth.config(0)
+    spec = rt.make_spectral(case.spec)
+    g = rt.rt_grid(64, 1, 1, 0, 1 / 64, math.inf, math.inf, 16, None, None)
+    t = rt.rt_tally_buf(16, 16, 16, 16)
+    k = ct.c_void_p(16)
+    assert L.rt_trace(None, k, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
+    bad = rt.rt_grid(0, 1, 1, 0, 1.0, 1.0, 1.0, 16, None, None)
+    assert L.rt_trace(ct.byref(bad), k, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
+    bad = rt.rt_grid(4, 4, 4, 0, math.inf, math.inf, math.inf, 16, None, None)
+    assert L.rt_trace(ct.byref(bad), k, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
+    bad = rt.rt_grid(4, 4, 4, 0, -1.0, 1.0, 1.0, 16, None, None)
+    assert L.rt_trace(ct.byref(bad), k, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
+    # n_rays_total smaller than n_rays, unknown flags, NULL tally member, NULL kappa
+    assert L.rt_trace(ct.byref(g), k, ct.byref(spec), 0, 10, 5, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
+    assert L.rt_trace(ct.byref(g), k, ct.byref(spec), 0, 10, 10, 0, 0, 1 << 9, ct.byref(t), None, None) == rt.RT_E_INVAL
+    tb = rt.rt_tally_buf(16, None, 16, 16)
+    assert L.rt_trace(ct.byref(g), k, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(tb), None, None) == rt.RT_E_INVAL
+    assert L.rt_trace(ct.byref(g), None, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
+    assert L.rt_tally(ct.byref(t), 0, None, None, None) == rt.RT_E_INVAL
+    assert L.rt_status_read(None, None) == rt.RT_E_INVAL
