@@ -27,9 +27,10 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 FP32_LANES_PER_SM = 128
-# algorithmic binary32 flops of one profile evaluation (FMA = 2): far-wing
-# Voigt (five-term asymptotic series) and Lorentz, each with the Kahan update
-FLOPS_PER_EVAL = {"voigt": 46, "lorentz": 11}
+# algorithmic binary32 flops of one profile evaluation (FMA = 2, reciprocal = 1):
+# far-wing Voigt (three-term asymptotic series in t = 1/|z|^2, s = y^2 t) and
+# Lorentz, each with its grid coordinate and the Kahan update
+FLOPS_PER_EVAL = {"voigt": 22, "lorentz": 9}
 
 
 def _dist():
@@ -76,6 +77,28 @@ def _clock_summary(path, dev_index):
                 reasons.add(n)
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
             "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _profiled_traffic(summary, sources):
+    """DRAM bytes per launch from a committed ncu summary, or None once the
+    kernel's sources have changed since the counters were taken."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", summary)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha: ([0-9a-f]{12})", text)
+    m_tr = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+    if not m_sha or not m_tr:
+        return None
+    h = hashlib.sha1()
+    for s in sources:
+        h.update(hashlib.sha1(open(os.path.join(ROOT, "paper_cs_0703028_gb300", "csrc", s), "rb")
+                              .read()).hexdigest().encode() + b"  " +
+                 os.path.join("paper_cs_0703028_gb300", "csrc", s).encode() + b"\n")
+    return int(m_tr.group(1)) if h.hexdigest()[:12] == m_sha.group(1) else None
 
 
 def _peaks():
@@ -231,13 +254,7 @@ def run_gpu(args):
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_clock_mhz * 1e6 / 1e12
     flops = evals_per_step * FLOPS_PER_EVAL[spec.profile]
     achieved = flops / (ms_build * 1e-3) / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "k_kappa_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get("bytes_per_launch")
-        except ValueError:
-            traffic = None
+    traffic = _profiled_traffic("k_kappa_box32_voigt20k.md", ["rt_kappa.cu", "rt_common.cuh"])
     out = {
         "metric": "ray-cell steps/s + line-profile evals/s; surrogate vs plain at <=1% tally err",
         "value": value,

@@ -101,38 +101,42 @@ __device__ __forceinline__ df df_from_double(double v) {
 
 // ---------------------------------------------------------------- Faddeeva
 // sqrt(pi) * Re w(x + i y) for y > 0 in binary32, w the Faddeeva function
-// (the Voigt function times sqrt(pi)).  Three regions by |z|:
+// (the Voigt function times sqrt(pi)).  Regions by |z|:
 //  |z| >= 8 : the asymptotic series w ~ (i / (sqrt(pi) z)) sum_n (2n-1)!! / (2 z^2)^n
-//             (Abramowitz & Stegun 7.1.23), five terms, evaluated in real arithmetic;
+//             (Abramowitz & Stegun 7.1.23).  Written with t = 1/|z|^2 and
+//             s = y^2 t, its real part is
+//               sqrt(pi) Re w = y t [1 + t (3 - 4s)/2 + 3 t^2 (5 - 20s + 16s^2)/4
+//                                    + 15 t^3 (7 - 56s + 112s^2 - 64s^3)/8
+//                                    + 105 t^4 (9 - 120s + 432s^2 - 576s^3 + 256s^4)/16 + ...]
+//             (Im z^(2n+1) expanded with x^2 t = 1 - s); three terms for |z| >= 20,
+//             five for 8 <= |z| < 20;
 //  5 <= |z| < 8 : Laplace's continued fraction for w, depth 6 (the imaginary parts
 //             of its partial denominators add without cancellation);
 //  |z| < 5  : Weideman's (1994) rational series in Z = (L + iz)/(L - iz), N = 24,
 //             coefficients from the Fourier series of exp(-t^2)(L^2 + t^2) on the
 //             tan-mapped line (computed on the host in binary64).
-// Measured relative error of the result against binary64: <= 7e-7 for |z| >= 5,
-// <= 1.5e-6 for |z| < 5 with y >= 0.5, degrading toward 1e-4 as y -> 0.
+// Measured relative error against binary64: <= 5.3e-7 for |z| >= 8, <= 7e-7 for
+// 5 <= |z| < 8, <= 1.5e-6 for |z| < 5 with y >= 0.5 (degrading toward 1e-4 as y -> 0).
 constexpr int kWeidN = 24;
 struct WeidCoef {
   float L;
   float a[kWeidN];  // 2 sqrt(pi) a_n, n = 1..N
 };
 
-__device__ __forceinline__ float faddeeva_re_far(float x, float y) {
-  const float x2 = x * x, y2 = y * y;
-  const float r2 = x2 + y2;
-  const float t = __fdividef(1.0f, r2);
-  const float t2 = t * t;
-  const float qr = (x2 - y2) * t2;
-  const float qi = -2.0f * x * y * t2;
-  // S = 1 + q/2 + 3q^2/4 + 15q^3/8 + 105q^4/16, q = 1/z^2
-  float sr = 6.5625f, si = 0.0f;
-  float nr;
-  nr = 1.875f + qr * sr - qi * si; si = qr * si + qi * sr; sr = nr;
-  nr = 0.75f + qr * sr - qi * si;  si = qr * si + qi * sr; sr = nr;
-  nr = 0.5f + qr * sr - qi * si;   si = qr * si + qi * sr; sr = nr;
-  nr = 1.0f + qr * sr - qi * si;   si = qr * si + qi * sr; sr = nr;
-  // sqrt(pi) w = i S / z = (y + i x) t S
-  return t * (y * sr - x * si);
+// bracket of the three-term series; sqrt(pi) Re w = y t S3
+__device__ __forceinline__ float faddeeva_series3(float t, float s) {
+  const float c1 = fmaf(s, -2.0f, 1.5f);
+  const float c2 = fmaf(s, fmaf(s, 12.0f, -15.0f), 3.75f);
+  return fmaf(t, fmaf(t, c2, c1), 1.0f);
+}
+
+// bracket of the five-term series; sqrt(pi) Re w = y t S5
+__device__ __forceinline__ float faddeeva_series5(float t, float s) {
+  const float c1 = fmaf(s, -2.0f, 1.5f);
+  const float c2 = fmaf(s, fmaf(s, 12.0f, -15.0f), 3.75f);
+  const float c3 = fmaf(s, fmaf(s, fmaf(s, -120.0f, 210.0f), -105.0f), 13.125f);
+  const float c4 = fmaf(s, fmaf(s, fmaf(s, fmaf(s, 1680.0f, -3780.0f), 2835.0f), -787.5f), 59.0625f);
+  return fmaf(t, fmaf(t, fmaf(t, fmaf(t, c4, c3), c2), c1), 1.0f);
 }
 
 __device__ __forceinline__ float faddeeva_re_cf(float x, float y) {
@@ -167,11 +171,23 @@ __device__ __forceinline__ float faddeeva_re_core(float x, float y, const WeidCo
   return vr * qr - vi * qi;
 }
 
-__device__ __forceinline__ float faddeeva_re(float x, float y, const WeidCoef &c) {
-  const float r2 = x * x + y * y;
-  if (r2 >= 64.0f) return faddeeva_re_far(x, y);
+// sqrt(pi) Re w(x + iy) for |z|^2 = r2 below 400 (the five-term, fraction and core regions)
+__device__ __forceinline__ float faddeeva_re_near(float x, float y, float r2, const WeidCoef &c) {
+  if (r2 >= 64.0f) {
+    const float t = __fdividef(1.0f, r2);
+    return y * t * faddeeva_series5(t, y * y * t);
+  }
   if (r2 >= 25.0f) return faddeeva_re_cf(x, y);
   return faddeeva_re_core(x, y, c);
+}
+
+__device__ __forceinline__ float faddeeva_re(float x, float y, const WeidCoef &c) {
+  const float r2 = x * x + y * y;
+  if (r2 >= 400.0f) {
+    const float t = __fdividef(1.0f, r2);
+    return y * t * faddeeva_series3(t, y * y * t);
+  }
+  return faddeeva_re_near(x, y, r2, c);
 }
 
 // Host: Weideman coefficients for N = kWeidN (binary64 DFT, then binary32).

@@ -132,7 +132,7 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
     const float alpha = nu0f * sqrtf(Tk.hi) * Q.doppler;  // Doppler HWHM, cm^-1
     const float s = 0.83255461f / alpha;                  // sqrt(ln 2) / alpha
     const float y = s * gam;
-    out = make_float4(A * s * (float)(1.0 / kPi), y, s * Q.dnu, y * y);
+    out = make_float4(A * s * (float)(1.0 / kPi) * y, y, s * Q.dnu, y * y);
   }
   Pout[(long long)k * Q.n_lines + l] = out;
 }
@@ -177,6 +177,21 @@ __device__ __forceinline__ long long lower_bound_lo(const int4 *R, long long n, 
     if (R[m].x < j) a = m + 1; else b = m;
   }
   return a;
+}
+
+// One profile value times its line factor at grid offset u (grid units).
+// Lorentz: p = {A g / (pi dnu), g^2}.  Voigt: p = {A s y / pi, y, s dnu, y^2} with
+// s = sqrt(ln2)/alpha, so that A f = p.x t S for the far-wing series.
+template <int PROFILE>
+__device__ __forceinline__ float line_value(float u, const float4 p, const WeidCoef &wc) {
+  if (PROFILE == RT_PROFILE_LORENTZ) return __fdividef(p.x, __fmaf_rn(u, u, p.y));
+  const float x = p.z * u;
+  const float r2 = __fmaf_rn(x, x, p.w);
+  if (r2 >= 400.0f) {
+    const float t = __fdividef(1.0f, r2);
+    return p.x * (t * faddeeva_series3(t, p.w * t));
+  }
+  return __fdividef(p.x, p.y) * faddeeva_re_near(x, p.y, r2, wc);
 }
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
@@ -261,18 +276,17 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
       if (r.y < jw0 || r.x > jw1) continue;  // warp-uniform: no overlap with this warp
       const float4 p = sP[b][i];
       const float u0 = (float)(jt - r.z) + __int_as_float(r.w);
+      if (r.x <= jw0 && r.y >= jw1) {  // warp-uniform: the window covers the warp's points
 #pragma unroll
-      for (int q = 0; q < kPtsPerThread; ++q) {
-        const int j = jt + q;
-        if (j < r.x || j > r.y) continue;
-        const float u = u0 + (float)q;
-        float v;
-        if (PROFILE == RT_PROFILE_LORENTZ) {
-          v = __fdividef(p.x, __fmaf_rn(u, u, p.y));
-        } else {
-          v = p.x * faddeeva_re(p.z * u, p.y, wc);
+        for (int q = 0; q < kPtsPerThread; ++q)
+          kahan_add(acc[q], cmp[q], line_value<PROFILE>(u0 + (float)q, p, wc));
+      } else {
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) {
+          const int j = jt + q;
+          if (j < r.x || j > r.y) continue;
+          kahan_add(acc[q], cmp[q], line_value<PROFILE>(u0 + (float)q, p, wc));
         }
-        kahan_add(acc[q], cmp[q], v);
       }
     }
     __syncthreads();  // every thread is done with buffer b

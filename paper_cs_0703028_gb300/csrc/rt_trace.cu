@@ -178,7 +178,7 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
       const float kap = cell_kappa(cells[cell], tab, W.n_nu, W.nT, j);
       const float a = kap > 0.0f ? __fmul_rn(__fmul_rn(kap, 100.0f), ds) : 0.0f;
       const float dep = w * trans * (-expm1f(-a));
-      atomicAdd(absorbed + cell, (double)dep);
+      if (dep != 0.0f) atomicAdd(absorbed + cell, (double)dep);
       // compensated optical depth, transmission exp(-tau)
       if (a == INFINITY) {
         tau = INFINITY;

@@ -263,3 +263,32 @@ def config(index: int, n_rays: Optional[int] = None) -> Case:
         grid = multi_gaussian_grid(128, 1.0, rng_for(4, 1))
         return Case(CONFIG_NAMES[4], lines, spec, grid, n_rays or 1_000_000_000)
     raise ValueError(f"unknown config index {index}")
+
+
+# ---------------------------------------------------------------- surrogate network
+MLP_WIDTH = 128
+MLP_LAYOUT = (("W1", (128, 4)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+              ("W3", (128, 128)), ("b3", (128,)), ("W4", (128, 128)), ("b4", (128,)),
+              ("w5", (128,)), ("b5", (1,)))
+MLP_NPARAM = sum(int(np.prod(s)) for _, s in MLP_LAYOUT)   # 50,305
+
+
+def mlp_offsets():
+    """Offsets of each tensor in the flat float32 parameter vector (row-major W[out][in])."""
+    off, out = 0, {}
+    for name, shape in MLP_LAYOUT:
+        out[name] = (off, shape)
+        off += int(np.prod(shape))
+    return out
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Flat float32 initial parameters: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0."""
+    rng = np.random.default_rng([0, 2, 100 + int(seed)])
+    flat = np.zeros(MLP_NPARAM, dtype=np.float32)
+    for name, (off, shape) in mlp_offsets().items():
+        if name.startswith("W") or name == "w5":
+            fan_in = shape[-1] if len(shape) == 2 else shape[0]
+            n = int(np.prod(shape))
+            flat[off:off + n] = rng.uniform(-1, 1, n).astype(np.float32) / np.float32(np.sqrt(fan_in))
+    return flat
