@@ -188,6 +188,32 @@ rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *
                          unsigned long long *evals_out, uint32_t *status, void *stream);
 
 /*
+ * rt_build_kappa_static -- rt_build_kappa for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this entry point exists for programs
+ * that must not call the CUDA allocator once they run, for example a flow solver
+ * that has handed all device memory to its own fixed pool, or a loop with a
+ * latency budget in which an allocation could stall or fail.  Arguments, result
+ * and errors are those of rt_build_kappa; the caller still provides the lines,
+ * the table and the optional counters.
+ * Scratch: a 32 MiB array in the library's device memory (a file-scope
+ *   __device__ array that every GPU loading the library holds until the process
+ *   exits); the call allocates and frees nothing.
+ * Limit: 16 B per (T node, line) + 16 B per line, plus 32 B per line when the
+ *   lines are host-resident, at most 32 MiB in all (about 2 million (T node, line)
+ *   pairs, e.g. 64 T nodes x 30,000 lines).  Larger inputs return RT_E_INVAL with
+ *   the required size before any work is queued.
+ * Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture.
+ * Sharing: all calls use the same array and it keeps the last call's contents;
+ *   every call writes the scratch it reads before reading it.  Calls whose work
+ *   can overlap on the GPU (other streams, other host threads) race on the array:
+ *   serialise them.
+ */
+rt_status rt_build_kappa_static(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                                unsigned long long *evals_out, uint32_t *status, void *stream);
+
+/*
  * rt_trace -- the Monte-Carlo ray-tracing estimator of Section 3 (Fig. ray).
  * Rays r in [ray_begin, ray_begin + n_rays) of an estimate over n_rays_total rays:
  *   RT_SRC_EMIT: Philox4x32-10 (key = seed, counter = (r_lo, r_hi, call, enclosure))

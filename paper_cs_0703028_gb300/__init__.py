@@ -79,6 +79,7 @@ _SIGNATURES = {
     "rt_last_error": ([], ct.c_char_p),
     "rt_kappa_table_elems": ([_P], ct.c_size_t),
     "rt_build_kappa": ([_P, _P, _P, _P, _P, _P], ct.c_int),
+    "rt_build_kappa_static": ([_P, _P, _P, _P, _P, _P], ct.c_int),
     "rt_trace": ([_P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
                   ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_tally_zero": ([_P, ct.c_int64, _P], ct.c_int),

@@ -437,9 +437,130 @@ rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float
   return RT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch is this file-scope device array: every
+// GPU that loads the library holds it until the process exits.  Host code must
+// not hand the array's name to a kernel (in host code it is a host-side stand-in
+// for the symbol); the device address is looked up once per device below.
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static rt_status static_scratch_address(void **out) {
+  static std::mutex mu;
+  static void *addr[256] = {};
+  int dev = 0;
+  RT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(RT_E_INVAL, "rt_build_kappa_static: device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_static_scratch)");
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return RT_OK;
+}
+
+rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                                  unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
+  rt_status v = validate_spec(spec);
+  if (v != RT_OK) return v;
+  if (!lines || !kappa) return fail(RT_E_INVAL, "rt_build_kappa_static: lines or kappa is NULL");
+  if (lines->n < 0 || lines->n > (1LL << 31) - 1) return fail(RT_E_INVAL, "lines.n out of range");
+  if (lines->memory != RT_MEM_HOST && lines->memory != RT_MEM_DEVICE)
+    return fail(RT_E_INVAL, "lines.memory must be RT_MEM_HOST or RT_MEM_DEVICE");
+  if (!std::isfinite(lines->T_ref) || !(lines->T_ref > 0) || !std::isfinite(lines->n_T) ||
+      !std::isfinite(lines->q_exp) || !std::isfinite(lines->mass_amu) || !(lines->mass_amu > 0))
+    return fail(RT_E_INVAL, "lines: T_ref, n_T, q_exp, mass_amu must be finite (T_ref, mass > 0)");
+  const long long n = lines->n;
+  if (n > 0 && (!lines->nu0 || !lines->S_ref || !lines->gamma_ref || !lines->E_lower))
+    return fail(RT_E_INVAL, "lines: NULL array");
+  if (lines->memory == RT_MEM_DEVICE && !status)
+    return fail(RT_E_INVAL, "device-resident lines need a device status word");
+  // same scratch layout as rt_build_kappa, checked against the fixed array
+  const size_t bytes_lines = (lines->memory == RT_MEM_HOST) ? 4 * (size_t)n * sizeof(double) : 0;
+  const size_t off_R = (bytes_lines + 255) & ~size_t(255);
+  const size_t off_P = (off_R + (size_t)n * sizeof(int4) + 255) & ~size_t(255);
+  const size_t total = off_P + (size_t)spec->nT * (size_t)n * sizeof(float4);
+  if (total > kStaticScratchBytes)
+    return fail(RT_E_INVAL,
+                "rt_build_kappa_static: needs %zu bytes of scratch (16 B per line and T node, 16 B "
+                "per line, plus 32 B per line for host-resident lines), the static array holds %zu",
+                total, kStaticScratchBytes);
+  if (lines->memory == RT_MEM_HOST && n > 0) {
+    v = validate_host_lines(lines, spec);
+    if (v != RT_OK) return v;
+  }
+  const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
+  if (n == 0) {
+    RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
+    return RT_OK;
+  }
+  void *scratch = nullptr;
+  v = static_scratch_address(&scratch);
+  if (v != RT_OK) return v;
+  char *base = reinterpret_cast<char *>(scratch);
+  const double *d_nu0 = lines->nu0, *d_S = lines->S_ref, *d_g = lines->gamma_ref, *d_E = lines->E_lower;
+  if (lines->memory == RT_MEM_HOST) {
+    double *d = reinterpret_cast<double *>(base);
+    RT_CUDA_TRY(cudaMemcpyAsync(d, lines->nu0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(d + n, lines->S_ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(d + 2 * n, lines->gamma_ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RT_CUDA_TRY(cudaMemcpyAsync(d + 3 * n, lines->E_lower, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    d_nu0 = d; d_S = d + n; d_g = d + 2 * n; d_E = d + 3 * n;
+  }
+  int4 *R = reinterpret_cast<int4 *>(base + off_R);
+  float4 *P = reinterpret_cast<float4 *>(base + off_P);
+
+  GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
+               lines->memory == RT_MEM_DEVICE ? 1 : 0};
+  const int tb = 256;
+  k_line_geometry<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d_nu0, d_S, d_g, d_E, G, R,
+                                                                evals_out, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  PrefParams Q;
+  Q.T_min = spec->T_min;
+  Q.T_max = spec->T_max;
+  Q.T_ref = lines->T_ref;
+  const double c2 = 100.0 * kH * kC / kKB;
+  Q.c2.hi = (float)c2;
+  Q.c2.lo = (float)(c2 - (double)Q.c2.hi);
+  Q.u_coef = (float)(spec->x_ref * spec->p_ref_atm * kAtm / kKB * 1e-6);
+  Q.p_ref = (float)spec->p_ref_atm;
+  Q.n_T = (float)lines->n_T;
+  Q.q_exp = (float)lines->q_exp;
+  Q.doppler = (float)(std::sqrt(2.0 * std::log(2.0) * kKB / (lines->mass_amu * kAmu)) / kC);
+  Q.inv_dnu = (float)(1.0 / spec->dnu);
+  Q.dnu = (float)spec->dnu;
+  Q.n_lines = n;
+  Q.nT = spec->nT;
+  Q.profile = spec->profile;
+  dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
+  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P);
+  RT_CUDA_TRY(cudaGetLastError());
+  static WeidCoef wc_static;
+  static std::once_flag wc_static_once;
+  std::call_once(wc_static_once, [] { weideman_coefficients(&wc_static); });
+  const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
+  dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)spec->nT);
+  if (spec->profile == RT_PROFILE_LORENTZ)
+    k_kappa<RT_PROFILE_LORENTZ><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc_static, vec_ok, kappa, status);
+  else
+    k_kappa<RT_PROFILE_VOIGT><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc_static, vec_ok, kappa, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
 }  // namespace rt
 
 extern "C" rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *kappa,
                                     unsigned long long *evals_out, uint32_t *status, void *stream) {
   return rt::build_kappa_impl(lines, spec, kappa, evals_out, status, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_build_kappa_static(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                                           unsigned long long *evals_out, uint32_t *status,
+                                           void *stream) {
+  return rt::build_kappa_static_impl(lines, spec, kappa, evals_out, status, (cudaStream_t)stream);
 }
