@@ -179,19 +179,46 @@ __device__ __forceinline__ long long lower_bound_lo(const int4 *R, long long n, 
   return a;
 }
 
-// One profile value times its line factor at grid offset u (grid units).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Profile values times the line factor at the thread's kPtsPerThread consecutive
+// points, u0 + q grid units from the line centre.
 // Lorentz: p = {A g / (pi dnu), g^2}.  Voigt: p = {A s y / pi, y, s dnu, y^2} with
-// s = sqrt(ln2)/alpha, so that A f = p.x t S for the far-wing series.
+// s = sqrt(ln2)/alpha: every point first takes the three-term far-wing series
+// (valid for |z| >= 20); one warp vote per line decides whether any point is
+// nearer the centre, and only then do those points take faddeeva_re_near.
 template <int PROFILE>
-__device__ __forceinline__ float line_value(float u, const float4 p, const WeidCoef &wc) {
-  if (PROFILE == RT_PROFILE_LORENTZ) return __fdividef(p.x, __fmaf_rn(u, u, p.y));
-  const float x = p.z * u;
-  const float r2 = __fmaf_rn(x, x, p.w);
-  if (r2 >= 400.0f) {
-    const float t = __fdividef(1.0f, r2);
-    return p.x * (t * faddeeva_series3(t, p.w * t));
+__device__ __forceinline__ void line_values(float u0, const float4 p, const WeidCoef &wc,
+                                            float (&v)[kPtsPerThread]) {
+  if (PROFILE == RT_PROFILE_LORENTZ) {
+#pragma unroll
+    for (int q = 0; q < kPtsPerThread; ++q) {
+      const float u = u0 + (float)q;
+      v[q] = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
+    }
+    return;
   }
-  return __fdividef(p.x, p.y) * faddeeva_re_near(x, p.y, r2, wc);
+  bool near = false;
+#pragma unroll
+  for (int q = 0; q < kPtsPerThread; ++q) {
+    const float x = p.z * (u0 + (float)q);
+    const float r2 = __fmaf_rn(x, x, p.w);
+    const float t = rcp_approx(r2);
+    v[q] = p.x * (t * faddeeva_series3(t, p.w * t));
+    near |= r2 < 400.0f;
+  }
+  if (__any_sync(0xffffffffu, near)) {
+#pragma unroll
+    for (int q = 0; q < kPtsPerThread; ++q) {
+      const float x = p.z * (u0 + (float)q);
+      const float r2 = __fmaf_rn(x, x, p.w);
+      if (r2 < 400.0f) v[q] = __fdividef(p.x, p.y) * faddeeva_re_near(x, p.y, r2, wc);
+    }
+  }
 }
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
@@ -276,18 +303,15 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
       if (r.y < jw0 || r.x > jw1) continue;  // warp-uniform: no overlap with this warp
       const float4 p = sP[b][i];
       const float u0 = (float)(jt - r.z) + __int_as_float(r.w);
-      if (r.x <= jw0 && r.y >= jw1) {  // warp-uniform: the window covers the warp's points
+      float v[kPtsPerThread];
+      line_values<PROFILE>(u0, p, wc, v);
+      if (r.x > jw0 || r.y < jw1) {  // warp-uniform: the window ends inside this warp's points
 #pragma unroll
         for (int q = 0; q < kPtsPerThread; ++q)
-          kahan_add(acc[q], cmp[q], line_value<PROFILE>(u0 + (float)q, p, wc));
-      } else {
-#pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) {
-          const int j = jt + q;
-          if (j < r.x || j > r.y) continue;
-          kahan_add(acc[q], cmp[q], line_value<PROFILE>(u0 + (float)q, p, wc));
-        }
+          if (jt + q < r.x || jt + q > r.y) v[q] = 0.0f;
       }
+#pragma unroll
+      for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], v[q]);
     }
     __syncthreads();  // every thread is done with buffer b
     if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);

@@ -105,125 +105,164 @@ __device__ __forceinline__ float tmax_of(int i, int step, float h, float pos, fl
   return __fmul_rn(__fsub_rn(plane, pos), invd);
 }
 
+// State of one ray between walk steps (registers of its lane).
+struct Ray {
+  int ix, iy, iz, sx, sy, sz, cell, j, nv, row;
+  float px, py, pz, ivx, ivy, ivz, tx, ty, tz, t, tau, tc, trans, w;
+};
+
+// Philox draws -> emission cell, wavenumber, position, direction, weight; DDA set-up.
+__device__ __forceinline__ void ray_init(const WalkParams &W, const float4 *__restrict__ cells,
+                                         const float *__restrict__ tab, unsigned long long rr,
+                                         bool record, Ray &R) {
+  const unsigned long long r = W.ray_begin + rr;
+  const long long nxy = (long long)W.n[0] * W.n[1];
+  float dx, dy, dz;
+  if (W.mode == RT_SRC_BEAM) {
+    R.j = (int)(r % (unsigned long long)W.n_nu);
+    R.ix = 0; R.iy = W.n[1] / 2; R.iz = W.n[2] / 2;
+    R.px = 0.0f;
+    R.py = W.fin[1] ? __fmul_rn(__fadd_rn((float)R.iy, 0.5f), W.h[1]) : 0.0f;
+    R.pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)R.iz, 0.5f), W.h[2]) : 0.0f;
+    dx = 1.0f; dy = 0.0f; dz = 0.0f;
+    R.w = 1.0f;
+  } else {
+    u32x4 ctr{(uint32_t)r, (uint32_t)(r >> 32), 0u, W.enclosure};
+    u32x4 v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
+    const long long c = (long long)(((unsigned long long)v.x * (unsigned long long)W.ncells) >> 32);
+    R.j = (int)(((unsigned long long)v.y * (unsigned long long)W.n_nu) >> 32);
+    const float fx = u24(v.z), fy = u24(v.w);
+    ctr.z = 1u;
+    v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
+    const float fz = u24(v.x);
+    bool ok = marsaglia(v.y, v.z, dx, dy, dz);
+    for (uint32_t call = 2; !ok && call < 64u; ++call) {
+      ctr.z = call;
+      v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
+      ok = marsaglia(v.x, v.y, dx, dy, dz);
+      if (!ok) ok = marsaglia(v.z, v.w, dx, dy, dz);
+    }
+    if (!ok) { dx = 0.0f; dy = 0.0f; dz = 1.0f; }
+    R.ix = (int)(c % W.n[0]);
+    R.iy = (int)((c / W.n[0]) % W.n[1]);
+    R.iz = (int)(c / nxy);
+    R.px = W.fin[0] ? __fmul_rn(__fadd_rn((float)R.ix, fx), W.h[0]) : 0.0f;
+    R.py = W.fin[1] ? __fmul_rn(__fadd_rn((float)R.iy, fy), W.h[1]) : 0.0f;
+    R.pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)R.iz, fz), W.h[2]) : 0.0f;
+    // emission weight: 4 pi V kappa I_b(nu_j, T_c) dnu * ncells n_nu / N  (Eq. planck)
+    const float4 cd = cells[c];
+    const float kap = cell_kappa(cd, tab, W.n_nu, W.nT, R.j);
+    const float nu_m = 100.0f * fmaf((float)R.j, W.dnu, W.nu_min);
+    const float ib = W.two_hc2 * nu_m * nu_m * nu_m / expm1f(W.c2_m * nu_m / cd.z);
+    R.w = W.w_scale * kap * ib;
+  }
+  R.sx = R.sy = R.sz = 0;
+  R.ivx = R.ivy = R.ivz = 0.0f;
+  R.tx = R.ty = R.tz = INFINITY;
+  if (W.fin[0] && dx != 0.0f) { R.sx = dx > 0.0f ? 1 : -1; R.ivx = __fdiv_rn(1.0f, dx); R.tx = tmax_of(R.ix, R.sx, W.h[0], R.px, R.ivx); }
+  if (W.fin[1] && dy != 0.0f) { R.sy = dy > 0.0f ? 1 : -1; R.ivy = __fdiv_rn(1.0f, dy); R.ty = tmax_of(R.iy, R.sy, W.h[1], R.py, R.ivy); }
+  if (W.fin[2] && dz != 0.0f) { R.sz = dz > 0.0f ? 1 : -1; R.ivz = __fdiv_rn(1.0f, dz); R.tz = tmax_of(R.iz, R.sz, W.h[2], R.pz, R.ivz); }
+  R.cell = (int)(R.ix + (long long)W.n[0] * R.iy + nxy * R.iz);
+  R.row = (record && rr < (unsigned long long)W.rec_n) ? (int)rr : -1;
+  R.t = 0.0f; R.tau = 0.0f; R.tc = 0.0f; R.trans = 1.0f;
+  R.nv = 0;
+}
+
+// One visit: deposit in the current cell (Eq. I, first term), advance to the next.
+// Returns true when the ray has left the grid (or can never reach a wall).
+__device__ __forceinline__ bool ray_step(const WalkParams &W, const float4 *__restrict__ cells,
+                                         const float *__restrict__ tab, double *__restrict__ absorbed,
+                                         uint32_t *status, const RecordPtrs &rec, Ray &R) {
+  int ax;
+  float tn;
+  if (R.tx <= R.ty && R.tx <= R.tz) { ax = 0; tn = R.tx; }
+  else if (R.ty <= R.tz) { ax = 1; tn = R.ty; }
+  else { ax = 2; tn = R.tz; }
+  const float ds = __fsub_rn(tn, R.t);
+  const float kap = cell_kappa(cells[R.cell], tab, W.n_nu, W.nT, R.j);
+  const float a = kap > 0.0f ? __fmul_rn(__fmul_rn(kap, 100.0f), ds) : 0.0f;
+  const float dep = R.w * R.trans * (-expm1f(-a));
+  if (dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
+  // compensated optical depth, transmission exp(-tau)
+  if (a == INFINITY) {
+    R.tau = INFINITY;
+    R.trans = 0.0f;
+  } else {
+    const float y = __fsub_rn(a, R.tc);
+    const float s = __fadd_rn(R.tau, y);
+    R.tc = __fsub_rn(__fsub_rn(s, R.tau), y);
+    R.tau = s;
+    R.trans = expf(__fsub_rn(R.tc, R.tau));
+  }
+  if (R.row >= 0 && R.nv < W.rec_max) {
+    rec.cells[(long long)R.row * W.rec_max + R.nv] = R.cell;
+    rec.ds[(long long)R.row * W.rec_max + R.nv] = ds;
+  }
+  ++R.nv;
+  if (tn == INFINITY) return true;
+  if (W.tau_cut && R.tau > 100.0f) return true;
+  if (R.nv >= W.step_cap) { status_or(status, RT_DEV_STEPCAP); return true; }
+  R.t = tn;
+  if (ax == 0) {
+    R.ix += R.sx;
+    if (R.ix < 0 || R.ix >= W.n[0]) return true;
+    R.cell += R.sx;
+    R.tx = tmax_of(R.ix, R.sx, W.h[0], R.px, R.ivx);
+  } else if (ax == 1) {
+    R.iy += R.sy;
+    if (R.iy < 0 || R.iy >= W.n[1]) return true;
+    R.cell += R.sy * W.n[0];
+    R.ty = tmax_of(R.iy, R.sy, W.h[1], R.py, R.ivy);
+  } else {
+    R.iz += R.sz;
+    if (R.iz < 0 || R.iz >= W.n[2]) return true;
+    R.cell += R.sz * W.n[0] * W.n[1];
+    R.tz = tmax_of(R.iz, R.sz, W.h[2], R.pz, R.ivz);
+  }
+  return false;
+}
+
+// Persistent walk: each warp owns a contiguous range of rays.  Lanes step their
+// own rays; when half of the warp's lanes are idle (ballot), the idle lanes take
+// the warp's next rays together, so ray set-up and stepping stay converged.
+constexpr int kRefillIdle = 16;
+
 __global__ void __launch_bounds__(kWalkThreads)
 k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
        double *__restrict__ absorbed, double *__restrict__ scalars,
        unsigned long long *__restrict__ steps_out, uint32_t *status, RecordPtrs rec) {
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  const unsigned long long wid = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  unsigned long long next = W.n_rays * wid / nwarps;
+  const unsigned long long last = W.n_rays * (wid + 1) / nwarps;
+  const bool record = rec.cells != nullptr;
   double em = 0.0, esc = 0.0;
   unsigned long long nsteps = 0;
-  const long long nxy = (long long)W.n[0] * W.n[1];
-  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-       rr < W.n_rays; rr += stride) {
-    const unsigned long long r = W.ray_begin + rr;
-    int ix, iy, iz;
-    long long j;
-    float px, py, pz, dx, dy, dz, w;
-    if (W.mode == RT_SRC_BEAM) {
-      j = (long long)(r % (unsigned long long)W.n_nu);
-      ix = 0; iy = W.n[1] / 2; iz = W.n[2] / 2;
-      px = 0.0f;
-      py = W.fin[1] ? __fmul_rn(__fadd_rn((float)iy, 0.5f), W.h[1]) : 0.0f;
-      pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)iz, 0.5f), W.h[2]) : 0.0f;
-      dx = 1.0f; dy = 0.0f; dz = 0.0f;
-      w = 1.0f;
-    } else {
-      u32x4 ctr{(uint32_t)r, (uint32_t)(r >> 32), 0u, W.enclosure};
-      u32x4 v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
-      const long long c = (long long)(((unsigned long long)v.x * (unsigned long long)W.ncells) >> 32);
-      j = (long long)(((unsigned long long)v.y * (unsigned long long)W.n_nu) >> 32);
-      const float fx = u24(v.z), fy = u24(v.w);
-      ctr.z = 1u;
-      v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
-      const float fz = u24(v.x);
-      bool ok = marsaglia(v.y, v.z, dx, dy, dz);
-      for (uint32_t call = 2; !ok && call < 64u; ++call) {
-        ctr.z = call;
-        v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
-        ok = marsaglia(v.x, v.y, dx, dy, dz);
-        if (!ok) ok = marsaglia(v.z, v.w, dx, dy, dz);
+  Ray R;
+  bool active = false;
+  for (;;) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !active);
+    if (next < last && (idle == 0xffffffffu || __popc(idle) >= kRefillIdle)) {
+      const unsigned rank = __popc(idle & ((1u << lane) - 1u));
+      if (!active && next + rank < last) {
+        ray_init(W, cells, tab, next + rank, record, R);
+        active = true;
       }
-      if (!ok) { dx = 0.0f; dy = 0.0f; dz = 1.0f; }
-      ix = (int)(c % W.n[0]);
-      iy = (int)((c / W.n[0]) % W.n[1]);
-      iz = (int)(c / nxy);
-      px = W.fin[0] ? __fmul_rn(__fadd_rn((float)ix, fx), W.h[0]) : 0.0f;
-      py = W.fin[1] ? __fmul_rn(__fadd_rn((float)iy, fy), W.h[1]) : 0.0f;
-      pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)iz, fz), W.h[2]) : 0.0f;
-      // emission weight: 4 pi V kappa I_b(nu_j, T_c) dnu * ncells n_nu / N
-      const float4 cd = cells[c];
-      const float kap = cell_kappa(cd, tab, W.n_nu, W.nT, j);
-      const float nu_m = 100.0f * fmaf((float)j, W.dnu, W.nu_min);
-      const float ib = W.two_hc2 * nu_m * nu_m * nu_m / expm1f(W.c2_m * nu_m / cd.z);
-      w = W.w_scale * kap * ib;
+      next += __popc(idle);
     }
-    // ---- walk (binary32 geometry, no contraction)
-    int sx = 0, sy = 0, sz = 0;
-    float ivx = 0.0f, ivy = 0.0f, ivz = 0.0f;
-    float tx = INFINITY, ty = INFINITY, tz = INFINITY;
-    if (W.fin[0] && dx != 0.0f) { sx = dx > 0.0f ? 1 : -1; ivx = __fdiv_rn(1.0f, dx); tx = tmax_of(ix, sx, W.h[0], px, ivx); }
-    if (W.fin[1] && dy != 0.0f) { sy = dy > 0.0f ? 1 : -1; ivy = __fdiv_rn(1.0f, dy); ty = tmax_of(iy, sy, W.h[1], py, ivy); }
-    if (W.fin[2] && dz != 0.0f) { sz = dz > 0.0f ? 1 : -1; ivz = __fdiv_rn(1.0f, dz); tz = tmax_of(iz, sz, W.h[2], pz, ivz); }
-    long long cell = ix + (long long)W.n[0] * iy + nxy * iz;
-    const long long row = (rec.cells && rr < (unsigned long long)W.rec_n) ? (long long)rr : -1;
-    float t = 0.0f, tau = 0.0f, tc = 0.0f, trans = 1.0f;
-    int nv = 0;
-    for (;;) {
-      int ax;
-      float tn;
-      if (tx <= ty && tx <= tz) { ax = 0; tn = tx; }
-      else if (ty <= tz) { ax = 1; tn = ty; }
-      else { ax = 2; tn = tz; }
-      const float ds = __fsub_rn(tn, t);
-      const float kap = cell_kappa(cells[cell], tab, W.n_nu, W.nT, j);
-      const float a = kap > 0.0f ? __fmul_rn(__fmul_rn(kap, 100.0f), ds) : 0.0f;
-      const float dep = w * trans * (-expm1f(-a));
-      if (dep != 0.0f) atomicAdd(absorbed + cell, (double)dep);
-      // compensated optical depth, transmission exp(-tau)
-      if (a == INFINITY) {
-        tau = INFINITY;
-        trans = 0.0f;
-      } else {
-        const float y = __fsub_rn(a, tc);
-        const float s = __fadd_rn(tau, y);
-        tc = __fsub_rn(__fsub_rn(s, tau), y);
-        tau = s;
-        trans = expf(__fsub_rn(tc, tau));
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active && ray_step(W, cells, tab, absorbed, status, rec, R)) {
+      const float out = R.w * R.trans;
+      em += (double)R.w;
+      esc += (double)out;
+      nsteps += (unsigned long long)R.nv;
+      if (R.row >= 0) {
+        rec.nvis[R.row] = R.nv;
+        if (rec.weight) rec.weight[R.row] = R.w;
+        if (rec.escaped) rec.escaped[R.row] = out;
       }
-      if (row >= 0 && nv < W.rec_max) {
-        rec.cells[row * W.rec_max + nv] = (int32_t)cell;
-        rec.ds[row * W.rec_max + nv] = ds;
-      }
-      ++nv;
-      if (tn == INFINITY) break;
-      if (W.tau_cut && tau > 100.0f) break;
-      if (nv >= W.step_cap) { status_or(status, RT_DEV_STEPCAP); break; }
-      t = tn;
-      if (ax == 0) {
-        ix += sx;
-        if (ix < 0 || ix >= W.n[0]) break;
-        cell += sx;
-        tx = tmax_of(ix, sx, W.h[0], px, ivx);
-      } else if (ax == 1) {
-        iy += sy;
-        if (iy < 0 || iy >= W.n[1]) break;
-        cell += sy * (long long)W.n[0];
-        ty = tmax_of(iy, sy, W.h[1], py, ivy);
-      } else {
-        iz += sz;
-        if (iz < 0 || iz >= W.n[2]) break;
-        cell += sz * nxy;
-        tz = tmax_of(iz, sz, W.h[2], pz, ivz);
-      }
-    }
-    const float out = w * trans;
-    em += (double)w;
-    esc += (double)out;
-    nsteps += (unsigned long long)nv;
-    if (row >= 0) {
-      rec.nvis[row] = nv;
-      if (rec.weight) rec.weight[row] = w;
-      if (rec.escaped) rec.escaped[row] = out;
+      active = false;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -231,7 +270,7 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
     esc += __shfl_down_sync(0xffffffffu, esc, o);
     nsteps += __shfl_down_sync(0xffffffffu, nsteps, o);
   }
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     if (em != 0.0) atomicAdd(scalars + 0, em);
     if (esc != 0.0) atomicAdd(scalars + 2, esc);
     if (nsteps) atomicAdd(steps_out, nsteps);
@@ -297,8 +336,9 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   if (mode == RT_SRC_BEAM && !std::isfinite(grid->hx))
     return fail(RT_E_INVAL, "beam mode needs a bounded x axis");
   if (record) {
-    if (record->n_rays < 0 || (record->n_rays > 0 && (!record->cells || !record->ds ||
-                                                      !record->n_visits || record->max_visits < 1)))
+    if (record->n_rays < 0 || record->n_rays > (1LL << 31) - 1 ||
+        (record->n_rays > 0 && (!record->cells || !record->ds || !record->n_visits ||
+                                record->max_visits < 1)))
       return fail(RT_E_INVAL, "record: bad buffers");
   }
   if (n_rays == 0) return RT_OK;
@@ -361,9 +401,13 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   int dev = 0, sms = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  unsigned long long want = (n_rays + kWalkThreads - 1) / kWalkThreads;
-  const unsigned long long cap = (unsigned long long)sms * 8ull;
-  const unsigned blocks = (unsigned)(want < cap ? want : cap);
+  int per_sm = 0;
+  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk, kWalkThreads, 0));
+  if (per_sm < 1) per_sm = 1;
+  // persistent warps, each with a contiguous ray range of at least 64 rays
+  unsigned long long want = (n_rays + 64ull * (kWalkThreads / 32) - 1) / (64ull * (kWalkThreads / 32));
+  const unsigned long long cap = (unsigned long long)sms * (unsigned long long)per_sm;
+  const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
   k_walk<<<blocks, kWalkThreads, 0, st>>>(cells, kappa, W, tally->absorbed, tally->scalars,
                                           tally->steps, tally->status, rp);
   RT_CUDA_TRY(cudaGetLastError());
