@@ -253,6 +253,48 @@ rt_status rt_tally_zero(const rt_tally_buf *tally, int64_t ncells, void *stream)
 rt_status rt_tally(const rt_tally_buf *tally, int64_t ncells, double *host_absorbed,
                    double host_scalars[4], void *stream);
 
+/*
+ * Surrogate network for the kappa lookup (the learned part; the paper has no
+ * network: it stands in for Eq. tau evaluated at a cell's state).  An MLP
+ * 4 -> 128 -> 128 -> 128 -> 128 -> 1 with SiLU on the four hidden layers maps
+ * u = affine(log nu, T, p, x) in [-1, 1]^4 to y, and log kappa = out_mean +
+ * out_scale * y (kappa in cm^-1, natural log).  Parameters are one binary32
+ * device vector of RT_MLP_NPARAM values, row-major W[out][in]:
+ *   W1[128][4] b1[128] W2[128][128] b2[128] W3[128][128] b3[128]
+ *   W4[128][128] b4[128] w5[128] b5[1].
+ * The hidden 128x128 layers run on the tensor cores in BF16 with FP32
+ * accumulation; the first layer, the head and the loss are FP32.
+ */
+#define RT_MLP_NPARAM 50305
+#define RT_MLP_GRAD_ONLY 1   /* rt_mlp_train_step: gradient only, no Adam update */
+
+typedef struct {
+  float in_lo[4], in_hi[4];  /* raw input range of (log nu [ln cm^-1], T [K], p [atm], x) */
+  float out_mean, out_scale; /* log kappa = out_mean + out_scale * y */
+} rt_mlp_norm;
+
+/* log kappa for n raw inputs (device [n][4]) into out (device [n]).  Asynchronous. */
+rt_status rt_mlp_forward(const float *params, const rt_mlp_norm *norm, const float *inputs,
+                         int64_t n, float *out, uint32_t *status, void *stream);
+
+/*
+ * One training step on a batch of n samples (device inputs [n][4], targets [n] =
+ * log kappa): loss = 0.5 mean((y - (target - out_mean)/out_scale)^2), its
+ * gradient into grad (device [RT_MLP_NPARAM], overwritten), and unless
+ * flags & RT_MLP_GRAD_ONLY one Adam update (beta 0.9 / 0.999, eps 1e-8, bias
+ * corrected with `step` >= 1) of params with moments adam_m, adam_v (device
+ * [RT_MLP_NPARAM], caller-zeroed before the first step).  loss (device [1]) is
+ * overwritten.  Asynchronous.
+ */
+rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *grad,
+                            const float *inputs, const float *targets, int64_t n,
+                            const rt_mlp_norm *norm, float lr, int32_t step, int32_t flags,
+                            float *loss, uint32_t *status, void *stream);
+
+/* Self-test of the tensor-core path: D = A B^T for 128x128 FP32 row-major A, B
+ * (rounded to BF16), D FP32 row-major [128][128].  Asynchronous. */
+rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream);
+
 /* Synchronise the stream and translate a device status word into an rt_status. */
 rt_status rt_status_read(const uint32_t *status, void *stream);
 

@@ -85,7 +85,20 @@ _SIGNATURES = {
     "rt_tally_zero": ([_P, ct.c_int64, _P], ct.c_int),
     "rt_tally": ([_P, ct.c_int64, _P, _P, _P], ct.c_int),
     "rt_status_read": ([_P, _P], ct.c_int),
+    "rt_mlp_forward": ([_P, _P, _P, ct.c_int64, _P, _P, _P], ct.c_int),
+    "rt_mlp_train_step": ([_P, _P, _P, _P, _P, _P, ct.c_int64, _P, ct.c_float, ct.c_int32, ct.c_int32,
+                           _P, _P, _P], ct.c_int),
+    "rt_tc_selftest": ([_P, _P, _P, _P, _P], ct.c_int),
 }
+
+
+class rt_mlp_norm(ct.Structure):
+    _fields_ = [("in_lo", ct.c_float * 4), ("in_hi", ct.c_float * 4), ("out_mean", ct.c_float),
+                ("out_scale", ct.c_float)]
+
+
+RT_MLP_NPARAM = 50305
+RT_MLP_GRAD_ONLY = 1
 
 _lib = None
 
@@ -244,3 +257,52 @@ def trace(grid_struct, kappa, spec, tally: Tally, n_rays: int, ray_begin: int = 
                         int(enclosure), int(flags), ct.byref(tally.buf),
                         None if record is None else ct.byref(record.buf), _stream_ptr(stream))
     _check(st, "rt_trace")
+
+
+# ---------------------------------------------------------------- surrogate network
+def make_norm(in_lo, in_hi, out_mean, out_scale) -> "rt_mlp_norm":
+    n = rt_mlp_norm()
+    for i in range(4):
+        n.in_lo[i] = float(in_lo[i])
+        n.in_hi[i] = float(in_hi[i])
+    n.out_mean = float(out_mean)
+    n.out_scale = float(out_scale)
+    return n
+
+
+def mlp_forward(params, norm, inputs, out=None, stream=None):
+    """rt_mlp_forward on CUDA tensors: params [RT_MLP_NPARAM], inputs [n, 4] -> log kappa [n]."""
+    import torch
+    n = int(inputs.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=inputs.device)
+    st = lib().rt_mlp_forward(_ptr(params), ct.byref(norm), _ptr(inputs), n, _ptr(out), None,
+                              _stream_ptr(stream))
+    _check(st, "rt_mlp_forward")
+    return out
+
+
+class MlpTrainer:
+    """Parameters, Adam moments, gradient and loss buffers (CUDA tensors)."""
+
+    def __init__(self, params, norm):
+        import torch
+        self.params = params
+        self.norm = norm
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.grad = torch.zeros_like(params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
+        self.step_no = 0
+
+    def step(self, inputs, targets, lr, grad_only=False, stream=None):
+        if not grad_only:
+            self.step_no += 1
+        st = lib().rt_mlp_train_step(_ptr(self.params), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
+                                     _ptr(inputs), _ptr(targets), int(inputs.shape[0]),
+                                     ct.byref(self.norm), float(lr), max(1, self.step_no),
+                                     RT_MLP_GRAD_ONLY if grad_only else 0, _ptr(self.loss),
+                                     _ptr(self.status), _stream_ptr(stream))
+        _check(st, "rt_mlp_train_step")
+        return self.loss

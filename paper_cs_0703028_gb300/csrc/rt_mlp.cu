@@ -1,0 +1,543 @@
+// Surrogate network for kappa: (log nu, T, p, x) -> log kappa, an MLP
+// 4 -> 128 -> 128 -> 128 -> 128 -> 1 with SiLU, trained and evaluated in BF16
+// on the fifth-generation tensor cores with FP32 accumulation in tensor memory.
+//   k_mlp_prep : FP32 master weights -> BF16 tiles in the K-major core-matrix
+//                layout (W2..W4 and their transposes), ready for bulk copies.
+//   k_mlp_fwd  : per 128-row tile, layer 1 on the CUDA cores, layers 2..4 as
+//                128x128x128 tcgen05 products with a bias + SiLU epilogue read
+//                from tensor memory, linear head; for training also the
+//                pre-activations, the output gradient and the loss.
+//   k_mlp_bwd  : per 128-row tile, for each of layers 4..2 two tcgen05 products
+//                (dW = dZ^T H, dH = dZ W), SiLU derivative epilogues, bias and
+//                first-layer gradients; gradients accumulate in FP32.
+//   k_mlp_adam : Adam update of the FP32 masters (Kingma and Ba).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "rt_common.cuh"
+#include "rt_tc.cuh"
+
+namespace rt {
+namespace {
+
+constexpr int kH = 128;
+constexpr int kNParam = 50305;
+constexpr int oW1 = 0, oB1 = 512, oW2 = 640, oB2 = 17024, oW3 = 17152, oB3 = 33536, oW4 = 33664,
+              oB4 = 50048, oW5 = 50176, oB5 = 50304;
+constexpr int kTileElems = kH * kH;           // 16384 bf16 = 32 KB
+constexpr uint32_t kTileBytes = kTileElems * 2;
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+struct Norm {
+  float lo[4], hi[4], mean, scale;
+};
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sigmoid_fast(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+  const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+  return lo | (hi << 16);
+}
+
+// bf16 element (r, k) of a K-major 128x128 tile (in units of 2-byte elements)
+__device__ __forceinline__ int tile_index(int r, int k) { return (int)(tc::kmajor_offset(r, k, kH) >> 1); }
+
+__global__ void k_mlp_prep(const float *__restrict__ P, uint16_t *__restrict__ tiles) {
+  const int m = blockIdx.y;  // 0..2: W2..W4 (rows = out), 3..5: transposes (rows = in)
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kTileElems) return;
+  const int r = idx / kH, k = idx % kH;
+  const int base = (m % 3 == 0) ? oW2 : (m % 3 == 1 ? oW3 : oW4);
+  const float w = (m < 3) ? P[base + r * kH + k] : P[base + k * kH + r];
+  tiles[m * kTileElems + tile_index(r, k)] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+}
+
+__device__ __forceinline__ void normalise(const float *__restrict__ in, long long row, bool valid,
+                                          const Norm &N, float (&u)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float v = valid ? in[row * 4 + i] : N.lo[i];
+    u[i] = 2.0f * (v - N.lo[i]) / (N.hi[i] - N.lo[i]) - 1.0f;
+  }
+}
+
+struct FwdSmem {
+  uint16_t W[3][kTileElems];  // W2..W4, rows = out
+  uint16_t A[kTileElems];     // current layer input, rows = samples
+  uint64_t bar_w, bar_mma;
+  uint32_t tmem;
+  float red[4];
+};
+
+template <bool TRAIN>
+__global__ void __launch_bounds__(128)
+k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
+          const float *__restrict__ inputs, const float *__restrict__ targets, long long n,
+          float *__restrict__ Z, float *__restrict__ dy, float *__restrict__ loss,
+          float *__restrict__ out, uint32_t *status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  FwdSmem &S = *reinterpret_cast<FwdSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long row = (long long)blockIdx.x * kH + tid;
+  const bool valid = row < n;
+
+  if (tid == 0) {
+    tc::mbar_init(&S.bar_w, 1);
+    tc::mbar_init(&S.bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(&S.tmem, kH);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = S.tmem;
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&S.bar_w, 3 * kTileBytes);
+    tc::bulk_g2s(&S.W[0][0], tiles, 3 * kTileBytes, &S.bar_w);
+  }
+
+  // layer 1 on the CUDA cores
+  float u[4];
+  normalise(inputs, row, valid, N, u);
+#pragma unroll 1
+  for (int c0 = 0; c0 < kH; c0 += 8) {
+    float h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = c0 + i;
+      float z = __ldg(P + oB1 + c);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z = fmaf(__ldg(P + oW1 + c * 4 + k), u[k], z);
+      if (TRAIN && valid) Z[(0 * n + row) * kH + c] = z;
+      h[i] = z * sigmoid_fast(z);
+    }
+    uint4 pk = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                          pack_bf16x2(h[6], h[7]));
+    *reinterpret_cast<uint4 *>(&S.A[tile_index(tid, c0)]) = pk;
+  }
+  int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
+
+  float y = 0.0f;
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    if (__syncthreads_or(timeout)) break;
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc::mma_128x128x128(tmem, S.A, S.W[l]);
+      tc::mma_commit(&S.bar_mma);
+    }
+    timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)(l & 1), kWaitLimit) ? 0 : 1;
+    if (__syncthreads_or(timeout)) break;
+    tc::fence_after_sync();
+    const float *bias = P + (l == 0 ? oB2 : (l == 1 ? oB3 : oB4));
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float acc[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+#pragma unroll
+      for (int i = 0; i < 32; i += 8) {
+        float h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + i + q;
+          const float z = acc[i + q] + __ldg(bias + c);
+          if (TRAIN && valid) Z[((long long)(l + 1) * n + row) * kH + c] = z;
+          h[q] = z * sigmoid_fast(z);
+          if (l == 2) y = fmaf(__ldg(P + oW5 + c), h[q], y);
+        }
+        if (l < 2) {
+          uint4 pk = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
+                                pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
+          *reinterpret_cast<uint4 *>(&S.A[tile_index(tid, c0 + i)]) = pk;
+        }
+      }
+    }
+  }
+  if (timeout) {
+    if (tid == 0) status_or(status, RT_DEV_TIMEOUT);
+  } else {
+    y += __ldg(P + oB5);
+    if (TRAIN) {
+      const float ts = valid ? (targets[row] - N.mean) / N.scale : 0.0f;
+      const float r = valid ? (y - ts) : 0.0f;
+      if (valid) dy[row] = r / (float)n;
+      float l2 = 0.5f * r * r / (float)n;
+      for (int o = 16; o > 0; o >>= 1) l2 += __shfl_down_sync(0xffffffffu, l2, o);
+      if (lane == 0) S.red[warp] = l2;
+    } else if (valid) {
+      out[row] = N.mean + N.scale * y;
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (TRAIN && tid == 0 && !timeout) atomicAdd(loss, S.red[0] + S.red[1] + S.red[2] + S.red[3]);
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kH);
+  }
+}
+
+struct BwdSmem {
+  uint16_t Wt[kTileElems];   // current layer's transposed weights, rows = in
+  uint16_t dZ[kTileElems];   // rows = samples, k = out
+  uint16_t dZt[kTileElems];  // rows = out, k = samples
+  uint16_t Ht[kTileElems];   // rows = in, k = samples
+  float buf[kH][kH + 1];     // FP32 [sample][column] for column sums (padded: no bank conflicts)
+  float u[kH][4];
+  float dyv[kH];
+  uint64_t bar_w, bar_mma;
+  uint32_t tmem;
+};
+
+__device__ __forceinline__ void put_bf16(uint16_t *tile, int r, int k, float v) {
+  tile[tile_index(r, k)] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// column c of buf summed over the 128 samples (thread c), after a barrier
+__device__ __forceinline__ float column_sum(const BwdSmem &S, int c) {
+  float s = 0.0f;
+#pragma unroll 8
+  for (int r = 0; r < kH; ++r) s += S.buf[r][c];
+  return s;
+}
+
+__global__ void __launch_bounds__(128)
+k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
+          const float *__restrict__ inputs, long long n, const float *__restrict__ Z,
+          const float *__restrict__ dy, float *__restrict__ G, uint32_t *status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long row = (long long)blockIdx.x * kH + tid;
+  const bool valid = row < n;
+
+  if (tid == 0) {
+    tc::mbar_init(&S.bar_w, 1);
+    tc::mbar_init(&S.bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(&S.tmem, 2 * kH);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = S.tmem;
+  if (tid == 0) {  // W4^T first
+    tc::mbar_arrive_expect_tx(&S.bar_w, kTileBytes);
+    tc::bulk_g2s(S.Wt, tiles + 5 * kTileElems, kTileBytes, &S.bar_w);
+  }
+  float u[4];
+  normalise(inputs, row, valid, N, u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) S.u[tid][k] = u[k];
+  const float dyv = valid ? dy[row] : 0.0f;
+  S.dyv[tid] = dyv;
+
+  // head: dw5 = sum_s dy h4, db5 = sum_s dy
+#pragma unroll 4
+  for (int c = 0; c < kH; ++c) {
+    const float z4 = valid ? Z[(3 * n + row) * kH + c] : 0.0f;
+    S.buf[tid][c] = dyv * z4 * sigmoid_fast(z4);
+  }
+  __syncthreads();
+  atomicAdd(G + oW5 + tid, column_sum(S, tid));
+  if (tid == 0) {
+    float d5 = 0.0f;
+    for (int r = 0; r < kH; ++r) d5 += S.dyv[r];
+    atomicAdd(G + oB5, d5);
+  }
+  __syncthreads();
+  // dz4 = dy w5 silu'(z4) -> dZ, dZ^T, buf (for db4); h3 -> H^T (for dW4)
+#pragma unroll 4
+  for (int c = 0; c < kH; ++c) {
+    const float z4 = valid ? Z[(3 * n + row) * kH + c] : 0.0f;
+    const float s4 = sigmoid_fast(z4);
+    const float dz = dyv * __ldg(P + oW5 + c) * (s4 * (1.0f + z4 * (1.0f - s4)));
+    S.buf[tid][c] = dz;
+    put_bf16(S.dZ, tid, c, dz);
+    put_bf16(S.dZt, c, tid, dz);
+    const float z3 = valid ? Z[(2 * n + row) * kH + c] : 0.0f;
+    put_bf16(S.Ht, c, tid, z3 * sigmoid_fast(z3));
+  }
+  __syncthreads();
+  atomicAdd(G + oB4 + tid, column_sum(S, tid));
+
+  int timeout = 0;
+  uint32_t wphase = 0;
+#pragma unroll 1
+  for (int l = 4; l >= 2; --l) {
+    // W_l (rows = out) maps h_{l-1} -> z_l
+    if (!tc::mbar_wait(&S.bar_w, wphase, kWaitLimit)) timeout = 1;
+    wphase ^= 1u;
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    if (__syncthreads_or(timeout)) break;
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc::mma_128x128x128(tmem, S.dZt, S.Ht);        // dW_l[out][in]
+      tc::mma_128x128x128(tmem + kH, S.dZ, S.Wt);    // dH_{l-1}[sample][in]
+      tc::mma_commit(&S.bar_mma);
+    }
+    timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)((4 - l) & 1), kWaitLimit) ? 0 : 1;
+    if (__syncthreads_or(timeout)) break;
+    tc::fence_after_sync();
+    if (tid == 0 && l > 2) {  // next transposed weights into the now free buffer
+      tc::mbar_arrive_expect_tx(&S.bar_w, kTileBytes);
+      tc::bulk_g2s(S.Wt, tiles + (l == 4 ? 4 : 3) * kTileElems, kTileBytes, &S.bar_w);
+    }
+    float *gW = G + (l == 4 ? oW4 : (l == 3 ? oW3 : oW2));
+    const long long zl = (long long)(l - 2);  // block of z_{l-1}
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float acc[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) atomicAdd(gW + tid * kH + c0 + i, acc[i]);
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kH + c0), acc);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int c = c0 + i;
+        const float z = valid ? Z[(zl * n + row) * kH + c] : 0.0f;
+        const float s = sigmoid_fast(z);
+        const float dz = acc[i] * (s * (1.0f + z * (1.0f - s)));
+        S.buf[tid][c] = dz;
+        if (l > 2) {
+          put_bf16(S.dZ, tid, c, dz);
+          put_bf16(S.dZt, c, tid, dz);
+          const float zp = valid ? Z[((zl - 1) * n + row) * kH + c] : 0.0f;
+          put_bf16(S.Ht, c, tid, zp * sigmoid_fast(zp));
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    const int ob = (l == 4 ? oB3 : (l == 3 ? oB2 : oB1));
+    atomicAdd(G + ob + tid, column_sum(S, tid));
+    if (l == 2) {  // first layer: dW1[c][k] = sum_s dz1[s][c] u[s][k]
+      float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 4
+      for (int r = 0; r < kH; ++r) {
+        const float d = S.buf[r][tid];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[k] = fmaf(d, S.u[r][k], g[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) atomicAdd(G + oW1 + tid * 4 + k, g[k]);
+    }
+    __syncthreads();  // buf is rewritten by the next layer
+  }
+  if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * kH);
+  }
+}
+
+__global__ void k_mlp_adam(float *__restrict__ P, float *__restrict__ m, float *__restrict__ v,
+                           const float *__restrict__ g, float lr, float b1, float b2, float eps,
+                           float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParam) return;
+  const float gi = g[i];
+  const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+  const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+  m[i] = mi;
+  v[i] = vi;
+  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Self-test of the tensor-core path: D = A B^T for 128 x 128 x 128, A and B
+// given as FP32 row-major [128][128] (rounded to bf16).
+__global__ void __launch_bounds__(128)
+k_tc_selftest(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ D,
+              uint32_t *status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint16_t *sA = reinterpret_cast<uint16_t *>(smem_raw);
+  uint16_t *sB = sA + kTileElems;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + kTileElems);
+  uint32_t *holder = reinterpret_cast<uint32_t *>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tc::tmem_alloc(holder, kH);
+  for (int k = 0; k < kH; ++k) {
+    put_bf16(sA, tid, k, A[tid * kH + k]);
+    put_bf16(sB, tid, k, B[tid * kH + k]);
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *holder;
+  if (tid == 0) {
+    tc::mma_128x128x128(tmem, sA, sB);
+    tc::mma_commit(bar);
+  }
+  const int ok = tc::mbar_wait(bar, 0, kWaitLimit) ? 1 : 0;
+  if (__syncthreads_and(ok)) {
+    tc::fence_after_sync();
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float acc[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+      for (int i = 0; i < 32; ++i) D[tid * kH + c0 + i] = acc[i];
+    }
+  } else if (tid == 0) {
+    status_or(status, RT_DEV_TIMEOUT);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kH);
+  }
+}
+
+rt_status set_smem(const void *fn, size_t bytes) {
+  RT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return RT_OK;
+}
+
+rt_status validate_norm(const rt_mlp_norm *nm) {
+  if (!nm) return fail(RT_E_INVAL, "norm is NULL");
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(nm->in_lo[i]) || !std::isfinite(nm->in_hi[i]) || !(nm->in_hi[i] > nm->in_lo[i]))
+      return fail(RT_E_INVAL, "norm: input range %d must be finite with hi > lo", i);
+  if (!std::isfinite(nm->out_mean) || !std::isfinite(nm->out_scale) || !(nm->out_scale > 0))
+    return fail(RT_E_INVAL, "norm: out_mean, out_scale must be finite, scale > 0");
+  return RT_OK;
+}
+
+Norm to_norm(const rt_mlp_norm *nm) {
+  Norm N;
+  for (int i = 0; i < 4; ++i) {
+    N.lo[i] = nm->in_lo[i];
+    N.hi[i] = nm->in_hi[i];
+  }
+  N.mean = nm->out_mean;
+  N.scale = nm->out_scale;
+  return N;
+}
+
+}  // namespace
+
+rt_status mlp_prep_tiles(const float *params, uint16_t *tiles, cudaStream_t st) {
+  k_mlp_prep<<<dim3(kTileElems / 256, 6), 256, 0, st>>>(params, tiles);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const float *inputs,
+                         const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
+                         int32_t flags, float *loss, uint32_t *status, cudaStream_t st) {
+  if (!params || !grad || !inputs || !targets || !loss)
+    return fail(RT_E_INVAL, "rt_mlp_train_step: NULL buffer");
+  if (!(flags & RT_MLP_GRAD_ONLY) && (!m || !v)) return fail(RT_E_INVAL, "rt_mlp_train_step: NULL Adam state");
+  if (n < 1 || n > (1LL << 26)) return fail(RT_E_INVAL, "rt_mlp_train_step: n out of range");
+  if (!(flags & RT_MLP_GRAD_ONLY) && (step < 1 || !std::isfinite(lr) || lr < 0))
+    return fail(RT_E_INVAL, "rt_mlp_train_step: step >= 1 and finite lr >= 0 required");
+  rt_status s = validate_norm(nm);
+  if (s != RT_OK) return s;
+  static std::once_flag once;
+  static rt_status attr = RT_OK;
+  std::call_once(once, [] {
+    attr = set_smem((const void *)k_mlp_fwd<true>, sizeof(FwdSmem));
+    if (attr == RT_OK) attr = set_smem((const void *)k_mlp_bwd, sizeof(BwdSmem));
+  });
+  if (attr != RT_OK) return attr;
+  Scratch scr;
+  const size_t zbytes = (size_t)4 * (size_t)n * kH * sizeof(float);
+  s = scr.alloc(6 * (size_t)kTileBytes + zbytes + (size_t)n * sizeof(float), st);
+  if (s != RT_OK) return s;
+  uint16_t *tiles = scr.as<uint16_t>();
+  float *Z = reinterpret_cast<float *>(scr.as<char>() + 6 * (size_t)kTileBytes);
+  float *dy = Z + (size_t)4 * n * kH;
+  RT_CUDA_TRY(cudaMemsetAsync(grad, 0, kNParam * sizeof(float), st));
+  RT_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  s = mlp_prep_tiles(params, tiles, st);
+  if (s != RT_OK) return s;
+  const Norm N = to_norm(nm);
+  const unsigned grid = (unsigned)((n + kH - 1) / kH);
+  k_mlp_fwd<true><<<grid, kH, sizeof(FwdSmem), st>>>(params, tiles, N, inputs, targets, n, Z, dy, loss,
+                                                     nullptr, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  k_mlp_bwd<<<grid, kH, sizeof(BwdSmem), st>>>(params, tiles, N, inputs, n, Z, dy, grad, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  if (!(flags & RT_MLP_GRAD_ONLY)) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, step)), c2 = (float)(1.0 - std::pow(0.999, step));
+    k_mlp_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(params, m, v, grad, lr, b1, b2, 1e-8f, c1, c2);
+    RT_CUDA_TRY(cudaGetLastError());
+  }
+  return RT_OK;
+}
+
+rt_status mlp_forward_impl(const float *params, const rt_mlp_norm *nm, const float *inputs, int64_t n,
+                           float *out, uint32_t *status, cudaStream_t st) {
+  if (!params || !inputs || !out) return fail(RT_E_INVAL, "rt_mlp_forward: NULL buffer");
+  if (n < 0) return fail(RT_E_INVAL, "rt_mlp_forward: n < 0");
+  if (n == 0) return RT_OK;
+  rt_status s = validate_norm(nm);
+  if (s != RT_OK) return s;
+  static std::once_flag once;
+  static rt_status attr = RT_OK;
+  std::call_once(once, [] { attr = set_smem((const void *)k_mlp_fwd<false>, sizeof(FwdSmem)); });
+  if (attr != RT_OK) return attr;
+  Scratch scr;
+  s = scr.alloc(6 * (size_t)kTileBytes, st);
+  if (s != RT_OK) return s;
+  s = mlp_prep_tiles(params, scr.as<uint16_t>(), st);
+  if (s != RT_OK) return s;
+  const unsigned grid = (unsigned)((n + kH - 1) / kH);
+  k_mlp_fwd<false><<<grid, kH, sizeof(FwdSmem), st>>>(params, scr.as<uint16_t>(), to_norm(nm), inputs,
+                                                      nullptr, n, nullptr, nullptr, nullptr, out, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status tc_selftest_impl(const float *A, const float *B, float *D, uint32_t *status, cudaStream_t st) {
+  if (!A || !B || !D) return fail(RT_E_INVAL, "rt_tc_selftest: NULL buffer");
+  const size_t bytes = 2 * (size_t)kTileBytes + 64;
+  static std::once_flag once;
+  static rt_status attr = RT_OK;
+  std::call_once(once, [bytes] { attr = set_smem((const void *)k_tc_selftest, bytes); });
+  if (attr != RT_OK) return attr;
+  k_tc_selftest<<<1, kH, bytes, st>>>(A, B, D, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
+}  // namespace rt
+
+extern "C" {
+
+rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *grad,
+                            const float *inputs, const float *targets, int64_t n,
+                            const rt_mlp_norm *norm, float lr, int32_t step, int32_t flags,
+                            float *loss, uint32_t *status, void *stream) {
+  return rt::mlp_train_impl(params, adam_m, adam_v, grad, inputs, targets, n, norm, lr, step, flags,
+                            loss, status, (cudaStream_t)stream);
+}
+
+rt_status rt_mlp_forward(const float *params, const rt_mlp_norm *norm, const float *inputs,
+                         int64_t n, float *out, uint32_t *status, void *stream) {
+  return rt::mlp_forward_impl(params, norm, inputs, n, out, status, (cudaStream_t)stream);
+}
+
+rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream) {
+  return rt::tc_selftest_impl(A, B, D, status, (cudaStream_t)stream);
+}
+
+}  // extern "C"

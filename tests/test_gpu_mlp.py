@@ -1,0 +1,122 @@
+"""GPU parity of the tensor-core surrogate network against the FP64 oracle.
+
+Tolerances follow from BF16 operands (8 significant bits) with FP32
+accumulation: network outputs within 2e-2 of the output's spread, gradients
+within 3e-2 relative L2 error per tensor with cosine similarity >= 0.999.
+"""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+LO = np.array([np.log(2000.0), 600.0, 0.5, 0.01])
+HI = np.array([np.log(3000.0), 2200.0, 5.0, 0.3])
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_cs_0703028_gb300 as rt
+    rt.lib()
+    return rt
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_tensor_core_selftest(rt):
+    import torch
+    rng = np.random.default_rng(0)
+    A = rng.normal(0, 1, (128, 128)).astype(np.float32)
+    B = rng.normal(0, 1, (128, 128)).astype(np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    D = torch.zeros((128, 128), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert rt.lib().rt_tc_selftest(ct.c_void_p(dA.data_ptr()), ct.c_void_p(dB.data_ptr()),
+                                   ct.c_void_p(D.data_ptr()), ct.c_void_p(st.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = _bf16(A) @ _bf16(B).T
+    assert np.allclose(D.cpu().numpy(), ref, rtol=1e-5, atol=1e-4)
+
+
+def _inputs(n, seed):
+    rng = np.random.default_rng(seed)
+    return (LO + (HI - LO) * rng.uniform(0, 1, (n, 4))).astype(np.float32)
+
+
+def test_forward_matches_oracle(rt):
+    import torch
+    params = synth.mlp_init(0) * 2.0
+    raw = _inputs(1000, 1)   # not a multiple of 128: ragged last tile
+    norm = rt.make_norm(LO, HI, -3.0, 4.0)
+    out = rt.mlp_forward(torch.from_numpy(params).cuda(), norm, torch.from_numpy(raw).cuda())
+    U = omlp.normalise(raw.astype(np.float64), LO.astype(np.float32), HI.astype(np.float32))
+    y, _ = omlp.forward(params.astype(np.float64), U)
+    ref = -3.0 + 4.0 * y
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 2e-2 * np.std(ref) * 4 + 1e-3
+
+
+def test_gradients_match_oracle(rt):
+    import torch
+    params = synth.mlp_init(1) * 2.0
+    n = 512
+    raw = _inputs(n, 2)
+    rng = np.random.default_rng(3)
+    target = rng.normal(-3.0, 4.0, n).astype(np.float32)
+    norm = rt.make_norm(LO, HI, -3.0, 4.0)
+    tr = rt.MlpTrainer(torch.from_numpy(params).cuda(), norm)
+    tr.step(torch.from_numpy(raw).cuda(), torch.from_numpy(target).cuda(), 0.0, grad_only=True)
+    torch.cuda.synchronize()
+    assert int(tr.status.item()) == 0
+    g = tr.grad.cpu().numpy().astype(np.float64)
+    U = omlp.normalise(raw.astype(np.float64), LO.astype(np.float32), HI.astype(np.float32))
+    loss, gref = omlp.loss_and_grad(params.astype(np.float64), U, (target.astype(np.float64) + 3.0) / 4.0)
+    assert float(tr.loss.item()) == pytest.approx(loss, rel=2e-2)
+    for name, (off, shape) in synth.mlp_offsets().items():
+        k = int(np.prod(shape))
+        a, b = g[off:off + k], gref[off:off + k]
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        assert rel <= 3e-2 and cos >= 0.999, (name, rel, cos)
+
+
+def test_adam_update_matches_oracle(rt):
+    import torch
+    params = synth.mlp_init(2)
+    raw = _inputs(256, 4)
+    target = np.random.default_rng(5).normal(0, 1, 256).astype(np.float32)
+    norm = rt.make_norm(LO, HI, 0.0, 1.0)
+    p = torch.from_numpy(params).cuda()
+    tr = rt.MlpTrainer(p, norm)
+    tr.step(torch.from_numpy(raw).cuda(), torch.from_numpy(target).cuda(), 1e-3)
+    torch.cuda.synchronize()
+    g = tr.grad.cpu().numpy().astype(np.float64)
+    new, _, _ = omlp.adam_step(params.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    assert np.allclose(p.cpu().numpy(), new, rtol=0, atol=2e-6)
+
+
+def test_training_reduces_loss(rt):
+    import torch
+    n = 4096
+    raw = _inputs(n, 6)
+    U = omlp.normalise(raw.astype(np.float64), LO, HI)
+    target = (np.sin(2.5 * U[:, 0]) + U[:, 1] * U[:, 2] - 0.5 * U[:, 3] ** 2).astype(np.float32)
+    norm = rt.make_norm(LO, HI, 0.0, 1.0)
+    tr = rt.MlpTrainer(torch.from_numpy(synth.mlp_init(3)).cuda(), norm)
+    x, t = torch.from_numpy(raw).cuda(), torch.from_numpy(target).cuda()
+    first = float(tr.step(x, t, 2e-3).item())
+    for _ in range(300):
+        tr.step(x, t, 2e-3)
+    last = float(tr.step(x, t, 2e-3).item())
+    assert last < 0.05 * first, (first, last)
