@@ -291,6 +291,44 @@ rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
                             const rt_mlp_norm *norm, float lr, int32_t step, int32_t flags,
                             float *loss, uint32_t *status, void *stream);
 
+/*
+ * rt_trace_mlp -- rt_trace (RT_SRC_EMIT) with the absorption coefficient of every
+ * visited cell taken from the surrogate network at the cell's state:
+ *   kappa = exp(MLP(log nu_j, T_cell, p_cell, x_cell)) [cm^-1]
+ * (p_cell = p_ref, x_cell = x_ref where the grid has no p / x field; no table,
+ * no interpolation, no density scaling).  The rays, walk, deposits and tallies
+ * are those of rt_trace; the emission weight uses the network's kappa of the
+ * emitting cell.  Rays are processed 256 per block, the queries of all live
+ * rays evaluated together on the tensor cores at every step.
+ */
+rt_status rt_trace_mlp(const rt_grid *grid, const float *params, const rt_mlp_norm *norm,
+                       const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays,
+                       uint64_t n_rays_total, uint64_t seed, uint32_t enclosure, int32_t flags,
+                       const rt_tally_buf *tally, const rt_record *record, void *stream);
+
+/*
+ * rt_mlp_make_samples -- n training samples for the surrogate drawn from n_p
+ * line-by-line tables (device kappa[n_p][nT][n_nu] from rt_build_kappa at
+ * pressures p_nodes (device [n_p]) and the spec's T grid and x_ref).  Sample i:
+ * Philox4x32-10 counter (i, 0, 0, 0x6d6c70), key = seed, picks j, the T node, the
+ * pressure node and x uniform in [x_lo, x_hi]; inputs[i] = (log nu_j, T_k, p, x),
+ * targets[i] = log(kappa x / x_ref) (kappa is linear in the mole fraction).
+ */
+rt_status rt_mlp_make_samples(const float *tables, int32_t n_p, const float *p_nodes,
+                              const rt_spectral *spec, float x_lo, float x_hi, uint64_t seed,
+                              int64_t n, float *inputs, float *targets, void *stream);
+
+/*
+ * rt_trace_lbl -- rt_trace with the absorption coefficient of every visited cell
+ * summed line by line at the cell's own (T, p, x): Eqs. (S) and (tau) evaluated
+ * per step over the lines within the cutoff of nu_j, in binary32 with a Kahan
+ * sum (no table, no interpolation).  One warp per ray; lines as in rt_build_kappa.
+ */
+rt_status rt_trace_lbl(const rt_grid *grid, const rt_lines *lines, const rt_spectral *spec,
+                       uint64_t ray_begin, uint64_t n_rays, uint64_t n_rays_total, uint64_t seed,
+                       uint32_t enclosure, int32_t flags, const rt_tally_buf *tally,
+                       const rt_record *record, void *stream);
+
 /* Self-test of the tensor-core path: D = A B^T for 128x128 FP32 row-major A, B
  * (rounded to BF16), D FP32 row-major [128][128].  Asynchronous. */
 rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream);

@@ -89,6 +89,12 @@ _SIGNATURES = {
     "rt_mlp_train_step": ([_P, _P, _P, _P, _P, _P, ct.c_int64, _P, ct.c_float, ct.c_int32, ct.c_int32,
                            _P, _P, _P], ct.c_int),
     "rt_tc_selftest": ([_P, _P, _P, _P, _P], ct.c_int),
+    "rt_trace_mlp": ([_P, _P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
+                      ct.c_int32, _P, _P, _P], ct.c_int),
+    "rt_mlp_make_samples": ([_P, ct.c_int32, _P, _P, ct.c_float, ct.c_float, ct.c_uint64, ct.c_int64,
+                             _P, _P, _P], ct.c_int),
+    "rt_trace_lbl": ([_P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
+                      ct.c_int32, _P, _P, _P], ct.c_int),
 }
 
 
@@ -306,3 +312,43 @@ class MlpTrainer:
                                      _ptr(self.status), _stream_ptr(stream))
         _check(st, "rt_mlp_train_step")
         return self.loss
+
+
+def trace_mlp(grid_struct, params, norm, spec, tally: Tally, n_rays: int, ray_begin: int = 0,
+              n_rays_total: int | None = None, seed: int = 0, enclosure: int = 0, flags: int = 0,
+              record: Record | None = None, stream=None):
+    """Run rt_trace_mlp (asynchronous); accumulates into ``tally``."""
+    S = make_spectral(spec)
+    st = lib().rt_trace_mlp(ct.byref(grid_struct), _ptr(params), ct.byref(norm), ct.byref(S),
+                            int(ray_begin), int(n_rays),
+                            int(n_rays_total if n_rays_total is not None else n_rays), int(seed),
+                            int(enclosure), int(flags), ct.byref(tally.buf),
+                            None if record is None else ct.byref(record.buf), _stream_ptr(stream))
+    _check(st, "rt_trace_mlp")
+
+
+def trace_lbl(grid_struct, lines, spec, tally: Tally, n_rays: int, ray_begin: int = 0,
+              n_rays_total: int | None = None, seed: int = 0, enclosure: int = 0, flags: int = 0,
+              record: Record | None = None, stream=None, memory="host"):
+    """Run rt_trace_lbl (asynchronous); accumulates into ``tally``."""
+    S = make_spectral(spec)
+    L, keep = make_lines(lines, memory)
+    st = lib().rt_trace_lbl(ct.byref(grid_struct), ct.byref(L), ct.byref(S), int(ray_begin), int(n_rays),
+                            int(n_rays_total if n_rays_total is not None else n_rays), int(seed),
+                            int(enclosure), int(flags), ct.byref(tally.buf),
+                            None if record is None else ct.byref(record.buf), _stream_ptr(stream))
+    _check(st, "rt_trace_lbl")
+    return keep
+
+
+def mlp_make_samples(tables, p_nodes, spec, x_lo, x_hi, seed, n, stream=None):
+    """rt_mlp_make_samples: (inputs [n, 4], targets [n]) CUDA tensors."""
+    import torch
+    inputs = torch.empty((n, 4), dtype=torch.float32, device=tables.device)
+    targets = torch.empty(n, dtype=torch.float32, device=tables.device)
+    S = make_spectral(spec)
+    st = lib().rt_mlp_make_samples(_ptr(tables), int(p_nodes.shape[0]), _ptr(p_nodes), ct.byref(S),
+                                   float(x_lo), float(x_hi), int(seed), int(n), _ptr(inputs),
+                                   _ptr(targets), _stream_ptr(stream))
+    _check(st, "rt_mlp_make_samples")
+    return inputs, targets

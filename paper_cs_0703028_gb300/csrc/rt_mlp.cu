@@ -18,6 +18,7 @@
 
 #include "rt_common.cuh"
 #include "rt_tc.cuh"
+#include "rt_walk.cuh"
 
 namespace rt {
 namespace {
@@ -405,6 +406,209 @@ k_tc_selftest(const float *__restrict__ A, const float *__restrict__ B, float *_
   }
 }
 
+// ---------------------------------------------------------------- surrogate walk
+constexpr int kWalkMlpThreads = 256;  // two 128-ray tiles share the resident weights
+
+struct WalkMlpSmem {
+  uint16_t W[3][kTileElems];  // W2..W4 (rows = out)
+  uint16_t A[2][kTileElems];  // layer inputs of the two tiles
+  uint64_t bar_w, bar_mma;
+  unsigned long long next;
+  uint32_t tmem;
+};
+
+// Network output (log kappa) for this thread's query, all 256 threads together.
+// Returns false if a bounded tensor-core wait ran out.
+__device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__restrict__ P,
+                                               uint32_t tmem, const Norm &N, const float (&raw)[4],
+                                               uint32_t &phase, float &logk) {
+  const int tid = threadIdx.x, tile = tid >> 7, r = tid & 127, warp = tid >> 5;
+  float u[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) u[i] = 2.0f * (raw[i] - N.lo[i]) / (N.hi[i] - N.lo[i]) - 1.0f;
+#pragma unroll 1
+  for (int c0 = 0; c0 < kH; c0 += 8) {
+    float h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = c0 + i;
+      float z = __ldg(P + oB1 + c);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) z = fmaf(__ldg(P + oW1 + c * 4 + k), u[k], z);
+      h[i] = z * sigmoid_fast(z);
+    }
+    *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0)]) =
+        make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                   pack_bf16x2(h[6], h[7]));
+  }
+  float y = 0.0f;
+  int timeout = 0;
+#pragma unroll 1
+  for (int l = 0; l < 3; ++l) {
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc::mma_128x128x128(tmem, S.A[0], S.W[l]);
+      tc::mma_128x128x128(tmem + kH, S.A[1], S.W[l]);
+      tc::mma_commit(&S.bar_mma);
+    }
+    timeout = tc::mbar_wait(&S.bar_mma, phase, kWaitLimit) ? 0 : 1;
+    phase ^= 1u;
+    if (__syncthreads_or(timeout)) return false;
+    tc::fence_after_sync();
+    const float *bias = P + (l == 0 ? oB2 : (l == 1 ? oB3 : oB4));
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 32) {
+      float acc[32];
+      tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kH + c0), acc);
+#pragma unroll
+      for (int i = 0; i < 32; i += 8) {
+        float h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = c0 + i + q;
+          const float z = acc[i + q] + __ldg(bias + c);
+          h[q] = z * sigmoid_fast(z);
+          if (l == 2) y = fmaf(__ldg(P + oW5 + c), h[q], y);
+        }
+        if (l < 2)
+          *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0 + i)]) =
+              make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                         pack_bf16x2(h[6], h[7]));
+      }
+    }
+  }
+  logk = N.mean + N.scale * (y + __ldg(P + oB5));
+  return true;
+}
+
+__global__ void __launch_bounds__(kWalkMlpThreads, 1)
+k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
+           const float *__restrict__ T, const float *__restrict__ Pf, const float *__restrict__ Xf,
+           float p_ref, float x_ref, WalkParams W, double *__restrict__ absorbed,
+           double *__restrict__ scalars, unsigned long long *__restrict__ steps_out,
+           uint32_t *status, RecordPtrs rec) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  WalkMlpSmem &S = *reinterpret_cast<WalkMlpSmem *>(smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned long long begin = W.n_rays * blockIdx.x / gridDim.x;
+  const unsigned long long end = W.n_rays * (blockIdx.x + 1) / gridDim.x;
+  if (tid == 0) {
+    tc::mbar_init(&S.bar_w, 1);
+    tc::mbar_init(&S.bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    S.next = begin;
+  }
+  if (warp == 0) tc::tmem_alloc(&S.tmem, 2 * kH);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = S.tmem;
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&S.bar_w, 3 * kTileBytes);
+    tc::bulk_g2s(&S.W[0][0], tiles, 3 * kTileBytes, &S.bar_w);
+  }
+  int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
+  const bool record = rec.cells != nullptr;
+  double em = 0.0, esc = 0.0;
+  unsigned long long nsteps = 0;
+  uint32_t phase = 0;
+  Ray R;
+  bool active = false;
+  if (!__syncthreads_or(timeout)) {
+    for (;;) {
+      if (!active) {
+        const unsigned long long claim = atomicAdd(&S.next, 1ull);
+        if (claim < end) {
+          ray_init(W, nullptr, nullptr, claim, record, R);
+          active = true;
+        }
+      }
+      if (!__syncthreads_or(active)) break;
+      float raw[4] = {N.lo[0], N.lo[1], N.lo[2], N.lo[3]};
+      float Tc = 1.0f;
+      if (active) {
+        Tc = T[R.cell];
+        raw[0] = __logf(fmaf((float)R.j, W.dnu, W.nu_min));
+        raw[1] = Tc;
+        raw[2] = Pf ? Pf[R.cell] : p_ref;
+        raw[3] = Xf ? Xf[R.cell] : x_ref;
+      }
+      float logk = 0.0f;
+      if (!mlp_eval_tiles(S, P, tmem, N, raw, phase, logk)) {
+        timeout = 1;
+        break;
+      }
+      if (active) {
+        const float kap = __expf(logk);
+        if (R.w < 0.0f) R.w = emission_weight(W, R.j, Tc, kap);
+        if (ray_step(W, kap, absorbed, status, rec, R)) {
+          const float out = R.w * R.trans;
+          em += (double)R.w;
+          esc += (double)out;
+          nsteps += (unsigned long long)R.nv;
+          if (R.row >= 0) {
+            rec.nvis[R.row] = R.nv;
+            if (rec.weight) rec.weight[R.row] = R.w;
+            if (rec.escaped) rec.escaped[R.row] = out;
+          }
+          active = false;
+        }
+      }
+    }
+  }
+  if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
+  for (int o = 16; o > 0; o >>= 1) {
+    em += __shfl_down_sync(0xffffffffu, em, o);
+    esc += __shfl_down_sync(0xffffffffu, esc, o);
+    nsteps += __shfl_down_sync(0xffffffffu, nsteps, o);
+  }
+  if (lane == 0) {
+    if (em != 0.0) atomicAdd(scalars + 0, em);
+    if (esc != 0.0) atomicAdd(scalars + 2, esc);
+    if (nsteps) atomicAdd(steps_out, nsteps);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, 2 * kH);
+  }
+}
+
+// Training samples drawn from line-by-line tables kappa[kp][kT][j] (x_ref mole
+// fraction): Philox counter (i, 0, 0, 0x6d6c70) under the seed picks the
+// wavenumber, temperature node, pressure node and a mole fraction in
+// [x_lo, x_hi]; the target is log(kappa x / x_ref) (kappa is linear in x).
+__global__ void k_mlp_samples(const float *__restrict__ tables, int np, int nT, long long n_nu,
+                              const float *__restrict__ p_nodes, float T_min, float dT, float nu_min,
+                              float dnu, float x_lo, float x_hi, float x_ref, uint32_t seed_lo,
+                              uint32_t seed_hi, long long n, float *__restrict__ inputs,
+                              float *__restrict__ targets) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u32x4 v = philox4x32_10(u32x4{(uint32_t)i, (uint32_t)((unsigned long long)i >> 32), 0u, 0x6d6c70u},
+                                seed_lo, seed_hi);
+  const long long j = (long long)(((unsigned long long)v.x * (unsigned long long)n_nu) >> 32);
+  const int kT = (int)(((unsigned long long)v.y * (unsigned long long)nT) >> 32);
+  const int kp = (int)(((unsigned long long)v.z * (unsigned long long)np) >> 32);
+  const float x = x_lo + (x_hi - x_lo) * ((float)(v.w >> 8) * 0x1p-24f);
+  const float kap = tables[((long long)kp * nT + kT) * n_nu + j];
+  inputs[i * 4 + 0] = __logf(fmaf((float)j, dnu, nu_min));
+  inputs[i * 4 + 1] = fmaf((float)kT, dT, T_min);
+  inputs[i * 4 + 2] = p_nodes[kp];
+  inputs[i * 4 + 3] = x;
+  targets[i] = logf(fmaxf(kap * (x / x_ref), 1e-30f));
+}
+
+}  // namespace
+
+rt_status validate_spec(const rt_spectral *s);
+
+namespace {
+
 rt_status set_smem(const void *fn, size_t bytes) {
   RT_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   return RT_OK;
@@ -519,9 +723,77 @@ rt_status tc_selftest_impl(const float *A, const float *B, float *D, uint32_t *s
   return RT_OK;
 }
 
+rt_status trace_mlp_impl(const rt_grid *grid, const float *params, const rt_mlp_norm *nm,
+                         const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays, uint64_t n_total,
+                         uint64_t seed, uint32_t enclosure, int32_t flags, const rt_tally_buf *tally,
+                         const rt_record *record, cudaStream_t st) {
+  if (!params) return fail(RT_E_INVAL, "rt_trace_mlp: params is NULL");
+  rt_status v = validate_norm(nm);
+  if (v != RT_OK) return v;
+  WalkParams W;
+  RecordPtrs rp;
+  v = walk_setup(grid, spec, ray_begin, n_rays, n_total, seed, enclosure, flags, tally, record, &W, &rp);
+  if (v != RT_OK) return v;
+  if ((flags & 0xF) != RT_SRC_EMIT) return fail(RT_E_INVAL, "rt_trace_mlp: only RT_SRC_EMIT");
+  if (n_rays == 0) return RT_OK;
+  static std::once_flag once;
+  static rt_status attr = RT_OK;
+  std::call_once(once, [] { attr = set_smem((const void *)k_walk_mlp, sizeof(WalkMlpSmem)); });
+  if (attr != RT_OK) return attr;
+  Scratch scr;
+  v = scr.alloc(6 * (size_t)kTileBytes, st);
+  if (v != RT_OK) return v;
+  v = mlp_prep_tiles(params, scr.as<uint16_t>(), st);
+  if (v != RT_OK) return v;
+  int dev = 0, sms = 0;
+  RT_CUDA_TRY(cudaGetDevice(&dev));
+  RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned long long want = (n_rays + 2047) / 2048;
+  const unsigned blocks = (unsigned)(want < (unsigned long long)sms ? (want > 0 ? want : 1) : sms);
+  k_walk_mlp<<<blocks, kWalkMlpThreads, sizeof(WalkMlpSmem), st>>>(
+      params, scr.as<uint16_t>(), to_norm(nm), grid->T, grid->p_atm, grid->x, (float)spec->p_ref_atm,
+      (float)spec->x_ref, W, tally->absorbed, tally->scalars, tally->steps, tally->status, rp);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
+rt_status mlp_samples_impl(const float *tables, int32_t np, const float *p_nodes, const rt_spectral *spec,
+                           float x_lo, float x_hi, uint64_t seed, int64_t n, float *inputs,
+                           float *targets, cudaStream_t st) {
+  rt_status v = validate_spec(spec);
+  if (v != RT_OK) return v;
+  if (!tables || !p_nodes || !inputs || !targets || np < 1 || n < 0)
+    return fail(RT_E_INVAL, "rt_mlp_make_samples: bad arguments");
+  if (!(x_lo > 0) || !(x_hi >= x_lo)) return fail(RT_E_INVAL, "rt_mlp_make_samples: need 0 < x_lo <= x_hi");
+  if (n == 0) return RT_OK;
+  const float dT = spec->nT > 1 ? (float)((spec->T_max - spec->T_min) / (spec->nT - 1)) : 0.0f;
+  k_mlp_samples<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      tables, np, spec->nT, spec->n_nu, p_nodes, (float)spec->T_min, dT, (float)spec->nu_min,
+      (float)spec->dnu, x_lo, x_hi, (float)spec->x_ref, (uint32_t)seed, (uint32_t)(seed >> 32), n, inputs,
+      targets);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
 }  // namespace rt
 
 extern "C" {
+
+rt_status rt_trace_mlp(const rt_grid *grid, const float *params, const rt_mlp_norm *norm,
+                       const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays,
+                       uint64_t n_rays_total, uint64_t seed, uint32_t enclosure, int32_t flags,
+                       const rt_tally_buf *tally, const rt_record *record, void *stream) {
+  return rt::trace_mlp_impl(grid, params, norm, spec, ray_begin, n_rays, n_rays_total, seed, enclosure,
+                            flags, tally, record, (cudaStream_t)stream);
+}
+
+rt_status rt_mlp_make_samples(const float *tables, int32_t n_p, const float *p_nodes,
+                              const rt_spectral *spec, float x_lo, float x_hi, uint64_t seed,
+                              int64_t n, float *inputs, float *targets, void *stream) {
+  return rt::mlp_samples_impl(tables, n_p, p_nodes, spec, x_lo, x_hi, seed, n, inputs, targets,
+                              (cudaStream_t)stream);
+}
+
 
 rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *grad,
                             const float *inputs, const float *targets, int64_t n,

@@ -1,0 +1,200 @@
+// Ray state, Philox ray sampling and one walk step, shared by the table walk,
+// the on-the-fly line-by-line walk and the surrogate-network walk, so that all
+// three trace the same rays (Section 3, Fig. ray; Eq. I first term).
+#pragma once
+
+#include "rt_common.cuh"
+
+namespace rt {
+
+struct WalkParams {
+  int n[3];
+  int fin[3];
+  float h[3];
+  long long ncells, n_nu;
+  int nT, mode, tau_cut, step_cap;
+  unsigned long long ray_begin, n_rays;
+  uint32_t seed_lo, seed_hi, enclosure;
+  float nu_min, dnu;
+  float w_scale;  // 4 pi V * 100 * (100 dnu) * ncells n_nu / N   [per (cm^-1 kappa) (I_b)]
+  // Planck, wavenumber form, nu in m^-1
+  float two_hc2, c2_m;
+  // record
+  long long rec_n;
+  int rec_max;
+};
+
+struct RecordPtrs {
+  int32_t *cells;
+  float *ds;
+  int32_t *nvis;
+  float *weight, *escaped;
+};
+
+__device__ __forceinline__ float u24(uint32_t u) { return __fmul_rn(__uint2float_rn(u >> 8), 0x1p-24f); }
+
+__device__ __forceinline__ bool marsaglia(uint32_t ua, uint32_t ub, float &dx, float &dy, float &dz) {
+  const float a = __fsub_rn(__fmul_rn(2.0f, u24(ua)), 1.0f);
+  const float b = __fsub_rn(__fmul_rn(2.0f, u24(ub)), 1.0f);
+  const float s = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
+  if (s >= 1.0f || s == 0.0f) return false;
+  const float q = __fsqrt_rn(__fsub_rn(1.0f, s));
+  dx = __fmul_rn(__fmul_rn(2.0f, a), q);
+  dy = __fmul_rn(__fmul_rn(2.0f, b), q);
+  dz = __fsub_rn(1.0f, __fmul_rn(2.0f, s));
+  return true;
+}
+
+__device__ __forceinline__ float cell_kappa(const float4 cd, const float *__restrict__ tab,
+                                            long long n_nu, int nT, long long j) {
+  const int k = __float_as_int(cd.w);
+  const float v0 = __ldg(tab + (long long)k * n_nu + j);
+  if (nT < 2) return cd.y * v0;
+  const float v1 = __ldg(tab + (long long)(k + 1) * n_nu + j);
+  return cd.y * fmaf(cd.x, v1, (1.0f - cd.x) * v0);
+}
+
+__device__ __forceinline__ float tmax_of(int i, int step, float h, float pos, float invd) {
+  const float plane = __fmul_rn((float)(i + (step > 0 ? 1 : 0)), h);
+  return __fmul_rn(__fsub_rn(plane, pos), invd);
+}
+
+// Emission weight 4 pi V kappa I_b(nu_j, T) dnu * ncells n_nu / N (Eq. planck,
+// wavenumber form), kappa of the emitting cell in cm^-1.
+__device__ __forceinline__ float emission_weight(const WalkParams &W, int j, float T, float kap) {
+  const float nu_m = 100.0f * fmaf((float)j, W.dnu, W.nu_min);
+  const float ib = W.two_hc2 * nu_m * nu_m * nu_m / expm1f(W.c2_m * nu_m / T);
+  return W.w_scale * kap * ib;
+}
+
+// State of one ray between walk steps (registers of its lane).
+struct Ray {
+  int ix, iy, iz, sx, sy, sz, cell, j, nv, row;
+  float px, py, pz, ivx, ivy, ivz, tx, ty, tz, t, tau, tc, trans, w;
+};
+
+// Philox draws -> emission cell, wavenumber, position, direction, weight; DDA set-up.
+__device__ __forceinline__ void ray_init(const WalkParams &W, const float4 *__restrict__ cells,
+                                         const float *__restrict__ tab, unsigned long long rr,
+                                         bool record, Ray &R) {
+  const unsigned long long r = W.ray_begin + rr;
+  const long long nxy = (long long)W.n[0] * W.n[1];
+  float dx, dy, dz;
+  if (W.mode == RT_SRC_BEAM) {
+    R.j = (int)(r % (unsigned long long)W.n_nu);
+    R.ix = 0; R.iy = W.n[1] / 2; R.iz = W.n[2] / 2;
+    R.px = 0.0f;
+    R.py = W.fin[1] ? __fmul_rn(__fadd_rn((float)R.iy, 0.5f), W.h[1]) : 0.0f;
+    R.pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)R.iz, 0.5f), W.h[2]) : 0.0f;
+    dx = 1.0f; dy = 0.0f; dz = 0.0f;
+    R.w = 1.0f;
+  } else {
+    u32x4 ctr{(uint32_t)r, (uint32_t)(r >> 32), 0u, W.enclosure};
+    u32x4 v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
+    const long long c = (long long)(((unsigned long long)v.x * (unsigned long long)W.ncells) >> 32);
+    R.j = (int)(((unsigned long long)v.y * (unsigned long long)W.n_nu) >> 32);
+    const float fx = u24(v.z), fy = u24(v.w);
+    ctr.z = 1u;
+    v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
+    const float fz = u24(v.x);
+    bool ok = marsaglia(v.y, v.z, dx, dy, dz);
+    for (uint32_t call = 2; !ok && call < 64u; ++call) {
+      ctr.z = call;
+      v = philox4x32_10(ctr, W.seed_lo, W.seed_hi);
+      ok = marsaglia(v.x, v.y, dx, dy, dz);
+      if (!ok) ok = marsaglia(v.z, v.w, dx, dy, dz);
+    }
+    if (!ok) { dx = 0.0f; dy = 0.0f; dz = 1.0f; }
+    R.ix = (int)(c % W.n[0]);
+    R.iy = (int)((c / W.n[0]) % W.n[1]);
+    R.iz = (int)(c / nxy);
+    R.px = W.fin[0] ? __fmul_rn(__fadd_rn((float)R.ix, fx), W.h[0]) : 0.0f;
+    R.py = W.fin[1] ? __fmul_rn(__fadd_rn((float)R.iy, fy), W.h[1]) : 0.0f;
+    R.pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)R.iz, fz), W.h[2]) : 0.0f;
+    // emission weight from the table; walks without a table set it at their first step
+    if (tab) {
+      const float4 cd = cells[c];
+      R.w = emission_weight(W, R.j, cd.z, cell_kappa(cd, tab, W.n_nu, W.nT, R.j));
+    } else {
+      R.w = -1.0f;
+    }
+  }
+  R.sx = R.sy = R.sz = 0;
+  R.ivx = R.ivy = R.ivz = 0.0f;
+  R.tx = R.ty = R.tz = INFINITY;
+  if (W.fin[0] && dx != 0.0f) { R.sx = dx > 0.0f ? 1 : -1; R.ivx = __fdiv_rn(1.0f, dx); R.tx = tmax_of(R.ix, R.sx, W.h[0], R.px, R.ivx); }
+  if (W.fin[1] && dy != 0.0f) { R.sy = dy > 0.0f ? 1 : -1; R.ivy = __fdiv_rn(1.0f, dy); R.ty = tmax_of(R.iy, R.sy, W.h[1], R.py, R.ivy); }
+  if (W.fin[2] && dz != 0.0f) { R.sz = dz > 0.0f ? 1 : -1; R.ivz = __fdiv_rn(1.0f, dz); R.tz = tmax_of(R.iz, R.sz, W.h[2], R.pz, R.ivz); }
+  R.cell = (int)(R.ix + (long long)W.n[0] * R.iy + nxy * R.iz);
+  R.row = (record && rr < (unsigned long long)W.rec_n) ? (int)rr : -1;
+  R.t = 0.0f; R.tau = 0.0f; R.tc = 0.0f; R.trans = 1.0f;
+  R.nv = 0;
+}
+
+// One visit: deposit in the current cell (Eq. I, first term), advance to the next.
+// Returns true when the ray has left the grid (or can never reach a wall).
+__device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double *__restrict__ absorbed,
+                                         uint32_t *status, const RecordPtrs &rec, Ray &R,
+                                         bool writes = true) {
+  int ax;
+  float tn;
+  if (R.tx <= R.ty && R.tx <= R.tz) { ax = 0; tn = R.tx; }
+  else if (R.ty <= R.tz) { ax = 1; tn = R.ty; }
+  else { ax = 2; tn = R.tz; }
+  const float ds = __fsub_rn(tn, R.t);
+  const float a = kap > 0.0f ? __fmul_rn(__fmul_rn(kap, 100.0f), ds) : 0.0f;
+  const float dep = R.w * R.trans * (-expm1f(-a));
+  if (writes && dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
+  // compensated optical depth, transmission exp(-tau)
+  if (a == INFINITY) {
+    R.tau = INFINITY;
+    R.trans = 0.0f;
+  } else {
+    const float y = __fsub_rn(a, R.tc);
+    const float s = __fadd_rn(R.tau, y);
+    R.tc = __fsub_rn(__fsub_rn(s, R.tau), y);
+    R.tau = s;
+    R.trans = expf(__fsub_rn(R.tc, R.tau));
+  }
+  if (writes && R.row >= 0 && R.nv < W.rec_max) {
+    rec.cells[(long long)R.row * W.rec_max + R.nv] = R.cell;
+    rec.ds[(long long)R.row * W.rec_max + R.nv] = ds;
+  }
+  ++R.nv;
+  if (tn == INFINITY) return true;
+  if (W.tau_cut && R.tau > 100.0f) return true;
+  if (R.nv >= W.step_cap) {
+    if (writes) status_or(status, RT_DEV_STEPCAP);
+    return true;
+  }
+  R.t = tn;
+  if (ax == 0) {
+    R.ix += R.sx;
+    if (R.ix < 0 || R.ix >= W.n[0]) return true;
+    R.cell += R.sx;
+    R.tx = tmax_of(R.ix, R.sx, W.h[0], R.px, R.ivx);
+  } else if (ax == 1) {
+    R.iy += R.sy;
+    if (R.iy < 0 || R.iy >= W.n[1]) return true;
+    R.cell += R.sy * W.n[0];
+    R.ty = tmax_of(R.iy, R.sy, W.h[1], R.py, R.ivy);
+  } else {
+    R.iz += R.sz;
+    if (R.iz < 0 || R.iz >= W.n[2]) return true;
+    R.cell += R.sz * W.n[0] * W.n[1];
+    R.tz = tmax_of(R.iz, R.sz, W.h[2], R.pz, R.ivz);
+  }
+  return false;
+}
+
+
+// Host: validation and walk parameters common to every walk (rt_trace.cu).
+rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_begin,
+                     uint64_t n_rays, uint64_t n_total, uint64_t seed, uint32_t enclosure,
+                     int32_t flags, const rt_tally_buf *tally, const rt_record *record,
+                     WalkParams *W, RecordPtrs *rp);
+// Host: per-cell T bracket, density scale and T (float4 per cell).
+rt_status cell_prep(const rt_grid *grid, const rt_spectral *spec, float4 *cells, uint32_t *status,
+                    cudaStream_t st);
+
+}  // namespace rt

@@ -1,0 +1,59 @@
+"""Surrogate-network pipeline: line-by-line training tables, samples, training.
+
+Every numeric step runs in the library's kernels (rt_build_kappa for the
+tables, rt_mlp_make_samples for the samples, rt_mlp_train_step for forward,
+backward and Adam); this module only orders the calls and picks the learning
+rate of each step (cosine decay).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import replace
+
+import numpy as np
+
+from . import MlpTrainer, build_kappa, make_norm, mlp_make_samples
+
+
+def training_tables(lines, spec, p_nodes):
+    """kappa[kp][kT][j] (CUDA float32) from rt_build_kappa at each pressure node."""
+    import torch
+    out = torch.empty((len(p_nodes), spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    for i, p in enumerate(p_nodes):
+        build_kappa(lines, replace(spec, p_ref_atm=float(p)), out=out[i])
+    return out
+
+
+def input_ranges(spec, p_nodes, x_lo, x_hi):
+    lo = [math.log(spec.nu_min), spec.T_min, float(min(p_nodes)), x_lo]
+    hi = [math.log(spec.nu_min + (spec.n_nu - 1) * spec.dnu), spec.T_max, float(max(p_nodes)), x_hi]
+    return lo, hi
+
+
+def train_surrogate(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, n_samples=2_000_000, batch=8192,
+                    epochs=1, lr0=1e-3, lr1=1e-5, seed=0, params=None, log_every=0):
+    """Train the network on samples drawn from line-by-line tables; returns
+    (params, norm, history) with history = [(step, loss)]."""
+    import torch
+    import synth
+    p_nodes = np.asarray(p_nodes, dtype=np.float32)
+    tables = training_tables(lines, spec, p_nodes)
+    pn = torch.from_numpy(p_nodes).cuda()
+    inputs, targets = mlp_make_samples(tables, pn, spec, x_lo, x_hi, seed, n_samples)
+    del tables
+    head = targets[:65536].cpu().numpy().astype(np.float64)
+    lo, hi = input_ranges(spec, p_nodes, x_lo, x_hi)
+    norm = make_norm(lo, hi, float(head.mean()), float(head.std()))
+    if params is None:
+        params = torch.from_numpy(synth.mlp_init(seed)).cuda()
+    tr = MlpTrainer(params, norm)
+    nb = n_samples // batch
+    total = nb * epochs
+    hist = []
+    for s in range(total):
+        b = s % nb
+        lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * s / max(1, total - 1)))
+        loss = tr.step(inputs[b * batch:(b + 1) * batch], targets[b * batch:(b + 1) * batch], lr)
+        if log_every and (s % log_every == 0 or s == total - 1):
+            hist.append((s, float(loss.item())))
+    return params, norm, hist

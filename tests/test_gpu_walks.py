@@ -1,0 +1,93 @@
+"""GPU parity of the two alternative walks.
+
+* rt_trace_lbl sums the lines at each visited cell's own state.  On cells whose
+  temperatures are table nodes, at the table's pressure and mole fraction, that
+  equals the oracle's table walk: per-cell tallies within 1e-4 relative (cells
+  >= 1e-6 of the largest), as for rt_trace.
+* rt_trace_mlp with a network whose output is the constant log kappa0 must give
+  the table walk's tallies for the constant table kappa0 (no BF16 rounding is
+  involved: zero weights give exact zero activations), within 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import kappa as okappa
+from oracle import trace as otrace
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_cs_0703028_gb300 as rt
+    rt.lib()
+    return rt
+
+
+def _node_grid(seed=0, n=8):
+    rng = np.random.default_rng(seed)
+    T = (800.0 + 100.0 * rng.integers(0, 13, n ** 3)).astype(np.float32)
+    return synth.Grid(n, n, n, 1.0 / n, 1.0 / n, 1.0 / n, T, np.full(n ** 3, 1.0, np.float32),
+                      np.full(n ** 3, 0.1, np.float32))
+
+
+def _tally(rt, run, ncells):
+    t = rt.Tally(ncells)
+    t.zero()
+    run(t)
+    ab, sc, st = t.read()
+    return ab, sc, int(t.steps.item())
+
+
+def _close(ab, ref, emitted, rtol):
+    big = ref >= 1e-6 * ref.max()
+    assert np.max(np.abs(ab[big] - ref[big]) / ref[big]) <= rtol
+    assert np.all(np.abs(ab[~big] - ref[~big]) <= 1e-10 * emitted)
+
+
+@pytest.mark.parametrize("profile", ["voigt", "lorentz"])
+def test_lbl_walk_matches_oracle_on_node_temperatures(rt, profile):
+    rng = synth.rng_for(9, 40)
+    lines = synth.make_lines(300, 2000.0, 2060.0, rng)
+    spec = synth.Spectral(nu_min=2010.0, dnu=0.02, n_nu=2000, cutoff=25.0, profile=profile,
+                          nT=13, T_min=800.0, T_max=2000.0, p_ref_atm=1.0, x_ref=0.1)
+    g = _node_grid()
+    gs, keep = rt.make_grid(g)
+    n = 20000
+    ab, sc, steps = _tally(rt, lambda t: rt.trace_lbl(gs, lines, spec, t, n_rays=n, seed=4), g.ncells)
+    K = okappa.kappa_table(lines, spec)
+    o = otrace.trace(g, spec, K, seed=4, n_rays=n)
+    _close(ab, o.absorbed, o.emitted, 1e-4)
+    assert steps == o.steps
+    assert sc[0] == pytest.approx(o.emitted, rel=2e-5)
+    assert sc[3] < 1e-5
+
+
+def test_mlp_walk_with_constant_network_matches_table_walk(rt):
+    import torch
+    case = synth.config(1)
+    g = synth.gaussian_hotspot_grid(12, 1.0, 800.0, 2000.0, 0.2)
+    spec = case.spec
+    kappa0 = 0.37
+    off = synth.mlp_offsets()
+    params = np.zeros(synth.MLP_NPARAM, np.float32)
+    mean, scale = -1.0, 2.0
+    params[off["b5"][0]] = (math.log(kappa0) - mean) / scale
+    norm = rt.make_norm([math.log(2000.0), 600.0, 0.5, 0.01], [math.log(3000.0), 2200.0, 5.0, 0.3],
+                        mean, scale)
+    gs, keep = rt.make_grid(g)
+    n = 30000
+    P = torch.from_numpy(params).cuda()
+    ab_m, sc_m, st_m = _tally(rt, lambda t: rt.trace_mlp(gs, P, norm, spec, t, n_rays=n, seed=2), g.ncells)
+    tab = torch.full((spec.nT, spec.n_nu), kappa0, dtype=torch.float32, device="cuda")
+    ab_t, sc_t, st_t = _tally(rt, lambda t: rt.trace(gs, tab, spec, t, n_rays=n, seed=2), g.ncells)
+    assert st_m == st_t
+    _close(ab_m, ab_t, sc_t[0], 1e-5)
+    assert sc_m[0] == pytest.approx(sc_t[0], rel=1e-5)
+    assert sc_m[3] < 1e-5
