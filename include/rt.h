@@ -239,6 +239,52 @@ rt_status rt_trace(const rt_grid *grid, const float *kappa, const rt_spectral *s
                    uint64_t seed, uint32_t enclosure, int32_t flags,
                    const rt_tally_buf *tally, const rt_record *record, void *stream);
 
+/*
+ * Batched tracing of many independent enclosures (Section 3's walk on each), in
+ * one persistent launch.  Enclosure e (0-based) is traced exactly as
+ * rt_trace(grid_e, kappa, spec, 0, n_rays_e, n_rays_e, seed, e, flags, tally_e)
+ * would trace it (Philox counter word 3 = e), into its own tally buffers.
+ * Work is split into items of rays_per_item rays pulled by the kernel's warps
+ * from one atomic counter, so grids of uneven size share the SMs.
+ */
+typedef struct {
+  rt_grid grid;          /* the enclosure's grid and device fields */
+  uint64_t n_rays;       /* rays of its estimate */
+  rt_tally_buf tally;    /* its tallies (accumulated) */
+} rt_enclosure;
+
+typedef struct {
+  int32_t rays_per_item; /* rays per work item (0 = 4096) */
+  int32_t threads;       /* walk threads per block, multiple of 32, <= 256 (0 = 256) */
+} rt_batch_opts;
+
+typedef struct rt_batch rt_batch;  /* opaque plan */
+
+/* Plan: validates every enclosure and uploads the per-enclosure tables to device
+ * memory it allocates (synchronous).  Only RT_SRC_EMIT (optionally | RT_TAU_CUT). */
+rt_status rt_batch_create(int32_t n_encl, const rt_enclosure *encl, const rt_spectral *spec,
+                          uint64_t seed, int32_t flags, const rt_batch_opts *opts, rt_batch **out);
+/* Trace all enclosures of a plan with the table kappa: one memset and two kernel
+ * launches on the stream, no allocation and no host synchronisation. */
+rt_status rt_batch_trace(rt_batch *plan, const float *kappa, void *stream);
+/* Free a plan (after its traces have completed). */
+rt_status rt_batch_destroy(rt_batch *plan);
+/* One-shot create + trace + destroy, stream-ordered. */
+rt_status rt_trace_batch(int32_t n_encl, const rt_enclosure *encl, const float *kappa,
+                         const rt_spectral *spec, uint64_t seed, int32_t flags,
+                         const rt_batch_opts *opts, void *stream);
+
+/*
+ * Process-wide launch shapes, set by an autotuner (no effect on results):
+ * kappa_t_per_block = temperature nodes per rt_build_kappa block (1..8, 0 = 8).
+ */
+typedef struct {
+  int32_t kappa_t_per_block;
+  int32_t reserved[7];
+} rt_tuning;
+rt_status rt_set_tuning(const rt_tuning *t);
+rt_status rt_get_tuning(rt_tuning *t);
+
 /* Zero a tally buffer of ncells cells (asynchronous). */
 rt_status rt_tally_zero(const rt_tally_buf *tally, int64_t ncells, void *stream);
 

@@ -95,6 +95,12 @@ _SIGNATURES = {
                              _P, _P, _P], ct.c_int),
     "rt_trace_lbl": ([_P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
                       ct.c_int32, _P, _P, _P], ct.c_int),
+    "rt_batch_create": ([ct.c_int32, _P, _P, ct.c_uint64, ct.c_int32, _P, _P], ct.c_int),
+    "rt_batch_trace": ([_P, _P, _P], ct.c_int),
+    "rt_batch_destroy": ([_P], ct.c_int),
+    "rt_trace_batch": ([ct.c_int32, _P, _P, _P, ct.c_uint64, ct.c_int32, _P, _P], ct.c_int),
+    "rt_set_tuning": ([_P], ct.c_int),
+    "rt_get_tuning": ([_P], ct.c_int),
 }
 
 
@@ -352,3 +358,60 @@ def mlp_make_samples(tables, p_nodes, spec, x_lo, x_hi, seed, n, stream=None):
                                    _ptr(targets), _stream_ptr(stream))
     _check(st, "rt_mlp_make_samples")
     return inputs, targets
+
+
+class rt_enclosure(ct.Structure):
+    _fields_ = [("grid", rt_grid), ("n_rays", ct.c_uint64), ("tally", rt_tally_buf)]
+
+
+class rt_batch_opts(ct.Structure):
+    _fields_ = [("rays_per_item", ct.c_int32), ("threads", ct.c_int32)]
+
+
+class rt_tuning(ct.Structure):
+    _fields_ = [("kappa_t_per_block", ct.c_int32), ("reserved", ct.c_int32 * 7)]
+
+
+def set_tuning(kappa_t_per_block: int = 0):
+    t = rt_tuning()
+    t.kappa_t_per_block = int(kappa_t_per_block)
+    _check(lib().rt_set_tuning(ct.byref(t)), "rt_set_tuning")
+
+
+class Batch:
+    """A plan over many enclosures: grids (synth.Grid-like), ray counts, one Tally each."""
+
+    def __init__(self, grids, n_rays, spec, seed=0, flags=0, rays_per_item=0, threads=0):
+        self.grids = [make_grid(g) for g in grids]
+        self.tallies = [Tally(g.ncells) for g in grids]
+        for t in self.tallies:
+            t.zero()
+        arr = (rt_enclosure * len(grids))()
+        for i, ((gs, _), t, n) in enumerate(zip(self.grids, self.tallies, n_rays)):
+            arr[i].grid = gs
+            arr[i].n_rays = int(n)
+            arr[i].tally = t.buf
+        self.encl = arr
+        self.spec = make_spectral(spec)
+        self.opts = rt_batch_opts(int(rays_per_item), int(threads))
+        self.plan = ct.c_void_p()
+        _check(lib().rt_batch_create(len(grids), arr, ct.byref(self.spec), int(seed), int(flags),
+                                     ct.byref(self.opts), ct.byref(self.plan)), "rt_batch_create")
+
+    def trace(self, kappa, stream=None):
+        _check(lib().rt_batch_trace(self.plan, _ptr(kappa), _stream_ptr(stream)), "rt_batch_trace")
+
+    def zero(self, stream=None):
+        for t in self.tallies:
+            t.zero(stream)
+
+    def close(self):
+        if self.plan:
+            lib().rt_batch_destroy(self.plan)
+            self.plan = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,98 @@
+"""Autotuner for launch shapes (no effect on results, only on speed).
+
+Each tuner times its candidates on the caller's actual workload with CUDA
+events (after one warm-up launch each), keeps the fastest, and caches the
+choice in a JSON file keyed by a signature of the workload's sizes
+(``$RT_GB300_TUNE_CACHE`` or ``~/.cache/paper_cs_0703028_gb300/tune.json``).
+
+* ``tune_kappa``: temperature nodes per rt_build_kappa block (1, 2, 4, 8).
+* ``tune_batch``: rays per work item and threads per block of the batched walk.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import Batch, build_kappa, set_tuning
+
+
+def _cache_path():
+    p = os.environ.get("RT_GB300_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_cs_0703028_gb300", "tune.json")
+
+
+def _load():
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key, value):
+    data = _load()
+    data[key] = value
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def _time(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_kappa(lines, spec, candidates=(1, 2, 4, 8), reps=3, use_cache=True):
+    """Pick the temperature nodes per block of rt_build_kappa; returns (best, {tpb: ms})."""
+    import torch
+    key = f"kappa:{spec.profile}:{lines.n}:{spec.n_nu}:{spec.nT}:{spec.dnu}:{spec.cutoff}"
+    if use_cache and key in _load():
+        best = int(_load()[key]["best"])
+        set_tuning(best)
+        return best, _load()[key]["ms"]
+    out = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    times = {}
+    for c in candidates:
+        set_tuning(c)
+        times[int(c)] = _time(lambda: build_kappa(lines, spec, out=out), reps)
+    best = min(times, key=times.get)
+    set_tuning(best)
+    _store(key, {"best": best, "ms": times})
+    return best, times
+
+
+def tune_batch(grids, n_rays, spec, kappa, candidates=None, reps=2, use_cache=True, seed=0):
+    """Pick (rays_per_item, threads) of the batched walk; returns (best, {str: ms})."""
+    if candidates is None:
+        candidates = [(r, t) for r in (1024, 4096, 16384) for t in (128, 256)]
+    sig = sum(g.nx * g.ny * g.nz for g in grids)
+    key = f"batch:{len(grids)}:{sig}:{int(sum(n_rays))}:{spec.n_nu}:{spec.nT}"
+    if use_cache and key in _load():
+        b = _load()[key]["best"]
+        return (int(b[0]), int(b[1])), _load()[key]["ms"]
+    times = {}
+    for rpi, th in candidates:
+        B = Batch(grids, n_rays, spec, seed=seed, rays_per_item=rpi, threads=th)
+        times[f"{rpi},{th}"] = _time(lambda: B.trace(kappa), reps)
+        B.close()
+    best = min(times, key=times.get)
+    rpi, th = (int(v) for v in best.split(","))
+    _store(key, {"best": [rpi, th], "ms": times})
+    return (rpi, th), times

@@ -20,10 +20,10 @@
 namespace rt {
 namespace {
 
-constexpr int kTileThreads = 256;
 constexpr int kPtsPerThread = 4;
-constexpr int kTilePts = kTileThreads * kPtsPerThread;  // 1024 wavenumbers per block
-constexpr int kChunk = 512;                              // lines per staged chunk
+constexpr int kTilePts = 32 * kPtsPerThread;  // 128 wavenumbers per block, one warp per T node
+constexpr int kMaxTPerBlock = 8;              // warps (T nodes) per block
+constexpr int kChunk = 128;                   // lines per staged chunk
 constexpr unsigned kWaitLimit = 1u << 22;                // bounded mbarrier waits
 
 // CODATA 2018 (SI); derived quantities are formed on the host in binary64.
@@ -132,7 +132,10 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
     const float alpha = nu0f * sqrtf(Tk.hi) * Q.doppler;  // Doppler HWHM, cm^-1
     const float s = 0.83255461f / alpha;                  // sqrt(ln 2) / alpha
     const float y = s * gam;
-    out = make_float4(A * s * (float)(1.0 / kPi) * y, y, s * Q.dnu, y * y);
+    const float sd = s * Q.dnu;
+    // half-width (grid units) of the region |z| < 20 where the far-wing series does not hold
+    const float u_near = sqrtf(fmaxf(400.0f - y * y, 0.0f)) / sd;
+    out = make_float4(A * s * (float)(1.0 / kPi) * y, sd, y * y, u_near);
   }
   Pout[(long long)k * Q.n_lines + l] = out;
 }
@@ -185,42 +188,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// Profile values times the line factor at the thread's kPtsPerThread consecutive
-// points, u0 + q grid units from the line centre.
-// Lorentz: p = {A g / (pi dnu), g^2}.  Voigt: p = {A s y / pi, y, s dnu, y^2} with
-// s = sqrt(ln2)/alpha: every point first takes the three-term far-wing series
-// (valid for |z| >= 20); one warp vote per line decides whether any point is
-// nearer the centre, and only then do those points take faddeeva_re_near.
-template <int PROFILE>
-__device__ __forceinline__ void line_values(float u0, const float4 p, const WeidCoef &wc,
-                                            float (&v)[kPtsPerThread]) {
-  if (PROFILE == RT_PROFILE_LORENTZ) {
-#pragma unroll
-    for (int q = 0; q < kPtsPerThread; ++q) {
-      const float u = u0 + (float)q;
-      v[q] = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
-    }
-    return;
-  }
-  bool near = false;
-#pragma unroll
-  for (int q = 0; q < kPtsPerThread; ++q) {
-    const float x = p.z * (u0 + (float)q);
-    const float r2 = __fmaf_rn(x, x, p.w);
-    const float t = rcp_approx(r2);
-    v[q] = p.x * (t * faddeeva_series3(t, p.w * t));
-    near |= r2 < 400.0f;
-  }
-  if (__any_sync(0xffffffffu, near)) {
-#pragma unroll
-    for (int q = 0; q < kPtsPerThread; ++q) {
-      const float x = p.z * (u0 + (float)q);
-      const float r2 = __fmaf_rn(x, x, p.w);
-      if (r2 < 400.0f) v[q] = __fdividef(p.x, p.y) * faddeeva_re_near(x, p.y, r2, wc);
-    }
-  }
-}
-
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   const float y = __fsub_rn(v, c);
   const float t = __fadd_rn(s, y);
@@ -228,28 +195,37 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
+// Block = 128 consecutive wavenumbers x up to 8 temperature nodes (one warp per
+// node, 4 consecutive points per lane).  All warps walk the same lines: the
+// block's lines are staged chunk by chunk (geometry R once, prefactors P per
+// node) with bulk asynchronous copies on an mbarrier, double buffered.
+// Far wing (|z| >= 20): with t = 1/|z|^2 the three-term series is the
+// polynomial 1 + 1.5 t + (3.75 - 2y^2) t^2 - 15 y^2 t^3 + 12 y^4 t^4 (times y t);
+// a warp-uniform interval test per line sends near-centre points to
+// faddeeva_re_near.  Lorentz: p = {A g / (pi dnu), g^2}.
 template <int PROFILE>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(32 * kMaxTPerBlock)
 k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_lines,
-        long long n_nu, WeidCoef wc, int vec_ok, float *__restrict__ kappa, uint32_t *status) {
-  __shared__ __align__(16) float4 sP[2][kChunk];
+        long long n_nu, int nT, WeidCoef wc, int vec_ok, float *__restrict__ kappa, uint32_t *status) {
   __shared__ __align__(16) int4 sR[2][kChunk];
+  __shared__ __align__(16) float4 sP[2][kMaxTPerBlock][kChunk];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ long long s_lb, s_ub;
-  __shared__ int s_abort;
 
-  const int k = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tpb = blockDim.x >> 5;
+  const int k0 = blockIdx.y * tpb;
+  const int nk = min(tpb, nT - k0);          // T nodes of this block
+  const int k = k0 + min(warp, nk - 1);      // surplus warps shadow the last node, store nothing
   const long long j0 = (long long)blockIdx.x * kTilePts;
   const long long jend = min(j0 + (long long)kTilePts, n_nu);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int jw0 = (int)(j0 + warp * 32 * kPtsPerThread);
-  const int jw1 = jw0 + 32 * kPtsPerThread - 1;
+  const int jw0 = (int)j0, jw1 = jw0 + kTilePts - 1;
   const int jt = jw0 + lane * kPtsPerThread;
+  const float off_t = (float)(lane * kPtsPerThread);
 
   if (threadIdx.x == 0) {
-    s_lb = lower_bound_hi(R, n_lines, (int)j0);
+    s_lb = lower_bound_hi(R, n_lines, jw0);
     s_ub = max(s_lb, lower_bound_lo(R, n_lines, (int)jend));
-    s_abort = 0;
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -257,26 +233,25 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
   __syncthreads();
   const long long lb = s_lb, ub = s_ub;
   const int nchunks = (int)((ub - lb + kChunk - 1) / kChunk);
-  const float4 *Pk = P + (long long)k * n_lines;
 
   auto issue = [&](int c) {
     const long long l0 = lb + (long long)c * kChunk;
     const uint32_t cnt = (uint32_t)min((long long)kChunk, ub - l0);
     const int b = c & 1;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bars[b], cnt * 32u);
-    bulk_g2s(&sP[b][0], Pk + l0, cnt * 16u, &bars[b]);
+    mbar_arrive_expect_tx(&bars[b], cnt * 16u * (uint32_t)(nk + 1));
     bulk_g2s(&sR[b][0], R + l0, cnt * 16u, &bars[b]);
+    for (int w = 0; w < nk; ++w) bulk_g2s(&sP[b][w][0], P + (long long)(k0 + w) * n_lines + l0, cnt * 16u, &bars[b]);
   };
 
   float acc[kPtsPerThread], cmp[kPtsPerThread];
 #pragma unroll
   for (int q = 0; q < kPtsPerThread; ++q) acc[q] = cmp[q] = 0.0f;
-
   if (threadIdx.x == 0) {
     if (nchunks > 0) issue(0);
     if (nchunks > 1) issue(1);
   }
+  bool aborted = false;
   for (int c = 0; c < nchunks; ++c) {
     const int b = c & 1;
     const uint32_t parity = (uint32_t)((c >> 1) & 1);
@@ -289,23 +264,48 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
       }
     }
     if (__syncthreads_or(timed_out)) {  // the block leaves together
-      if (threadIdx.x == 0) {
-        s_abort = 1;
-        status_or(status, RT_DEV_TIMEOUT);
-      }
+      if (threadIdx.x == 0) status_or(status, RT_DEV_TIMEOUT);
+      aborted = true;
       break;
     }
     const long long l0 = lb + (long long)c * kChunk;
     const int cnt = (int)min((long long)kChunk, ub - l0);
+    const int wsel = min(warp, nk - 1);
 #pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
       const int4 r = sR[b][i];
-      if (r.y < jw0 || r.x > jw1) continue;  // warp-uniform: no overlap with this warp
-      const float4 p = sP[b][i];
-      const float u0 = (float)(jt - r.z) + __int_as_float(r.w);
+      const float4 p = sP[b][wsel][i];
+      const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);  // grid offset of the warp's first point
       float v[kPtsPerThread];
-      line_values<PROFILE>(u0, p, wc, v);
-      if (r.x > jw0 || r.y < jw1) {  // warp-uniform: the window ends inside this warp's points
+      if (PROFILE == RT_PROFILE_LORENTZ) {
+        const float u = fu + off_t;
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) {
+          const float uq = u + (float)q;
+          v[q] = p.x * rcp_approx(__fmaf_rn(uq, uq, p.y));
+        }
+      } else {
+        const float y2 = p.z;
+        const float a2 = __fmaf_rn(-2.0f, y2, 3.75f), a3 = -15.0f * y2, a4 = 12.0f * y2 * y2;
+        const float xt = p.y * (fu + off_t);
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) {
+          const float x = __fmaf_rn(p.y, (float)q, xt);
+          const float t = rcp_approx(__fmaf_rn(x, x, y2));
+          const float S = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, a4, a3), a2), 1.5f), 1.0f);
+          v[q] = p.x * (t * S);
+        }
+        if (fu < p.w + 1.0f && fu + (float)kTilePts > -p.w - 1.0f) {  // warp-uniform
+          const float y = sqrtf(y2);
+#pragma unroll
+          for (int q = 0; q < kPtsPerThread; ++q) {
+            const float x = __fmaf_rn(p.y, (float)q, xt);
+            const float r2 = __fmaf_rn(x, x, y2);
+            if (r2 < 400.0f) v[q] = __fdividef(p.x, y) * faddeeva_re_near(x, y, r2, wc);
+          }
+        }
+      }
+      if (r.x > jw0 || r.y < jw1) {  // warp-uniform: the window ends inside this block's points
 #pragma unroll
         for (int q = 0; q < kPtsPerThread; ++q)
           if (jt + q < r.x || jt + q > r.y) v[q] = 0.0f;
@@ -313,11 +313,10 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
 #pragma unroll
       for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], v[q]);
     }
-    __syncthreads();  // every thread is done with buffer b
+    __syncthreads();  // every warp is done with buffer b
     if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
   }
-  __syncthreads();
-  if (s_abort) return;
+  if (aborted || warp >= nk) return;
 
   float *row = kappa + (long long)k * n_nu;
   float out[kPtsPerThread];
@@ -330,6 +329,26 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
     for (int q = 0; q < kPtsPerThread; ++q)
       if ((long long)jt + q < jend) row[jt + q] = out[q];
   }
+}
+
+int g_kappa_tpb = kMaxTPerBlock;
+
+rt_status launch_kappa(const float4 *P, const int4 *R, long long n, const rt_spectral *spec,
+                       float *kappa, uint32_t *status, cudaStream_t st) {
+  static WeidCoef wc;
+  static std::once_flag wc_once;
+  std::call_once(wc_once, [] { weideman_coefficients(&wc); });
+  const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
+  int want = g_kappa_tpb;
+  if (want < 1 || want > kMaxTPerBlock) want = kMaxTPerBlock;
+  const int tpb = spec->nT < want ? spec->nT : want;
+  dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)((spec->nT + tpb - 1) / tpb));
+  if (spec->profile == RT_PROFILE_LORENTZ)
+    k_kappa<RT_PROFILE_LORENTZ><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok, kappa, status);
+  else
+    k_kappa<RT_PROFILE_VOIGT><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok, kappa, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
 }
 
 }  // namespace
@@ -372,6 +391,16 @@ rt_status validate_host_lines(const rt_lines *L, const rt_spectral *s) {
 }
 
 }  // namespace
+
+rt_status launch_line_geometry(const double *nu0, const double *S, const double *g, const double *E,
+                               long long n, const rt_spectral *spec, int check, int4 *R,
+                               unsigned long long *evals, uint32_t *status, cudaStream_t st) {
+  if (n <= 0) return RT_OK;
+  GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT, check};
+  k_line_geometry<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nu0, S, g, E, G, R, evals, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
 
 rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float *kappa,
                            unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
@@ -448,17 +477,7 @@ rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float
   k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P);
   RT_CUDA_TRY(cudaGetLastError());
 
-  static WeidCoef wc;
-  static std::once_flag wc_once;
-  std::call_once(wc_once, [] { weideman_coefficients(&wc); });
-  const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
-  dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)spec->nT);
-  if (spec->profile == RT_PROFILE_LORENTZ)
-    k_kappa<RT_PROFILE_LORENTZ><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc, vec_ok, kappa, status);
-  else
-    k_kappa<RT_PROFILE_VOIGT><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc, vec_ok, kappa, status);
-  RT_CUDA_TRY(cudaGetLastError());
-  return RT_OK;
+  return launch_kappa(P, R, n, spec, kappa, status, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -563,17 +582,7 @@ rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec
   dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
   k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P);
   RT_CUDA_TRY(cudaGetLastError());
-  static WeidCoef wc_static;
-  static std::once_flag wc_static_once;
-  std::call_once(wc_static_once, [] { weideman_coefficients(&wc_static); });
-  const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
-  dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)spec->nT);
-  if (spec->profile == RT_PROFILE_LORENTZ)
-    k_kappa<RT_PROFILE_LORENTZ><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc_static, vec_ok, kappa, status);
-  else
-    k_kappa<RT_PROFILE_VOIGT><<<gk, kTileThreads, 0, st>>>(P, R, n, spec->n_nu, wc_static, vec_ok, kappa, status);
-  RT_CUDA_TRY(cudaGetLastError());
-  return RT_OK;
+  return launch_kappa(P, R, n, spec, kappa, status, st);
 }
 
 }  // namespace rt
@@ -587,4 +596,19 @@ extern "C" rt_status rt_build_kappa_static(const rt_lines *lines, const rt_spect
                                            unsigned long long *evals_out, uint32_t *status,
                                            void *stream) {
   return rt::build_kappa_static_impl(lines, spec, kappa, evals_out, status, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_set_tuning(const rt_tuning *t) {
+  if (!t) return rt::fail(RT_E_INVAL, "rt_set_tuning: NULL");
+  if (t->kappa_t_per_block < 0 || t->kappa_t_per_block > 8)
+    return rt::fail(RT_E_INVAL, "rt_set_tuning: kappa_t_per_block must be in [0, 8]");
+  rt::g_kappa_tpb = t->kappa_t_per_block == 0 ? 8 : t->kappa_t_per_block;
+  return RT_OK;
+}
+
+extern "C" rt_status rt_get_tuning(rt_tuning *t) {
+  if (!t) return rt::fail(RT_E_INVAL, "rt_get_tuning: NULL");
+  *t = rt_tuning{};
+  t->kappa_t_per_block = rt::g_kappa_tpb;
+  return RT_OK;
 }

@@ -21,37 +21,12 @@ namespace {
 constexpr int kWalkThreads = 256;
 constexpr int kReduceBlocks = 256;
 
-struct CellParams {
-  long long ncells;
-  float Tmin, dT, den, pref, xref;
-  int nT, has_px;
-};
-
 __global__ void k_cell_prep(const float *__restrict__ T, const float *__restrict__ p,
                             const float *__restrict__ x, CellParams C, float4 *__restrict__ out,
                             uint32_t *status) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C.ncells) return;
-  const float Tc = T[c];
-  int k = 0;
-  float frac = 0.0f;
-  if (!(Tc > 0.0f) || !isfinite(Tc)) status_or(status, RT_DEV_NONFINITE);
-  if (C.nT >= 2) {
-    const float u = __fdiv_rn(__fsub_rn(Tc, C.Tmin), C.dT);
-    float fl = floorf(u);
-    fl = fminf(fmaxf(fl, 0.0f), (float)(C.nT - 2));
-    k = (int)fl;
-    frac = fminf(fmaxf(__fsub_rn(u, fl), 0.0f), 1.0f);
-  }
-  float sc = 1.0f;
-  if (C.has_px) {
-    const float pc = p ? p[c] : C.pref;
-    const float xc = x ? x[c] : C.xref;
-    if (!(pc > 0.0f) || !isfinite(pc) || !(xc > 0.0f) || !isfinite(xc))
-      status_or(status, RT_DEV_NONFINITE);
-    sc = __fdiv_rn(__fmul_rn(pc, xc), C.den);
-  }
-  out[c] = make_float4(frac, sc, Tc, __int_as_float(k));
+  out[c] = cell_prep_one(T, p, x, c, C, status);
 }
 
 // Persistent walk: each warp owns a contiguous range of rays.  Lanes step their
@@ -212,18 +187,23 @@ rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_
   return RT_OK;
 }
 
-rt_status cell_prep(const rt_grid *grid, const rt_spectral *spec, float4 *cells, uint32_t *status,
-                    cudaStream_t st) {
-  const long long nc = (long long)grid->nx * grid->ny * grid->nz;
+CellParams cell_params(const rt_spectral *spec, long long ncells, int has_px) {
   CellParams C;
-  C.ncells = nc;
+  C.ncells = ncells;
   C.Tmin = (float)spec->T_min;
   C.dT = spec->nT >= 2 ? (float)((spec->T_max - spec->T_min) / (double)(spec->nT - 1)) : 1.0f;
   C.den = (float)(spec->p_ref_atm * spec->x_ref);
   C.pref = (float)spec->p_ref_atm;
   C.xref = (float)spec->x_ref;
   C.nT = spec->nT;
-  C.has_px = (grid->p_atm || grid->x) ? 1 : 0;
+  C.has_px = has_px;
+  return C;
+}
+
+rt_status cell_prep(const rt_grid *grid, const rt_spectral *spec, float4 *cells, uint32_t *status,
+                    cudaStream_t st) {
+  const long long nc = (long long)grid->nx * grid->ny * grid->nz;
+  const CellParams C = cell_params(spec, nc, (grid->p_atm || grid->x) ? 1 : 0);
   k_cell_prep<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(grid->T, grid->p_atm, grid->x, C, cells,
                                                            status);
   RT_CUDA_TRY(cudaGetLastError());

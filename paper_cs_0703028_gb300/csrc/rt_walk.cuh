@@ -7,6 +7,40 @@
 
 namespace rt {
 
+struct CellParams {
+  long long ncells;
+  float Tmin, dT, den, pref, xref;
+  int nT, has_px;
+};
+
+// Cell c's temperature bracket in the table (binary32: u = (T - T_min) / dT,
+// k = clamp(floor u, 0, nT - 2), frac = clamp(u - k, 0, 1)), density scale
+// (p x) / (p_ref x_ref) and T, packed as {frac, scale, T, k bits}.
+__device__ __forceinline__ float4 cell_prep_one(const float *__restrict__ T, const float *__restrict__ p,
+                                                const float *__restrict__ x, long long c,
+                                                const CellParams &C, uint32_t *status) {
+  const float Tc = T[c];
+  int k = 0;
+  float frac = 0.0f;
+  if (!(Tc > 0.0f) || !isfinite(Tc)) status_or(status, RT_DEV_NONFINITE);
+  if (C.nT >= 2) {
+    const float u = __fdiv_rn(__fsub_rn(Tc, C.Tmin), C.dT);
+    float fl = floorf(u);
+    fl = fminf(fmaxf(fl, 0.0f), (float)(C.nT - 2));
+    k = (int)fl;
+    frac = fminf(fmaxf(__fsub_rn(u, fl), 0.0f), 1.0f);
+  }
+  float sc = 1.0f;
+  if (C.has_px) {
+    const float pc = p ? p[c] : C.pref;
+    const float xc = x ? x[c] : C.xref;
+    if (!(pc > 0.0f) || !isfinite(pc) || !(xc > 0.0f) || !isfinite(xc))
+      status_or(status, RT_DEV_NONFINITE);
+    sc = __fdiv_rn(__fmul_rn(pc, xc), C.den);
+  }
+  return make_float4(frac, sc, Tc, __int_as_float(k));
+}
+
 struct WalkParams {
   int n[3];
   int fin[3];
@@ -193,6 +227,8 @@ rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_
                      uint64_t n_rays, uint64_t n_total, uint64_t seed, uint32_t enclosure,
                      int32_t flags, const rt_tally_buf *tally, const rt_record *record,
                      WalkParams *W, RecordPtrs *rp);
+// Host: the CellParams of a spectral spec (table T grid, reference state).
+CellParams cell_params(const rt_spectral *spec, long long ncells, int has_px);
 // Host: per-cell T bracket, density scale and T (float4 per cell).
 rt_status cell_prep(const rt_grid *grid, const rt_spectral *spec, float4 *cells, uint32_t *status,
                     cudaStream_t st);
