@@ -73,6 +73,7 @@ def lib():
             L.oracle_emission_indices.restype = None
             L.oracle_walk_rays.argtypes = [P, P, P, ct.c_int64, P, P, P, P, P, P, P]
             L.oracle_cell_prep.argtypes = [P, P, P, P, P]
+            L.oracle_march.argtypes = [P, P, P, ct.c_int64, P, P, P, P, P]
             _lib = L
     return _lib
 
@@ -243,3 +244,20 @@ def trace_case(case, ray_begin=0, n_rays=None, n_record=0, tau_cut=False, thread
     res.columns = cols
     res.kappa = K
     return res
+
+
+def march(grid, spec, kappa, pos, dirs, I_in=None, columns=None):
+    """Eq. (I) marched per spectral sample along given rays (start position inside
+    the grid, direction).  Returns (I_out (n, n_nu), power (n,) = sum_j (I_in - I_out) dnu)."""
+    I = _Inputs(grid, spec, kappa, columns)
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float32)
+    n = int(pos.shape[0])
+    Iin = None if I_in is None else np.ascontiguousarray(I_in, dtype=np.float64)
+    out = np.zeros((n, spec.n_nu), dtype=np.float64)
+    pw = np.zeros(n, dtype=np.float64)
+    e = lib().oracle_march(ct.byref(I.g), ct.byref(I.s), ct.byref(I.t), n, _p(pos), _p(dirs), _p(Iin),
+                           _p(out), _p(pw))
+    if e != 0:
+        raise RuntimeError(f"oracle_march failed with code {e}")
+    return out, pw

@@ -57,3 +57,17 @@ def train_surrogate(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, n_samples=2_000_0
         if log_every and (s % log_every == 0 or s == total - 1):
             hist.append((s, float(loss.item())))
     return params, norm, hist
+
+
+def save(path, params, norm):
+    """Store parameters and normalisation (numpy .npz)."""
+    np.savez(path, params=params.detach().cpu().numpy(), in_lo=np.array(norm.in_lo[:]),
+             in_hi=np.array(norm.in_hi[:]), out=np.array([norm.out_mean, norm.out_scale]))
+
+
+def load(path):
+    """Parameters (CUDA tensor) and normalisation stored by save()."""
+    import torch
+    d = np.load(path)
+    return (torch.from_numpy(d["params"].astype(np.float32)).cuda(),
+            make_norm(d["in_lo"], d["in_hi"], float(d["out"][0]), float(d["out"][1])))
