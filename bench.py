@@ -374,6 +374,142 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _ev_time(fn, reps=1):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_surrogate(args):
+    """Table walk vs surrogate-network walk vs on-the-fly line-by-line walk on the
+    64^3 learned-part workload (same rays), after training the network."""
+    import torch
+    import paper_cs_0703028_gb300 as rt
+    from paper_cs_0703028_gb300 import surrogate
+    case = synth.config(2)
+    spec = case.spec
+    ex = case.extra
+    p_nodes = np.exp(np.linspace(np.log(ex["train_p"][0]), np.log(ex["train_p"][1]), ex["train_p"][2]))
+    t0 = time.time()
+    params, norm, hist = surrogate.train_surrogate(case.lines, spec, p_nodes, ex["train_x"][0],
+                                                   ex["train_x"][1], n_samples=args.samples,
+                                                   batch=8192, epochs=args.epochs, log_every=500)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    g = case.grid
+    gs, keep = rt.make_grid(g)
+    kap = rt.build_kappa(case.lines, spec)
+    n = args.rays
+    out = {}
+    runs = {"table": (lambda t: rt.trace(gs, kap, spec, t, n_rays=n, n_rays_total=n)),
+            "mlp": (lambda t: rt.trace_mlp(gs, params, norm, spec, t, n_rays=n, n_rays_total=n)),
+            "lbl": (lambda t: rt.trace_lbl(gs, case.lines, spec, t, n_rays=n // 50, n_rays_total=n))}
+    tallies = {}
+    for name, fn in runs.items():
+        t = rt.Tally(g.ncells)
+        t.zero()
+        fn(t)
+        t.zero()
+        ms = _ev_time(lambda: fn(t))
+        ab, sc, _ = t.read()
+        steps = int(t.steps.item())
+        tallies[name] = ab
+        out[name] = {"ray_cell_steps_per_s": steps / (ms * 1e-3), "ms": ms, "steps": steps,
+                     "energy_residual": float(sc[3])}
+    ref = tallies["table"]
+    big = ref >= 1e-3 * ref.max()
+    err = np.abs(tallies["mlp"][big] - ref[big]) / ref[big]
+    res = {"metric": "ray-cell steps/s, surrogate walk vs on-the-fly line-by-line walk",
+           "value": out["mlp"]["ray_cell_steps_per_s"], "unit": "ray-cell steps/s",
+           "higher_is_better": True, "config": {"workload": "box64 learned part, 20k Voigt lines, "
+                                                           f"{n} rays (line-by-line walk: {n // 50})"},
+           "walks": out, "speedup_vs_lbl": out["mlp"]["ray_cell_steps_per_s"] / out["lbl"]["ray_cell_steps_per_s"],
+           "tally_error_vs_table": {"median": float(np.median(err)), "p90": float(np.percentile(err, 90)),
+                                    "max": float(err.max()), "cells": int(big.sum()),
+                                    "total": float(tallies["mlp"].sum() / ref.sum() - 1.0)},
+           "training": {"seconds": train_s, "samples": args.samples, "epochs": args.epochs,
+                        "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
+    print(json.dumps(res), flush=True)
+
+
+def run_batched(args):
+    """256 enclosures in one persistent (graph-replayed) launch vs 256 rt_trace calls."""
+    import torch
+    import paper_cs_0703028_gb300 as rt
+    from paper_cs_0703028_gb300 import autotune
+    case = synth.config(3)
+    encl = case.extra["enclosures"]
+    scale = args.rays_scale
+    grids = [g for g, _ in encl]
+    rays = [max(1, int(r * scale)) for _, r in encl]
+    kap = rt.build_kappa(case.lines, case.spec)
+    (rpi, th), tune_ms = autotune.tune_batch(grids, rays, case.spec, kap, reps=1)
+    B = rt.Batch(grids, rays, case.spec, rays_per_item=rpi, threads=th)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    gph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gph, stream=s):
+        B.zero(stream=s)
+        B.trace(kap, stream=s)
+    gph.replay()
+    ms_graph = _ev_time(gph.replay, reps=args.steps)
+    steps = sum(int(t.steps.item()) for t in B.tallies)
+    singles = [(rt.make_grid(g), rt.Tally(g.ncells)) for g in grids]
+
+    def separate():
+        for e, ((gs, _), t) in enumerate(singles):
+            t.zero()
+            rt.trace(gs, kap, case.spec, t, n_rays=rays[e], n_rays_total=rays[e], enclosure=e)
+    separate()
+    ms_sep = _ev_time(separate, reps=args.steps)
+    res = {"metric": "ray-cell steps/s, 256 enclosures", "value": steps / (ms_graph * 1e-3),
+           "unit": "ray-cell steps/s", "higher_is_better": True,
+           "config": {"workload": f"batched256: sides 8..48, {sum(rays)} rays ({scale:g} x 1e3 per cell)",
+                      "cells": int(sum(g.ncells for g in grids))},
+           "graph_ms": ms_graph, "separate_launches_ms": ms_sep, "speedup": ms_sep / ms_graph,
+           "steps": steps, "autotuned": {"rays_per_item": rpi, "threads": th, "candidates_ms": tune_ms}}
+    B.close()
+    print(json.dumps(res), flush=True)
+
+
+def run_box128(args):
+    """The 128^3 workload: 100k lines, 64 T x 400k nu table, and the walk."""
+    import torch
+    import paper_cs_0703028_gb300 as rt
+    case = synth.config(4)
+    spec = case.spec
+    n = int(case.n_rays * args.rays_scale)
+    gs, keep = rt.make_grid(case.grid)
+    kap = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    evals = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rt.build_kappa(case.lines, spec, out=kap, evals=evals)
+    torch.cuda.synchronize()
+    ev = int(evals.item())
+    ms_build = _ev_time(lambda: rt.build_kappa(case.lines, spec, out=kap), reps=args.steps)
+    t = rt.Tally(case.grid.ncells)
+    t.zero()
+    rt.trace(gs, kap, spec, t, n_rays=min(n, 10_000_000), n_rays_total=n)
+    t.zero()
+    ms_trace = _ev_time(lambda: rt.trace(gs, kap, spec, t, n_rays=n, n_rays_total=n))
+    ab, sc, _ = t.read()
+    steps = int(t.steps.item())
+    hbm = _peaks().get("hbm_gbs", 6771.5)
+    res = {"metric": "ray-cell steps/s + line-profile evals/s", "value": steps / (ms_trace * 1e-3),
+           "unit": "ray-cell steps/s", "higher_is_better": True,
+           "config": {"workload": f"box128_voigt100k: 128^3 cells, 100k Voigt lines, 64 T x 400k nu, {n} rays"},
+           "build_ms": ms_build, "evals": ev, "line_profile_evals_per_s": ev / (ms_build * 1e-3),
+           "trace_ms": ms_trace, "steps": steps, "energy_residual": float(sc[3]),
+           "walk_hbm_frac_at_16B_per_step": steps * 16 / (ms_trace * 1e-3) / (hbm * 1e9)}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -382,7 +518,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="box32", choices=["box32", "surrogate", "batched", "box128"])
+    ap.add_argument("--samples", type=int, default=20_000_000)
+    ap.add_argument("--epochs", type=int, default=1)
+    ap.add_argument("--rays", type=int, default=5_000_000)
+    ap.add_argument("--rays-scale", type=float, default=1.0)
     args = ap.parse_args()
+    if args.workload == "surrogate":
+        return run_surrogate(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "box128":
+        return run_box128(args)
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":

@@ -52,12 +52,15 @@ __global__ void k_cell_prep_batch(const EnclDev *__restrict__ E, const long long
 
 constexpr int kRefillIdleBatch = 16;
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_off, int n_encl,
              long long n_items, int rays_per_item, const float4 *__restrict__ cells_all,
              const float *__restrict__ tab, unsigned long long *__restrict__ counter) {
-  const int lane = threadIdx.x & 31;
+  // the current item's walk parameters, one slot per warp (read like the constant bank)
+  __shared__ __align__(16) WalkParams s_w[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const RecordPtrs rec{nullptr, nullptr, nullptr, nullptr, nullptr};
+  const WalkParams &W = s_w[warp];
   for (;;) {
     unsigned long long it = 0;
     if (lane == 0) it = atomicAdd(counter, 1ull);
@@ -65,7 +68,12 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
     if ((long long)it >= n_items) break;
     const int e = find_segment(item_off, n_encl, (long long)it);
     const EnclDev &D = E[e];
-    const WalkParams W = D.W;
+    {
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(&D.W);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&s_w[warp]);
+      for (int w = lane; w < (int)(sizeof(WalkParams) / 4); w += 32) dst[w] = src[w];
+      __syncwarp();
+    }
     const float4 *cells = cells_all + D.cell_off;
     unsigned long long next = ((long long)it - D.item_off) * (unsigned long long)rays_per_item;
     const unsigned long long last = min(next + (unsigned long long)rays_per_item, W.n_rays);
@@ -84,7 +92,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
         next += __popc(idle);
       }
       if (!__any_sync(0xffffffffu, active)) break;
-      if (active && ray_step(W, cell_kappa(cells[R.cell], tab, W.n_nu, W.nT, R.j), D.absorbed, D.status,
+      if (active && ray_step(W, cell_kappa_t(cells[R.cell], tab, W.nT, R.j), D.absorbed, D.status,
                              rec, R)) {
         em += (double)R.w;
         esc += (double)(R.w * R.trans);
@@ -102,6 +110,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
       if (esc != 0.0) atomicAdd(D.scalars + 2, esc);
       if (nsteps) atomicAdd(D.steps, nsteps);
     }
+    __syncwarp();  // the slot is rewritten by the next item
   }
 }
 
@@ -118,6 +127,9 @@ struct rt_batch {
   long long *d_item_off = nullptr, *d_cell_off = nullptr;
   unsigned long long *d_counter = nullptr;
   float4 *d_cells = nullptr;
+  float *d_tabt = nullptr;  // wavenumber-major copy of the table
+  int nT = 0;
+  long long n_nu = 0;
   void *mem = nullptr;
   cudaStream_t alloc_stream = nullptr;
   bool async_alloc = false;
@@ -149,6 +161,7 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
       snprintf(msg, sizeof(msg), "%s", rt_last_error());
       return fail(v, "enclosure %d: %s", e, msg);
     }
+    H[e].W.nu_major = 1;
     H[e].T = encl[e].grid.T;
     H[e].p = encl[e].grid.p_atm;
     H[e].x = encl[e].grid.x;
@@ -171,7 +184,8 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
   const size_t o_cell = (o_item + 8 * ((size_t)n_encl + 1) + 255) & ~size_t(255);
   const size_t o_cnt = (o_cell + 8 * ((size_t)n_encl + 1) + 255) & ~size_t(255);
   const size_t o_cells = o_cnt + 256;
-  const size_t total = o_cells + sizeof(float4) * (size_t)cells;
+  const size_t o_tabt = (o_cells + sizeof(float4) * (size_t)cells + 255) & ~size_t(255);
+  const size_t total = o_tabt + sizeof(float) * (size_t)spec->nT * (size_t)spec->n_nu;
   rt_batch *B = new rt_batch();
   cudaError_t ce = async ? cudaMallocAsync(&B->mem, total, st) : cudaMalloc(&B->mem, total);
   if (ce != cudaSuccess) {
@@ -186,6 +200,9 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
   B->d_cell_off = (long long *)(base + o_cell);
   B->d_counter = (unsigned long long *)(base + o_cnt);
   B->d_cells = (float4 *)(base + o_cells);
+  B->d_tabt = (float *)(base + o_tabt);
+  B->nT = spec->nT;
+  B->n_nu = spec->n_nu;
   B->n_encl = n_encl;
   B->n_items = items;
   B->total_cells = cells;
@@ -214,14 +231,17 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
 
 static rt_status batch_run(rt_batch *B, const float *kappa, cudaStream_t st) {
   if (!B || !kappa) return fail(RT_E_INVAL, "rt_batch_trace: NULL plan or kappa");
+  rt_status v = RT_OK;
   RT_CUDA_TRY(cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned long long), st));
   if (B->total_cells > 0) {
     k_cell_prep_batch<<<(unsigned)((B->total_cells + 255) / 256), 256, 0, st>>>(
         B->d_encl, B->d_cell_off, B->n_encl, B->total_cells, B->C, B->d_cells);
     RT_CUDA_TRY(cudaGetLastError());
   }
+  v = launch_transpose(kappa, B->nT, B->n_nu, B->d_tabt, st);
+  if (v != RT_OK) return v;
   k_walk_batch<<<B->blocks, B->threads, 0, st>>>(B->d_encl, B->d_item_off, B->n_encl, B->n_items,
-                                                 B->rays_per_item, B->d_cells, kappa, B->d_counter);
+                                                 B->rays_per_item, B->d_cells, B->d_tabt, B->d_counter);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }

@@ -211,6 +211,9 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
   __shared__ __align__(16) float4 sP[2][kMaxTPerBlock][kChunk];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ long long s_lb, s_ub;
+  __shared__ float s_qx[kMaxTPerBlock][kTilePts];           // near-centre queue: x
+  __shared__ unsigned char s_qs[kMaxTPerBlock][kTilePts];   // near-centre queue: owner slot
+  __shared__ float s_res[kMaxTPerBlock][kTilePts];          // near-centre values by slot
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tpb = blockDim.x >> 5;
@@ -271,47 +274,93 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
     const long long l0 = lb + (long long)c * kChunk;
     const int cnt = (int)min((long long)kChunk, ub - l0);
     const int wsel = min(warp, nk - 1);
-#pragma unroll 1
-    for (int i = 0; i < cnt; ++i) {
-      const int4 r = sR[b][i];
-      const float4 p = sP[b][wsel][i];
-      const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);  // grid offset of the warp's first point
-      float v[kPtsPerThread];
-      if (PROFILE == RT_PROFILE_LORENTZ) {
-        const float u = fu + off_t;
+    // lines enter the compensated sum in pairs: the sum of two positive line
+    // values is rounded once (relative error <= 2^-24 of the pair)
+    auto line_vals = [&](int i, float (&v)[kPtsPerThread]) {
+        const int4 r = sR[b][i];
+        const float4 p = sP[b][wsel][i];
+        const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);  // grid offset of the warp's first point
+        if (PROFILE == RT_PROFILE_LORENTZ) {
+          const float u = fu + off_t;
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) {
-          const float uq = u + (float)q;
-          v[q] = p.x * rcp_approx(__fmaf_rn(uq, uq, p.y));
-        }
-      } else {
-        const float y2 = p.z;
-        const float a2 = __fmaf_rn(-2.0f, y2, 3.75f), a3 = -15.0f * y2, a4 = 12.0f * y2 * y2;
-        const float xt = p.y * (fu + off_t);
-#pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) {
-          const float x = __fmaf_rn(p.y, (float)q, xt);
-          const float t = rcp_approx(__fmaf_rn(x, x, y2));
-          const float S = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, a4, a3), a2), 1.5f), 1.0f);
-          v[q] = p.x * (t * S);
-        }
-        if (fu < p.w + 1.0f && fu + (float)kTilePts > -p.w - 1.0f) {  // warp-uniform
-          const float y = sqrtf(y2);
+          for (int q = 0; q < kPtsPerThread; ++q) {
+            const float uq = u + (float)q;
+            v[q] = p.x * rcp_approx(__fmaf_rn(uq, uq, p.y));
+          }
+        } else {
+          const float y2 = p.z;
+          const float a2 = __fmaf_rn(-2.0f, y2, 3.75f), a3 = -15.0f * y2, a4 = 12.0f * y2 * y2;
+          const float xt = p.y * (fu + off_t);
 #pragma unroll
           for (int q = 0; q < kPtsPerThread; ++q) {
             const float x = __fmaf_rn(p.y, (float)q, xt);
-            const float r2 = __fmaf_rn(x, x, y2);
-            if (r2 < 400.0f) v[q] = __fdividef(p.x, y) * faddeeva_re_near(x, y, r2, wc);
+            const float t = rcp_approx(__fmaf_rn(x, x, y2));
+            const float S = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, a4, a3), a2), 1.5f), 1.0f);
+            v[q] = p.x * (t * S);
+          }
+          if (fu < p.w + 1.0f && fu + (float)kTilePts > -p.w - 1.0f) {  // warp-uniform
+            // compact this warp's near-centre points so one pass of the lanes evaluates them
+            float xs[kPtsPerThread];
+            unsigned nearbits = 0;
+#pragma unroll
+            for (int q = 0; q < kPtsPerThread; ++q) {
+              xs[q] = __fmaf_rn(p.y, (float)q, xt);
+              nearbits |= (__fmaf_rn(xs[q], xs[q], y2) < 400.0f ? 1u : 0u) << q;
+            }
+            const int cnt = __popc(nearbits);
+            int pre = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int t = __shfl_up_sync(0xffffffffu, pre, o);
+              if (lane >= o) pre += t;
+            }
+            const int total = __shfl_sync(0xffffffffu, pre, 31);
+            if (total > 0) {
+              float *qx = s_qx[warp];
+              unsigned char *qs = s_qs[warp];
+              float *res = s_res[warp];
+              int pos = pre - cnt;
+#pragma unroll
+              for (int q = 0; q < kPtsPerThread; ++q)
+                if ((nearbits >> q) & 1u) {
+                  qx[pos] = xs[q];
+                  qs[pos] = (unsigned char)(lane * kPtsPerThread + q);
+                  ++pos;
+                }
+              __syncwarp();
+              const float y = sqrtf(y2);
+              const float coef = __fdividef(p.x, y);
+              for (int e = lane; e < total; e += 32) {
+                const float xe = qx[e];
+                res[qs[e]] = coef * faddeeva_re_near(xe, y, __fmaf_rn(xe, xe, y2), wc);
+              }
+              __syncwarp();
+#pragma unroll
+              for (int q = 0; q < kPtsPerThread; ++q)
+                if ((nearbits >> q) & 1u) v[q] = res[lane * kPtsPerThread + q];
+              __syncwarp();
+            }
           }
         }
-      }
-      if (r.x > jw0 || r.y < jw1) {  // warp-uniform: the window ends inside this block's points
+        if (r.x > jw0 || r.y < jw1) {  // warp-uniform: the window ends inside this block's points
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q)
-          if (jt + q < r.x || jt + q > r.y) v[q] = 0.0f;
-      }
+          for (int q = 0; q < kPtsPerThread; ++q)
+            if (jt + q < r.x || jt + q > r.y) v[q] = 0.0f;
+        }
+    };
+#pragma unroll 1
+    for (int i = 0; i + 1 < cnt; i += 2) {
+      float va[kPtsPerThread], vb[kPtsPerThread];
+      line_vals(i, va);
+      line_vals(i + 1, vb);
 #pragma unroll
-      for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], v[q]);
+      for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], __fadd_rn(va[q], vb[q]));
+    }
+    if (cnt & 1) {
+      float va[kPtsPerThread];
+      line_vals(cnt - 1, va);
+#pragma unroll
+      for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], va[q]);
     }
     __syncthreads();  // every warp is done with buffer b
     if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);

@@ -34,7 +34,25 @@ __global__ void k_cell_prep(const float *__restrict__ T, const float *__restrict
 // the warp's next rays together, so ray set-up and stepping stay converged.
 constexpr int kRefillIdle = 16;
 
-__global__ void __launch_bounds__(kWalkThreads)
+// [nT][n_nu] -> [n_nu][nT] through 32 x 33 shared tiles
+__global__ void k_transpose(const float *__restrict__ in, int rows, long long cols, float *__restrict__ out) {
+  __shared__ float t[32][33];
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i;
+    const long long c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long long c = c0 + i;
+    const int r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[c * rows + r] = t[threadIdx.x][i];
+  }
+}
+
+__global__ void __launch_bounds__(kWalkThreads, 5)
 k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
        double *__restrict__ absorbed, double *__restrict__ scalars,
        unsigned long long *__restrict__ steps_out, uint32_t *status, RecordPtrs rec) {
@@ -59,8 +77,7 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
       next += __popc(idle);
     }
     if (!__any_sync(0xffffffffu, active)) break;
-    if (active && ray_step(W, cell_kappa(cells[R.cell], tab, W.n_nu, W.nT, R.j), absorbed, status,
-                           rec, R)) {
+    if (active && ray_step(W, cell_kappa_t(cells[R.cell], tab, W.nT, R.j), absorbed, status, rec, R)) {
       const float out = R.w * R.trans;
       em += (double)R.w;
       esc += (double)out;
@@ -168,6 +185,7 @@ rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_
   W->seed_lo = (uint32_t)seed;
   W->seed_hi = (uint32_t)(seed >> 32);
   W->enclosure = enclosure;
+  W->nu_major = 0;
   W->nu_min = (float)spec->nu_min;
   W->dnu = (float)spec->dnu;
   const double pi = 3.14159265358979323846;
@@ -184,6 +202,13 @@ rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_
     W->rec_n = record->n_rays;
     W->rec_max = record->max_visits;
   }
+  return RT_OK;
+}
+
+rt_status launch_transpose(const float *tab, int nT, long long n_nu, float *tabt, cudaStream_t st) {
+  dim3 tg((unsigned)((n_nu + 31) / 32), (unsigned)((nT + 31) / 32));
+  k_transpose<<<tg, dim3(32, 8), 0, st>>>(tab, nT, n_nu, tabt);
+  RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
 
@@ -222,11 +247,16 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   if (v != RT_OK) return v;
   if (n_rays == 0) return RT_OK;
   Scratch scr;
-  v = scr.alloc((size_t)W.ncells * sizeof(float4), st);
+  const size_t cbytes = ((size_t)W.ncells * sizeof(float4) + 255) & ~size_t(255);
+  v = scr.alloc(cbytes + (size_t)spec->nT * (size_t)spec->n_nu * sizeof(float), st);
   if (v != RT_OK) return v;
   float4 *cells = scr.as<float4>();
+  float *tabt = reinterpret_cast<float *>(scr.as<char>() + cbytes);
   v = cell_prep(grid, spec, cells, tally->status, st);
   if (v != RT_OK) return v;
+  v = launch_transpose(kappa, spec->nT, spec->n_nu, tabt, st);
+  if (v != RT_OK) return v;
+  W.nu_major = 1;
   int dev = 0, sms = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -237,7 +267,7 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   unsigned long long want = (n_rays + 64ull * (kWalkThreads / 32) - 1) / (64ull * (kWalkThreads / 32));
   const unsigned long long cap = (unsigned long long)sms * (unsigned long long)per_sm;
   const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-  k_walk<<<blocks, kWalkThreads, 0, st>>>(cells, kappa, W, tally->absorbed, tally->scalars,
+  k_walk<<<blocks, kWalkThreads, 0, st>>>(cells, tabt, W, tally->absorbed, tally->scalars,
                                           tally->steps, tally->status, rp);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;

@@ -47,6 +47,7 @@ struct WalkParams {
   float h[3];
   long long ncells, n_nu;
   int nT, mode, tau_cut, step_cap;
+  int nu_major;  // the walk's table is the wavenumber-major copy
   unsigned long long ray_begin, n_rays;
   uint32_t seed_lo, seed_hi, enclosure;
   float nu_min, dnu;
@@ -79,12 +80,25 @@ __device__ __forceinline__ bool marsaglia(uint32_t ua, uint32_t ub, float &dx, f
   return true;
 }
 
+// kappa of a cell from the table, linear in T between its bracketing nodes, times
+// the density scale.  T-major table: tab[k * n_nu + j].
 __device__ __forceinline__ float cell_kappa(const float4 cd, const float *__restrict__ tab,
                                             long long n_nu, int nT, long long j) {
   const int k = __float_as_int(cd.w);
   const float v0 = __ldg(tab + (long long)k * n_nu + j);
   if (nT < 2) return cd.y * v0;
   const float v1 = __ldg(tab + (long long)(k + 1) * n_nu + j);
+  return cd.y * fmaf(cd.x, v1, (1.0f - cd.x) * v0);
+}
+
+// The same from a wavenumber-major copy tabt[j * nT + k]: both nodes share a cache line.
+__device__ __forceinline__ float cell_kappa_t(const float4 cd, const float *__restrict__ tabt, int nT,
+                                              long long j) {
+  const int k = __float_as_int(cd.w);
+  const float *c = tabt + j * (long long)nT + k;
+  const float v0 = __ldg(c);
+  if (nT < 2) return cd.y * v0;
+  const float v1 = __ldg(c + 1);
   return cd.y * fmaf(cd.x, v1, (1.0f - cd.x) * v0);
 }
 
@@ -148,7 +162,8 @@ __device__ __forceinline__ void ray_init(const WalkParams &W, const float4 *__re
     // emission weight from the table; walks without a table set it at their first step
     if (tab) {
       const float4 cd = cells[c];
-      R.w = emission_weight(W, R.j, cd.z, cell_kappa(cd, tab, W.n_nu, W.nT, R.j));
+      const float ke = W.nu_major ? cell_kappa_t(cd, tab, W.nT, R.j) : cell_kappa(cd, tab, W.n_nu, W.nT, R.j);
+      R.w = emission_weight(W, R.j, cd.z, ke);
     } else {
       R.w = -1.0f;
     }
@@ -227,6 +242,8 @@ rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_
                      uint64_t n_rays, uint64_t n_total, uint64_t seed, uint32_t enclosure,
                      int32_t flags, const rt_tally_buf *tally, const rt_record *record,
                      WalkParams *W, RecordPtrs *rp);
+// Host: wavenumber-major copy tabt[j * nT + k] of a T-major table.
+rt_status launch_transpose(const float *tab, int nT, long long n_nu, float *tabt, cudaStream_t st);
 // Host: the CellParams of a spectral spec (table T grid, reference state).
 CellParams cell_params(const rt_spectral *spec, long long ncells, int has_px);
 // Host: per-cell T bracket, density scale and T (float4 per cell).
