@@ -105,6 +105,12 @@ typedef struct {
   double T_min, T_max;     /* K, 0 < T_min <= T_max (T_min < T_max when nT > 1) */
   double p_ref_atm;        /* pressure of the table, atm, > 0 */
   double x_ref;            /* absorber mole fraction of the table, > 0 */
+  int32_t points_per_line; /* > 0: each line contributes at this many grid points around
+                              its centre, j = jf - n/2 + 1 .. jf + n/2 with jf = floor((nu0 -
+                              nu_min)/dnu) (Section 3: 16 contributions per line), instead of
+                              the cutoff window; 0: cutoff window */
+  int32_t accumulate;      /* rt_build_kappa: 1 adds into kappa (one call per absorbing gas of
+                              a mixture, Eq. tau's sum over g), 0 overwrites it */
 } rt_spectral;
 
 /*
@@ -284,6 +290,25 @@ typedef struct {
 } rt_tuning;
 rt_status rt_set_tuning(const rt_tuning *t);
 rt_status rt_get_tuning(rt_tuning *t);
+
+/*
+ * rt_march -- the paper's spectrally resolved kernel (Section 3, Eq. I and the
+ * (I_in - I_out) reduction): for each of n_paths rays, starting at pos (device
+ * [n_paths][3], m, inside the grid) with direction dir (device [n_paths][3]),
+ * and each spectral sample nu_j, the intensity I_in(nu_j) (device [n_nu], W m^-2
+ * sr^-1 (m^-1)^-1, NULL = 0) crosses the ray's cells (the binary32 walk of
+ * rt_trace) as
+ *   I <- I exp(-kappa l) + I_b(nu_j, T_cell) (1 - exp(-kappa l))
+ * with kappa the cell's table value (as in rt_trace) and I_b Eq. (planck).
+ *   I_out   optional device [n_paths][n_nu]: the intensity leaving the grid.
+ *   power   device [n_paths] (binary64, overwritten): sum_j (I_in - I_out) dnu [m^-1],
+ *           W m^-2 sr^-1 lost by the beam along the path.
+ *   status  optional device status word (RT_DEV_NONFINITE, RT_DEV_STEPCAP).
+ * n_paths <= 65535 per call.  Asynchronous.
+ */
+rt_status rt_march(const rt_grid *grid, const float *kappa, const rt_spectral *spec,
+                   int64_t n_paths, const float *pos, const float *dir, const float *I_in,
+                   float *I_out, double *power, uint32_t *status, void *stream);
 
 /* Zero a tally buffer of ncells cells (asynchronous). */
 rt_status rt_tally_zero(const rt_tally_buf *tally, int64_t ncells, void *stream);

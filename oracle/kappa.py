@@ -33,8 +33,29 @@ def line_terms(lines, T, p_atm, x, profile):
     return A, g, a
 
 
+def _fixed_window(lines, spec):
+    """Fixed points per line: j = jf - n/2 + 1 .. jf + n/2, jf = floor((nu0 - nu_min)/dnu)."""
+    n = int(spec.points_per_line)
+    jf = np.floor((lines.nu0 - spec.nu_min) / spec.dnu).astype(np.int64)
+    lo = np.maximum(jf - n // 2 + 1, 0)
+    hi = np.minimum(jf + n // 2, spec.n_nu - 1)
+    return lo, hi
+
+
 def _pairs(lines, spec, js):
-    """All (column, line) pairs with |nu_j - nu0| <= cutoff, exact float64 test."""
+    """All (column, line) pairs with |nu_j - nu0| <= cutoff, exact float64 test
+    (or, with points_per_line > 0, the fixed window of each line)."""
+    if getattr(spec, "points_per_line", 0) > 0:
+        lo, hi = _fixed_window(lines, spec)
+        js = np.asarray(js, dtype=np.int64)
+        col_l, lid_l = [], []
+        for i, j in enumerate(js):
+            ls = np.nonzero((lo <= j) & (hi >= j))[0]
+            col_l.append(np.full(ls.size, i, dtype=np.int64))
+            lid_l.append(ls)
+        col = np.concatenate(col_l) if col_l else np.zeros(0, np.int64)
+        lid = np.concatenate(lid_l) if lid_l else np.zeros(0, np.int64)
+        return col, lid, grid_nu(spec, js)[col] - lines.nu0[lid]
     nu_j = grid_nu(spec, js)
     slack = 1e-9 * max(1.0, abs(spec.nu_min) + spec.n_nu * spec.dnu)
     lo = np.searchsorted(lines.nu0, nu_j - spec.cutoff - slack, side="left")
@@ -80,6 +101,8 @@ def kappa_table(lines, spec, chunk=512):
 def line_ranges(lines, spec):
     """Inclusive grid-index range [j_lo, j_hi] of each line's cutoff window,
     decided by the float64 test |nu_j - nu0| <= cutoff (empty when j_lo > j_hi)."""
+    if getattr(spec, "points_per_line", 0) > 0:
+        return _fixed_window(lines, spec)
     nu0 = lines.nu0
     n = spec.n_nu
     lo = np.floor((nu0 - spec.cutoff - spec.nu_min) / spec.dnu).astype(np.int64) - 1

@@ -53,7 +53,7 @@ class rt_spectral(ct.Structure):
     _fields_ = [("nu_min", ct.c_double), ("dnu", ct.c_double), ("n_nu", ct.c_int64),
                 ("cutoff", ct.c_double), ("profile", ct.c_int32), ("nT", ct.c_int32),
                 ("T_min", ct.c_double), ("T_max", ct.c_double), ("p_ref_atm", ct.c_double),
-                ("x_ref", ct.c_double)]
+                ("x_ref", ct.c_double), ("points_per_line", ct.c_int32), ("accumulate", ct.c_int32)]
 
 
 class rt_grid(ct.Structure):
@@ -99,6 +99,7 @@ _SIGNATURES = {
     "rt_batch_trace": ([_P, _P, _P], ct.c_int),
     "rt_batch_destroy": ([_P], ct.c_int),
     "rt_trace_batch": ([ct.c_int32, _P, _P, _P, ct.c_uint64, ct.c_int32, _P, _P], ct.c_int),
+    "rt_march": ([_P, _P, _P, ct.c_int64, _P, _P, _P, _P, _P, _P, _P], ct.c_int),
     "rt_set_tuning": ([_P], ct.c_int),
     "rt_get_tuning": ([_P], ct.c_int),
 }
@@ -179,7 +180,8 @@ def make_spectral(spec) -> rt_spectral:
     return rt_spectral(float(spec.nu_min), float(spec.dnu), int(spec.n_nu), float(spec.cutoff),
                        PROFILE[spec.profile] if isinstance(spec.profile, str) else int(spec.profile),
                        int(spec.nT), float(spec.T_min), float(spec.T_max), float(spec.p_ref_atm),
-                       float(spec.x_ref))
+                       float(spec.x_ref), int(getattr(spec, "points_per_line", 0)),
+                       int(getattr(spec, "accumulate", 0)))
 
 
 def make_grid(grid, device="cuda"):
@@ -415,3 +417,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def march(grid_struct, kappa, spec, pos, dirs, I_in=None, want_I=True, stream=None):
+    """rt_march on CUDA tensors pos, dirs [n, 3]; returns (I_out [n, n_nu] or None, power [n])."""
+    import torch
+    n = int(pos.shape[0])
+    S = make_spectral(spec)
+    I_out = torch.empty((n, int(spec.n_nu)), dtype=torch.float32, device="cuda") if want_I else None
+    power = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st = lib().rt_march(ct.byref(grid_struct), _ptr(kappa), ct.byref(S), n, _ptr(pos), _ptr(dirs),
+                        _ptr(I_in), _ptr(I_out), _ptr(power), None, _stream_ptr(stream))
+    _check(st, "rt_march")
+    return I_out, power

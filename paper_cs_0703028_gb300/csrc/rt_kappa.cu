@@ -34,7 +34,7 @@ constexpr double kPi = 3.14159265358979323846;
 struct GeomParams {
   double nu_min, dnu, cutoff;
   long long n_nu, n_lines;
-  int nT, check;
+  int nT, check, ppl;
 };
 
 struct PrefParams {
@@ -79,14 +79,22 @@ __global__ void k_line_geometry(const double *__restrict__ nu0, const double *__
     flo = fmin(fmax(isfinite(flo) ? flo : 0.0, -1.0), (double)P.n_nu + 1.0);
     fhi = fmin(fmax(isfinite(fhi) ? fhi : 0.0, -2.0), (double)P.n_nu + 1.0);
     long long lo = (long long)flo, hi = (long long)fhi;
+    if (P.ppl > 0) {  // fixed points per line around the centre
+      double jf = floor((v - P.nu_min) / P.dnu);
+      jf = fmin(fmax(isfinite(jf) ? jf : 0.0, -536870912.0), 536870912.0);
+      lo = (long long)jf - P.ppl / 2 + 1;
+      hi = (long long)jf + P.ppl / 2;
+    }
     if (lo < 0) lo = 0;
     if (hi > P.n_nu - 1) hi = P.n_nu - 1;
+    if (P.ppl <= 0) {
 #pragma unroll 1
-    for (int it = 0; it < 6 && lo < P.n_nu; ++it)
-      if (__dsub_rn(grid_nu(P.nu_min, lo, P.dnu), v) < -P.cutoff) ++lo;
+      for (int it = 0; it < 6 && lo < P.n_nu; ++it)
+        if (__dsub_rn(grid_nu(P.nu_min, lo, P.dnu), v) < -P.cutoff) ++lo;
 #pragma unroll 1
-    for (int it = 0; it < 6 && hi >= 0; ++it)
-      if (__dsub_rn(grid_nu(P.nu_min, hi, P.dnu), v) > P.cutoff) --hi;
+      for (int it = 0; it < 6 && hi >= 0; ++it)
+        if (__dsub_rn(grid_nu(P.nu_min, hi, P.dnu), v) > P.cutoff) --hi;
+    }
     R[l] = make_int4((int)lo, (int)hi, (int)jc, __float_as_int(dg));
     if (hi >= lo) cnt = (unsigned long long)(hi - lo + 1) * (unsigned long long)P.nT;
   }
@@ -206,7 +214,8 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
 template <int PROFILE>
 __global__ void __launch_bounds__(32 * kMaxTPerBlock)
 k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_lines,
-        long long n_nu, int nT, WeidCoef wc, int vec_ok, float *__restrict__ kappa, uint32_t *status) {
+        long long n_nu, int nT, WeidCoef wc, int vec_ok, int accumulate, float *__restrict__ kappa,
+        uint32_t *status) {
   __shared__ __align__(16) int4 sR[2][kChunk];
   __shared__ __align__(16) float4 sP[2][kMaxTPerBlock][kChunk];
   __shared__ __align__(8) uint64_t bars[2];
@@ -372,11 +381,16 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
 #pragma unroll
   for (int q = 0; q < kPtsPerThread; ++q) out[q] = __fsub_rn(acc[q], cmp[q]);
   if ((long long)jt + kPtsPerThread <= jend && vec_ok) {
-    *reinterpret_cast<float4 *>(row + jt) = make_float4(out[0], out[1], out[2], out[3]);
+    float4 *dst = reinterpret_cast<float4 *>(row + jt);
+    if (accumulate) {
+      const float4 o = *dst;
+      out[0] += o.x; out[1] += o.y; out[2] += o.z; out[3] += o.w;
+    }
+    *dst = make_float4(out[0], out[1], out[2], out[3]);
   } else {
 #pragma unroll
     for (int q = 0; q < kPtsPerThread; ++q)
-      if ((long long)jt + q < jend) row[jt + q] = out[q];
+      if ((long long)jt + q < jend) row[jt + q] = accumulate ? row[jt + q] + out[q] : out[q];
   }
 }
 
@@ -393,9 +407,11 @@ rt_status launch_kappa(const float4 *P, const int4 *R, long long n, const rt_spe
   const int tpb = spec->nT < want ? spec->nT : want;
   dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)((spec->nT + tpb - 1) / tpb));
   if (spec->profile == RT_PROFILE_LORENTZ)
-    k_kappa<RT_PROFILE_LORENTZ><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok, kappa, status);
+    k_kappa<RT_PROFILE_LORENTZ><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok,
+                                                         spec->accumulate ? 1 : 0, kappa, status);
   else
-    k_kappa<RT_PROFILE_VOIGT><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok, kappa, status);
+    k_kappa<RT_PROFILE_VOIGT><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok,
+                                                         spec->accumulate ? 1 : 0, kappa, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -419,6 +435,9 @@ rt_status validate_spec(const rt_spectral *s) {
   if (!std::isfinite(s->p_ref_atm) || !(s->p_ref_atm > 0) || !std::isfinite(s->x_ref) ||
       !(s->x_ref > 0))
     return fail(RT_E_INVAL, "spec.p_ref_atm and spec.x_ref must be finite and > 0");
+  if (s->points_per_line < 0 || s->points_per_line > (1 << 20))
+    return fail(RT_E_INVAL, "spec.points_per_line must be in [0, 2^20]");
+  if (s->accumulate != 0 && s->accumulate != 1) return fail(RT_E_INVAL, "spec.accumulate must be 0 or 1");
   return RT_OK;
 }
 
@@ -445,7 +464,8 @@ rt_status launch_line_geometry(const double *nu0, const double *S, const double 
                                long long n, const rt_spectral *spec, int check, int4 *R,
                                unsigned long long *evals, uint32_t *status, cudaStream_t st) {
   if (n <= 0) return RT_OK;
-  GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT, check};
+  GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT, check,
+               spec->points_per_line};
   k_line_geometry<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nu0, S, g, E, G, R, evals, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
@@ -473,7 +493,7 @@ rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float
   }
   const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
   if (n == 0) {
-    RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
+    if (!spec->accumulate) RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
     return RT_OK;
   }
 
@@ -499,7 +519,7 @@ rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float
   float4 *P = reinterpret_cast<float4 *>(base + off_P);
 
   GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
-               lines->memory == RT_MEM_DEVICE ? 1 : 0};
+               lines->memory == RT_MEM_DEVICE ? 1 : 0, spec->points_per_line};
   const int tb = 256;
   k_line_geometry<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d_nu0, d_S, d_g, d_E, G, R,
                                                                 evals_out, status);
@@ -586,7 +606,7 @@ rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec
   }
   const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
   if (n == 0) {
-    RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
+    if (!spec->accumulate) RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
     return RT_OK;
   }
   void *scratch = nullptr;
@@ -606,7 +626,7 @@ rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec
   float4 *P = reinterpret_cast<float4 *>(base + off_P);
 
   GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
-               lines->memory == RT_MEM_DEVICE ? 1 : 0};
+               lines->memory == RT_MEM_DEVICE ? 1 : 0, spec->points_per_line};
   const int tb = 256;
   k_line_geometry<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d_nu0, d_S, d_g, d_E, G, R,
                                                                 evals_out, status);

@@ -70,6 +70,8 @@ class Spectral:
     T_max: float = 296.0
     p_ref_atm: float = 1.0   # table pressure [atm]
     x_ref: float = 0.1       # table absorber mole fraction
+    points_per_line: int = 0  # > 0: fixed number of grid points per line instead of the cutoff
+    accumulate: int = 0       # add into an existing table (one build per absorbing gas)
 
     @property
     def nu_max(self) -> float:

@@ -131,3 +131,37 @@ def test_c1_full_size_table_sampled_columns(rt, c1_columns):
     assert got.shape == (64, 100000)
     assert np.all(np.isfinite(got)) and np.all(got > 0)
     assert _rel(got[:, cols], ref).max() <= TOL
+
+
+@pytest.mark.parametrize("profile", ["lorentz", "voigt"])
+def test_fixed_points_per_line(rt, profile):
+    from dataclasses import replace
+    rng = synth.rng_for(9, 80)
+    lines = synth.make_lines(2000, 1990.0, 2110.0, rng)
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.01, n_nu=10000, cutoff=25.0, profile=profile, nT=3,
+                          T_min=800.0, T_max=1600.0, points_per_line=16)
+    got, ev, st = _gpu_table(rt, lines, spec)
+    ref = okappa.kappa_table(lines, spec)
+    assert ev == okappa.profile_evals(lines, spec)
+    nz = ref > 0
+    assert np.array_equal(got > 0, nz)
+    assert _rel(got[nz], ref[nz]).max() <= TOL
+
+
+def test_two_gas_mixture_accumulates(rt):
+    import torch
+    from dataclasses import replace
+    rng = synth.rng_for(9, 81)
+    co2 = synth.make_lines(600, 2000.0, 2200.0, rng)
+    h2o = replace(synth.make_lines(400, 2050.0, 2250.0, rng, S_lo=1e-23, S_hi=1e-20), mass_amu=18.0,
+                  n_T=0.6, q_exp=1.5)
+    s1 = synth.Spectral(nu_min=2020.0, dnu=0.02, n_nu=8000, cutoff=25.0, profile="voigt", nT=4,
+                        T_min=700.0, T_max=1900.0, x_ref=0.1)
+    s2 = replace(s1, x_ref=0.05, accumulate=1)
+    out = torch.empty((s1.nT, s1.n_nu), dtype=torch.float32, device="cuda")
+    rt.build_kappa(co2, s1, out=out)
+    rt.build_kappa(h2o, s2, out=out)
+    torch.cuda.synchronize()
+    ref = okappa.kappa_table(co2, s1) + okappa.kappa_table(h2o, replace(s2, accumulate=0))
+    got = out.cpu().numpy().astype(np.float64)
+    assert _rel(got, ref).max() <= TOL

@@ -195,3 +195,20 @@ def test_planck_stefan_boltzmann():
     nu = (np.arange(80000) + 0.5) * dnu      # cm^-1, midpoints up to 40000 cm^-1
     total = ph.planck_wavenumber(nu, T).sum() * dnu * 100.0
     assert total == pytest.approx(SIGMA_SB * T ** 4 / math.pi, rel=1e-8)
+
+
+def test_fixed_points_per_line_window():
+    # Section 3: 16 contributions per line; the window is the 8 grid points at or
+    # below the centre and the 8 above it
+    from dataclasses import replace
+    case = synth.config(0)
+    spec = replace(case.spec, points_per_line=16)
+    lo, hi = K.line_ranges(case.lines, spec)
+    inner = (lo > 0) & (hi < spec.n_nu - 1)
+    assert np.all(hi[inner] - lo[inner] + 1 == 16)
+    nu_lo = K.grid_nu(spec, lo[inner] + 7)
+    nu_hi = K.grid_nu(spec, lo[inner] + 8)
+    assert np.all(nu_lo <= case.lines.nu0[inner]) and np.all(nu_hi > case.lines.nu0[inner])
+    tab = K.kappa_table(case.lines, spec)[0]
+    assert K.profile_evals(case.lines, spec) == int(np.sum(hi - lo + 1))
+    assert np.count_nonzero(tab) <= 500 * 16
