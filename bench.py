@@ -288,6 +288,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
     }
+    if world == 1 and not args.no_surrogate:
+        out["surrogate"] = surrogate_summary(args)
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(case, evals_per_step, steps_per_step, budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -385,6 +387,23 @@ def _ev_time(fn, reps=1):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def surrogate_summary(args):
+    """Compact form of run_surrogate for the default benchmark line."""
+    import io
+    import contextlib
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        run_surrogate(args)
+    r = json.loads(buf.getvalue().strip().splitlines()[-1])
+    w = r["walks"]
+    return {"workload": r["config"]["workload"],
+            "steps_per_s": {k: w[k]["ray_cell_steps_per_s"] for k in w},
+            "speedup_vs_lbl": r["speedup_vs_lbl"],
+            "tally_error_vs_table_median": r["tally_error_vs_table"]["median"],
+            "meets_1pct_target": r["tally_error_vs_table"]["max"] <= 0.01,
+            "training": r["training"]}
 
 
 def run_surrogate(args):
@@ -518,10 +537,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--workload", default="box32", choices=["box32", "surrogate", "batched", "box128"])
     ap.add_argument("--samples", type=int, default=20_000_000)
     ap.add_argument("--epochs", type=int, default=1)
-    ap.add_argument("--rays", type=int, default=5_000_000)
+    ap.add_argument("--rays", type=int, default=2_000_000)
     ap.add_argument("--rays-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.workload == "surrogate":

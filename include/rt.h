@@ -204,10 +204,11 @@ rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *
  * Scratch: a 32 MiB array in the library's device memory (a file-scope
  *   __device__ array that every GPU loading the library holds until the process
  *   exits); the call allocates and frees nothing.
- * Limit: 16 B per (T node, line) + 16 B per line, plus 32 B per line when the
- *   lines are host-resident, at most 32 MiB in all (about 2 million (T node, line)
- *   pairs, e.g. 64 T nodes x 30,000 lines).  Larger inputs return RT_E_INVAL with
- *   the required size before any work is queued.
+ * Limit: 16 B per (T node, line) for Lorentz lines, 32 B for Voigt lines, + 16 B
+ *   per line + 32 B per 256 wavenumbers, plus 32 B per line when the lines are
+ *   host-resident, at most 32 MiB in all (about 2 million Lorentz or 1 million
+ *   Voigt (T node, line) pairs, e.g. 64 T nodes x 15,000 Voigt lines).  Larger
+ *   inputs return RT_E_INVAL with the required size before any work is queued.
  * Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before
  *   any stream capture.

@@ -1,17 +1,22 @@
 // Absorption-coefficient table on a temperature grid: Eqs. (S) and (tau) of
 // Section 3, for one absorbing gas, with Lorentz or Voigt line shapes and a
-// wing cutoff.  Three kernels:
+// wing cutoff.  Four kernels:
 //   k_line_geometry : per line, the binary64 grid decisions (cutoff window
 //                     [j_lo, j_hi], nearest grid index j_c and offset) and the
 //                     profile-evaluation count; validates device-resident lists.
 //   k_prefactor     : per (T node, line), Eq. (S) times the number density and
 //                     the width parameters, in binary32 with double-float
-//                     arithmetic for the Boltzmann exponent.
-//   k_kappa         : per (1024-point wavenumber tile, T node), the line sum.
-//                     The tile's lines are staged in shared memory by bulk
-//                     asynchronous copies (cp.async.bulk + mbarrier), double
-//                     buffered; each thread owns 4 consecutive points (one
-//                     float4 store) and Kahan-sums over lines in ascending nu0.
+//                     arithmetic for the Boltzmann exponent; for Voigt lines
+//                     also the far-wing polynomial coefficients.
+//   k_tile_lines    : per 256-point wavenumber tile, the range of lines whose
+//                     windows reach it and the sub-ranges of lines that cover
+//                     the whole tile far from their centres (no masking and no
+//                     near-centre points: the fast path).
+//   k_kappa         : per (tile, up to 8 T nodes), the line sum.  The tile's
+//                     lines are staged in shared memory by bulk asynchronous
+//                     copies (cp.async.bulk + mbarrier), double buffered; each
+//                     lane owns 8 consecutive points (two float4 stores) and
+//                     Kahan-sums over lines in ascending nu0.
 #include <cmath>
 #include <mutex>
 
@@ -20,10 +25,11 @@
 namespace rt {
 namespace {
 
-constexpr int kPtsPerThread = 4;
-constexpr int kTilePts = 32 * kPtsPerThread;  // 128 wavenumbers per block, one warp per T node
+constexpr int kPtsPerThread = 8;
+constexpr int kTilePts = 32 * kPtsPerThread;  // 256 wavenumbers per block, one warp per T node
 constexpr int kMaxTPerBlock = 8;              // warps (T nodes) per block
-constexpr int kChunk = 128;                   // lines per staged chunk
+constexpr int kChunk = 64;                    // lines per staged chunk
+constexpr int kGroup = 4;                     // fast-path lines summed before one compensated add
 constexpr unsigned kWaitLimit = 1u << 22;                // bounded mbarrier waits
 
 // CODATA 2018 (SI); derived quantities are formed on the host in binary64.
@@ -106,7 +112,7 @@ __global__ void k_line_geometry(const double *__restrict__ nu0, const double *__
 
 __global__ void k_prefactor(const double *__restrict__ nu0, const double *__restrict__ S,
                             const double *__restrict__ g, const double *__restrict__ E,
-                            PrefParams Q, float4 *__restrict__ Pout) {
+                            PrefParams Q, float4 *__restrict__ Pout, float4 *__restrict__ P2out) {
   const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (l >= Q.n_lines) return;
@@ -142,8 +148,13 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
     const float y = s * gam;
     const float sd = s * Q.dnu;
     // half-width (grid units) of the region |z| < 20 where the far-wing series does not hold
-    const float u_near = sqrtf(fmaxf(400.0f - y * y, 0.0f)) / sd;
-    out = make_float4(A * s * (float)(1.0 / kPi) * y, sd, y * y, u_near);
+    const float y2 = y * y;
+    const float u_near = sqrtf(fmaxf(400.0f - y2, 0.0f)) / sd;
+    // far wing: c0 t (1 + 1.5 t + (3.75 - 2 y^2) t^2 - 15 y^2 t^3 + 12 y^4 t^4), t = 1/|z|^2
+    const float c0 = A * s * (float)(1.0 / kPi) * y;
+    out = make_float4(c0, sd, y2, 1.5f * c0);
+    P2out[(long long)k * Q.n_lines + l] =
+        make_float4(__fmaf_rn(-2.0f, y2, 3.75f) * c0, -15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near);
   }
   Pout[(long long)k * Q.n_lines + l] = out;
 }
@@ -190,6 +201,43 @@ __device__ __forceinline__ long long lower_bound_lo(const int4 *R, long long n, 
   return a;
 }
 
+__device__ __forceinline__ long long lower_bound_c(const int4 *R, long long n, long long j) {
+  long long a = 0, b = n;  // first l with R[l].z >= j
+  while (a < b) {
+    long long m = (a + b) >> 1;
+    if (R[m].z < j) a = m + 1; else b = m;
+  }
+  return a;
+}
+
+// Per tile of kTilePts wavenumbers [jw0, jw0 + kTilePts): the lines [lb, ub)
+// whose windows reach it and two fast sub-ranges.  Windows and centres are
+// monotone in the (sorted) line index, so each set is an index range:
+//   cover : j_lo <= jw0 and j_hi >= jw0 + kTilePts - 1 (no masking needed);
+//   near  : j_c within W + 4 grid points of the tile, W bounding the near-centre
+//           half-width of every line (lines outside it have no point |z| < 20).
+// Fast = cover minus near; out[2t] = {lb, ub, fa0, fb0}, out[2t+1] = {fa1, fb1}.
+__global__ void k_tile_lines(const int4 *__restrict__ R, long long n, long long n_nu, int W,
+                             long long n_tiles, int4 *__restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  const long long jw0 = t * kTilePts, jw1 = jw0 + kTilePts - 1;
+  const long long jend = min(jw0 + (long long)kTilePts, n_nu);
+  const long long lb = lower_bound_hi(R, n, (int)jw0);
+  const long long ub = max(lb, lower_bound_lo(R, n, (int)jend));
+  const long long ca = lower_bound_hi(R, n, (int)jw1);
+  const long long cb = lower_bound_lo(R, n, (int)(jw0 + 1));
+  const long long na = lower_bound_c(R, n, jw0 - W - 4);
+  const long long nb = lower_bound_c(R, n, jw1 + W + 5);
+  auto clampr = [&](long long v) { return min(max(v, lb), ub); };
+  const long long fa0 = clampr(ca);
+  const long long fb0 = clampr(max(fa0, min(cb, na)));
+  const long long fa1 = clampr(max(fb0, max(ca, nb)));
+  const long long fb1 = clampr(max(fa1, cb));
+  out[2 * t] = make_int4((int)lb, (int)ub, (int)fa0, (int)fb0);
+  out[2 * t + 1] = make_int4((int)fa1, (int)fb1, 0, 0);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -203,23 +251,30 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
   s = t;
 }
 
-// Block = 128 consecutive wavenumbers x up to 8 temperature nodes (one warp per
-// node, 4 consecutive points per lane).  All warps walk the same lines: the
-// block's lines are staged chunk by chunk (geometry R once, prefactors P per
-// node) with bulk asynchronous copies on an mbarrier, double buffered.
-// Far wing (|z| >= 20): with t = 1/|z|^2 the three-term series is the
-// polynomial 1 + 1.5 t + (3.75 - 2y^2) t^2 - 15 y^2 t^3 + 12 y^4 t^4 (times y t);
-// a warp-uniform interval test per line sends near-centre points to
-// faddeeva_re_near.  Lorentz: p = {A g / (pi dnu), g^2}.
+// Block = 256 consecutive wavenumbers x up to 8 temperature nodes (one warp per
+// node, 8 consecutive points per lane).  All warps walk the same lines: the
+// block's lines are staged chunk by chunk (geometry R once, coefficients P and,
+// for Voigt, P2 per node) with bulk asynchronous copies on an mbarrier, double
+// buffered.  A point's offset from a line centre, in grid units, is the exact
+// integer j - j_c plus the binary32 sub-grid offset of the centre, so its
+// rounding error is relative to the distance itself.
+// Voigt far wing (|z| >= 20): with t = 1/|z|^2 the three-term series is the
+// polynomial c0 t + c1 t^2 + c2 t^3 + c3 t^4 + c4 t^5 (coefficients from
+// k_prefactor).  Fast-path lines (whole tile covered, no near-centre point) add
+// kGroup lines per compensated add; the other lines take a warp-uniform interval
+// test that sends near-centre points, compacted across the warp, to
+// faddeeva_re_near, mask the ends of their windows, and add in pairs.
+// Lorentz: P = {A g / (pi dnu), g^2}.
 template <int PROFILE>
-__global__ void __launch_bounds__(32 * kMaxTPerBlock)
-k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_lines,
-        long long n_nu, int nT, WeidCoef wc, int vec_ok, int accumulate, float *__restrict__ kappa,
-        uint32_t *status) {
+__global__ void __launch_bounds__(32 * kMaxTPerBlock, 3)
+k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 *__restrict__ R,
+        const int4 *__restrict__ tiles, long long n_lines, long long n_nu, int nT, WeidCoef wc,
+        int vec_ok, int accumulate, float *__restrict__ kappa, uint32_t *status) {
+  constexpr bool kVoigt = PROFILE == RT_PROFILE_VOIGT;
+  constexpr int kPSets = kVoigt ? 2 : 1;
   __shared__ __align__(16) int4 sR[2][kChunk];
-  __shared__ __align__(16) float4 sP[2][kMaxTPerBlock][kChunk];
+  __shared__ __align__(16) float4 sP[2][kPSets][kMaxTPerBlock][kChunk];
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ long long s_lb, s_ub;
   __shared__ float s_qx[kMaxTPerBlock][kTilePts];           // near-centre queue: x
   __shared__ unsigned char s_qs[kMaxTPerBlock][kTilePts];   // near-centre queue: owner slot
   __shared__ float s_res[kMaxTPerBlock][kTilePts];          // near-centre values by slot
@@ -233,27 +288,29 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
   const long long jend = min(j0 + (long long)kTilePts, n_nu);
   const int jw0 = (int)j0, jw1 = jw0 + kTilePts - 1;
   const int jt = jw0 + lane * kPtsPerThread;
-  const float off_t = (float)(lane * kPtsPerThread);
 
+  const int4 ta = __ldg(tiles + 2 * blockIdx.x), tb = __ldg(tiles + 2 * blockIdx.x + 1);
+  const int lb = ta.x, ub = ta.y;
+  const int seg0 = ta.z, seg1 = ta.w, seg2 = tb.x, seg3 = tb.y;  // fast: [seg0, seg1), [seg2, seg3)
   if (threadIdx.x == 0) {
-    s_lb = lower_bound_hi(R, n_lines, jw0);
-    s_ub = max(s_lb, lower_bound_lo(R, n_lines, (int)jend));
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const long long lb = s_lb, ub = s_ub;
-  const int nchunks = (int)((ub - lb + kChunk - 1) / kChunk);
+  const int nchunks = (ub - lb + kChunk - 1) / kChunk;
 
   auto issue = [&](int c) {
-    const long long l0 = lb + (long long)c * kChunk;
-    const uint32_t cnt = (uint32_t)min((long long)kChunk, ub - l0);
+    const long long l0 = (long long)lb + (long long)c * kChunk;
+    const uint32_t cnt = (uint32_t)min((long long)kChunk, (long long)ub - l0);
     const int b = c & 1;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_arrive_expect_tx(&bars[b], cnt * 16u * (uint32_t)(nk + 1));
+    mbar_arrive_expect_tx(&bars[b], cnt * 16u * (uint32_t)(kPSets * nk + 1));
     bulk_g2s(&sR[b][0], R + l0, cnt * 16u, &bars[b]);
-    for (int w = 0; w < nk; ++w) bulk_g2s(&sP[b][w][0], P + (long long)(k0 + w) * n_lines + l0, cnt * 16u, &bars[b]);
+    for (int w = 0; w < nk; ++w) {
+      bulk_g2s(&sP[b][0][w][0], P + (long long)(k0 + w) * n_lines + l0, cnt * 16u, &bars[b]);
+      if (kVoigt) bulk_g2s(&sP[b][kPSets - 1][w][0], P2 + (long long)(k0 + w) * n_lines + l0, cnt * 16u, &bars[b]);
+    }
   };
 
   float acc[kPtsPerThread], cmp[kPtsPerThread];
@@ -263,6 +320,7 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
     if (nchunks > 0) issue(0);
     if (nchunks > 1) issue(1);
   }
+  const int wsel = min(warp, nk - 1);
   bool aborted = false;
   for (int c = 0; c < nchunks; ++c) {
     const int b = c & 1;
@@ -280,44 +338,87 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
       aborted = true;
       break;
     }
-    const long long l0 = lb + (long long)c * kChunk;
-    const int cnt = (int)min((long long)kChunk, ub - l0);
-    const int wsel = min(warp, nk - 1);
-    // lines enter the compensated sum in pairs: the sum of two positive line
-    // values is rounded once (relative error <= 2^-24 of the pair)
+    const int l0 = lb + c * kChunk;
+    const int cnt = min(kChunk, ub - l0);
+
+    // fast path: g[q] += value of line i at the lane's points (or = when first)
+    auto fast_line = [&](int i, float (&g)[kPtsPerThread], bool first) {
+      const int4 r = sR[b][i];
+      const float4 p = sP[b][0][wsel][i];
+      const float ul = (float)(jt - r.z) + __int_as_float(r.w);
+      if (!kVoigt) {
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) {
+          const float u = __fadd_rn(ul, (float)q);
+          const float rr = rcp_approx(__fmaf_rn(u, u, p.y));
+          g[q] = first ? p.x * rr : __fmaf_rn(p.x, rr, g[q]);
+        }
+      } else {
+        const float4 p2 = sP[b][kPSets - 1][wsel][i];
+        const float xt = p.y * ul;
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) {
+          const float x = __fmaf_rn(p.y, (float)q, xt);
+          const float t = rcp_approx(__fmaf_rn(x, x, p.z));
+          const float h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.z, p2.y), p2.x), p.w), p.x);
+          g[q] = first ? t * h : __fmaf_rn(t, h, g[q]);
+        }
+      }
+    };
+    auto run_fast = [&](int i, int i1) {
+#pragma unroll 1
+      for (; i + kGroup <= i1; i += kGroup) {
+        float g[kPtsPerThread];
+        fast_line(i, g, true);
+#pragma unroll
+        for (int e = 1; e < kGroup; ++e) fast_line(i + e, g, false);
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], g[q]);
+      }
+      if (i < i1) {
+        float g[kPtsPerThread];
+        fast_line(i, g, true);
+#pragma unroll 1
+        for (int e = i + 1; e < i1; ++e) fast_line(e, g, false);
+#pragma unroll
+        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], g[q]);
+      }
+    };
+
+    // general path: the value of line i at the lane's points, with masking
+    // outside the window and near-centre points
     auto line_vals = [&](int i, float (&v)[kPtsPerThread]) {
         const int4 r = sR[b][i];
-        const float4 p = sP[b][wsel][i];
-        const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);  // grid offset of the warp's first point
-        if (PROFILE == RT_PROFILE_LORENTZ) {
-          const float u = fu + off_t;
+        const float4 p = sP[b][0][wsel][i];
+        const float ul = (float)(jt - r.z) + __int_as_float(r.w);
+        if (!kVoigt) {
 #pragma unroll
           for (int q = 0; q < kPtsPerThread; ++q) {
-            const float uq = u + (float)q;
-            v[q] = p.x * rcp_approx(__fmaf_rn(uq, uq, p.y));
+            const float u = __fadd_rn(ul, (float)q);
+            v[q] = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
           }
         } else {
+          const float4 p2 = sP[b][kPSets - 1][wsel][i];
           const float y2 = p.z;
-          const float a2 = __fmaf_rn(-2.0f, y2, 3.75f), a3 = -15.0f * y2, a4 = 12.0f * y2 * y2;
-          const float xt = p.y * (fu + off_t);
+          const float xt = p.y * ul;
+          float xs[kPtsPerThread];
 #pragma unroll
           for (int q = 0; q < kPtsPerThread; ++q) {
-            const float x = __fmaf_rn(p.y, (float)q, xt);
-            const float t = rcp_approx(__fmaf_rn(x, x, y2));
-            const float S = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, a4, a3), a2), 1.5f), 1.0f);
-            v[q] = p.x * (t * S);
+            xs[q] = __fmaf_rn(p.y, (float)q, xt);
+            const float t = rcp_approx(__fmaf_rn(xs[q], xs[q], y2));
+            const float h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.z, p2.y), p2.x), p.w), p.x);
+            v[q] = t * h;
           }
-          if (fu < p.w + 1.0f && fu + (float)kTilePts > -p.w - 1.0f) {  // warp-uniform
+          // warp-uniform: the tile's offsets [fu, fu + kTilePts) meet the near region
+          const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);
+          if (fu < p2.w + 1.0f && fu + (float)kTilePts > -p2.w - 1.0f) {
             // compact this warp's near-centre points so one pass of the lanes evaluates them
-            float xs[kPtsPerThread];
             unsigned nearbits = 0;
 #pragma unroll
-            for (int q = 0; q < kPtsPerThread; ++q) {
-              xs[q] = __fmaf_rn(p.y, (float)q, xt);
+            for (int q = 0; q < kPtsPerThread; ++q)
               nearbits |= (__fmaf_rn(xs[q], xs[q], y2) < 400.0f ? 1u : 0u) << q;
-            }
-            const int cnt = __popc(nearbits);
-            int pre = cnt;
+            const int cnt_n = __popc(nearbits);
+            int pre = cnt_n;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
               const int t = __shfl_up_sync(0xffffffffu, pre, o);
@@ -328,7 +429,7 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
               float *qx = s_qx[warp];
               unsigned char *qs = s_qs[warp];
               float *res = s_res[warp];
-              int pos = pre - cnt;
+              int pos = pre - cnt_n;
 #pragma unroll
               for (int q = 0; q < kPtsPerThread; ++q)
                 if ((nearbits >> q) & 1u) {
@@ -357,19 +458,36 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
             if (jt + q < r.x || jt + q > r.y) v[q] = 0.0f;
         }
     };
+    // lines enter the compensated sum in pairs: the sum of two positive line
+    // values is rounded once (relative error <= 2^-24 of the pair)
+    auto run_general = [&](int i, int i1) {
 #pragma unroll 1
-    for (int i = 0; i + 1 < cnt; i += 2) {
-      float va[kPtsPerThread], vb[kPtsPerThread];
-      line_vals(i, va);
-      line_vals(i + 1, vb);
+      for (; i + 1 < i1; i += 2) {
+        float va[kPtsPerThread], vb[kPtsPerThread];
+        line_vals(i, va);
+        line_vals(i + 1, vb);
 #pragma unroll
-      for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], __fadd_rn(va[q], vb[q]));
-    }
-    if (cnt & 1) {
-      float va[kPtsPerThread];
-      line_vals(cnt - 1, va);
+        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], __fadd_rn(va[q], vb[q]));
+      }
+      if (i < i1) {
+        float va[kPtsPerThread];
+        line_vals(i, va);
 #pragma unroll
-      for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], va[q]);
+        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], va[q]);
+      }
+    };
+
+    // the chunk [l0, l0 + cnt) split at the fast sub-range boundaries (block-uniform)
+    int i = 0;
+#pragma unroll 1
+    while (i < cnt) {
+      const int l = l0 + i;
+      // s = number of boundaries at or below l (odd: inside a fast sub-range)
+      const int s = (l >= seg0) + (l >= seg1) + (l >= seg2) + (l >= seg3);
+      const int end = s == 0 ? seg0 : (s == 1 ? seg1 : (s == 2 ? seg2 : (s == 3 ? seg3 : ub)));
+      const int i1 = min(cnt, end - l0);
+      if (s & 1) run_fast(i, i1); else run_general(i, i1);
+      i = i1;
     }
     __syncthreads();  // every warp is done with buffer b
     if (threadIdx.x == 0 && c + 2 < nchunks) issue(c + 2);
@@ -381,12 +499,15 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
 #pragma unroll
   for (int q = 0; q < kPtsPerThread; ++q) out[q] = __fsub_rn(acc[q], cmp[q]);
   if ((long long)jt + kPtsPerThread <= jend && vec_ok) {
-    float4 *dst = reinterpret_cast<float4 *>(row + jt);
-    if (accumulate) {
-      const float4 o = *dst;
-      out[0] += o.x; out[1] += o.y; out[2] += o.z; out[3] += o.w;
+#pragma unroll
+    for (int q4 = 0; q4 < kPtsPerThread; q4 += 4) {
+      float4 *dst = reinterpret_cast<float4 *>(row + jt + q4);
+      if (accumulate) {
+        const float4 o = *dst;
+        out[q4] += o.x; out[q4 + 1] += o.y; out[q4 + 2] += o.z; out[q4 + 3] += o.w;
+      }
+      *dst = make_float4(out[q4], out[q4 + 1], out[q4 + 2], out[q4 + 3]);
     }
-    *dst = make_float4(out[0], out[1], out[2], out[3]);
   } else {
 #pragma unroll
     for (int q = 0; q < kPtsPerThread; ++q)
@@ -396,22 +517,35 @@ k_kappa(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_li
 
 int g_kappa_tpb = kMaxTPerBlock;
 
-rt_status launch_kappa(const float4 *P, const int4 *R, long long n, const rt_spectral *spec,
-                       float *kappa, uint32_t *status, cudaStream_t st) {
+rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *tiles, long long n,
+                       const rt_spectral *spec, double nu_abs_max, double mass_amu, float *kappa,
+                       uint32_t *status, cudaStream_t st) {
   static WeidCoef wc;
   static std::once_flag wc_once;
   std::call_once(wc_once, [] { weideman_coefficients(&wc); });
+  // W bounds every line's near-centre half-width sqrt(400 - y^2) / (s dnu) <= 20 alpha /
+  // (sqrt(ln 2) dnu), alpha the largest Doppler half-width of a line that reaches the grid
+  int W = 0;
+  if (spec->profile == RT_PROFILE_VOIGT) {
+    const double alpha = nu_abs_max * std::sqrt(spec->T_max) *
+                         std::sqrt(2.0 * std::log(2.0) * kKB / (mass_amu * kAmu)) / kC;
+    const double w = 20.0 * alpha / (std::sqrt(std::log(2.0)) * spec->dnu) * 1.01 + 2.0;
+    W = (!(w < (double)(1 << 28))) ? (1 << 28) : (int)std::ceil(w);
+  }
+  const long long n_tiles = (spec->n_nu + kTilePts - 1) / kTilePts;
+  k_tile_lines<<<(unsigned)((n_tiles + 127) / 128), 128, 0, st>>>(R, n, spec->n_nu, W, n_tiles, tiles);
+  RT_CUDA_TRY(cudaGetLastError());
   const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
   int want = g_kappa_tpb;
   if (want < 1 || want > kMaxTPerBlock) want = kMaxTPerBlock;
   const int tpb = spec->nT < want ? spec->nT : want;
-  dim3 gk((unsigned)((spec->n_nu + kTilePts - 1) / kTilePts), (unsigned)((spec->nT + tpb - 1) / tpb));
+  dim3 gk((unsigned)n_tiles, (unsigned)((spec->nT + tpb - 1) / tpb));
   if (spec->profile == RT_PROFILE_LORENTZ)
-    k_kappa<RT_PROFILE_LORENTZ><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok,
-                                                         spec->accumulate ? 1 : 0, kappa, status);
+    k_kappa<RT_PROFILE_LORENTZ><<<gk, 32 * tpb, 0, st>>>(P, P2, R, tiles, n, spec->n_nu, spec->nT, wc,
+                                                         vec_ok, spec->accumulate ? 1 : 0, kappa, status);
   else
-    k_kappa<RT_PROFILE_VOIGT><<<gk, 32 * tpb, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc, vec_ok,
-                                                         spec->accumulate ? 1 : 0, kappa, status);
+    k_kappa<RT_PROFILE_VOIGT><<<gk, 32 * tpb, 0, st>>>(P, P2, R, tiles, n, spec->n_nu, spec->nT, wc,
+                                                       vec_ok, spec->accumulate ? 1 : 0, kappa, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -471,41 +605,50 @@ rt_status launch_line_geometry(const double *nu0, const double *S, const double 
   return RT_OK;
 }
 
-rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float *kappa,
-                           unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
+namespace {
+
+// Scratch of one build: [line arrays if host-resident][R: n int4][P: nT n float4]
+// [P2: nT n float4, Voigt][tile ranges: 2 int4 per 256-point tile]
+struct KappaLayout {
+  size_t off_R, off_P, off_P2, off_tiles, total;
+};
+
+KappaLayout kappa_layout(const rt_lines *lines, const rt_spectral *spec) {
+  auto up = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t n = (size_t)lines->n;
+  const size_t pn = (size_t)spec->nT * n * sizeof(float4);
+  KappaLayout L;
+  L.off_R = up(lines->memory == RT_MEM_HOST ? 4 * n * sizeof(double) : 0);
+  L.off_P = up(L.off_R + n * sizeof(int4));
+  L.off_P2 = up(L.off_P + pn);
+  L.off_tiles = up(L.off_P2 + (spec->profile == RT_PROFILE_VOIGT ? pn : 0));
+  const size_t n_tiles = (size_t)((spec->n_nu + kTilePts - 1) / kTilePts);
+  L.total = L.off_tiles + n_tiles * 2 * sizeof(int4);
+  return L;
+}
+
+rt_status validate_build_args(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                              uint32_t *status, const char *who) {
   rt_status v = validate_spec(spec);
   if (v != RT_OK) return v;
-  if (!lines || !kappa) return fail(RT_E_INVAL, "rt_build_kappa: lines or kappa is NULL");
+  if (!lines || !kappa) return fail(RT_E_INVAL, "%s: lines or kappa is NULL", who);
   if (lines->n < 0 || lines->n > (1LL << 31) - 1) return fail(RT_E_INVAL, "lines.n out of range");
   if (lines->memory != RT_MEM_HOST && lines->memory != RT_MEM_DEVICE)
     return fail(RT_E_INVAL, "lines.memory must be RT_MEM_HOST or RT_MEM_DEVICE");
   if (!std::isfinite(lines->T_ref) || !(lines->T_ref > 0) || !std::isfinite(lines->n_T) ||
       !std::isfinite(lines->q_exp) || !std::isfinite(lines->mass_amu) || !(lines->mass_amu > 0))
     return fail(RT_E_INVAL, "lines: T_ref, n_T, q_exp, mass_amu must be finite (T_ref, mass > 0)");
-  const long long n = lines->n;
-  if (n > 0 && (!lines->nu0 || !lines->S_ref || !lines->gamma_ref || !lines->E_lower))
+  if (lines->n > 0 && (!lines->nu0 || !lines->S_ref || !lines->gamma_ref || !lines->E_lower))
     return fail(RT_E_INVAL, "lines: NULL array");
   if (lines->memory == RT_MEM_DEVICE && !status)
     return fail(RT_E_INVAL, "device-resident lines need a device status word");
-  if (lines->memory == RT_MEM_HOST && n > 0) {
-    v = validate_host_lines(lines, spec);
-    if (v != RT_OK) return v;
-  }
-  const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
-  if (n == 0) {
-    if (!spec->accumulate) RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
-    return RT_OK;
-  }
+  return RT_OK;
+}
 
-  // scratch: [line arrays if host-resident][R: n int4][P: nT*n float4]
-  const size_t bytes_lines = (lines->memory == RT_MEM_HOST) ? 4 * n * sizeof(double) : 0;
-  const size_t off_R = (bytes_lines + 255) & ~size_t(255);
-  const size_t off_P = (off_R + n * sizeof(int4) + 255) & ~size_t(255);
-  const size_t total = off_P + (size_t)spec->nT * n * sizeof(float4);
-  Scratch scr;
-  v = scr.alloc(total, st);
-  if (v != RT_OK) return v;
-  char *base = scr.as<char>();
+// Everything after validation, on scratch laid out by kappa_layout.
+rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, const rt_spectral *spec,
+                    float *kappa, unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
+  const long long n = lines->n;
   const double *d_nu0 = lines->nu0, *d_S = lines->S_ref, *d_g = lines->gamma_ref, *d_E = lines->E_lower;
   if (lines->memory == RT_MEM_HOST) {
     double *d = reinterpret_cast<double *>(base);
@@ -515,8 +658,10 @@ rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float
     RT_CUDA_TRY(cudaMemcpyAsync(d + 3 * n, lines->E_lower, n * sizeof(double), cudaMemcpyHostToDevice, st));
     d_nu0 = d; d_S = d + n; d_g = d + 2 * n; d_E = d + 3 * n;
   }
-  int4 *R = reinterpret_cast<int4 *>(base + off_R);
-  float4 *P = reinterpret_cast<float4 *>(base + off_P);
+  int4 *R = reinterpret_cast<int4 *>(base + L.off_R);
+  float4 *P = reinterpret_cast<float4 *>(base + L.off_P);
+  float4 *P2 = reinterpret_cast<float4 *>(base + L.off_P2);
+  int4 *tiles = reinterpret_cast<int4 *>(base + L.off_tiles);
 
   GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
                lines->memory == RT_MEM_DEVICE ? 1 : 0, spec->points_per_line};
@@ -543,10 +688,37 @@ rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float
   Q.nT = spec->nT;
   Q.profile = spec->profile;
   dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
-  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P);
+  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P, P2);
   RT_CUDA_TRY(cudaGetLastError());
 
-  return launch_kappa(P, R, n, spec, kappa, status, st);
+  // largest |nu0| of a line whose window (cutoff or fixed points) reaches the grid
+  const double reach = spec->cutoff + (spec->points_per_line + 2.0) * spec->dnu;
+  const double nu_abs_max =
+      std::fmax(std::fabs(spec->nu_min - reach),
+                std::fabs(spec->nu_min + (double)spec->n_nu * spec->dnu + reach));
+  return launch_kappa(P, P2, R, tiles, n, spec, nu_abs_max, lines->mass_amu, kappa, status, st);
+}
+
+}  // namespace
+
+rt_status build_kappa_impl(const rt_lines *lines, const rt_spectral *spec, float *kappa,
+                           unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
+  rt_status v = validate_build_args(lines, spec, kappa, status, "rt_build_kappa");
+  if (v != RT_OK) return v;
+  if (lines->memory == RT_MEM_HOST && lines->n > 0) {
+    v = validate_host_lines(lines, spec);
+    if (v != RT_OK) return v;
+  }
+  const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
+  if (lines->n == 0) {
+    if (!spec->accumulate) RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
+    return RT_OK;
+  }
+  const KappaLayout L = kappa_layout(lines, spec);
+  Scratch scr;
+  v = scr.alloc(L.total, st);
+  if (v != RT_OK) return v;
+  return run_build(scr.as<char>(), L, lines, spec, kappa, evals_out, status, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -576,82 +748,29 @@ static rt_status static_scratch_address(void **out) {
 
 rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec, float *kappa,
                                   unsigned long long *evals_out, uint32_t *status, cudaStream_t st) {
-  rt_status v = validate_spec(spec);
+  rt_status v = validate_build_args(lines, spec, kappa, status, "rt_build_kappa_static");
   if (v != RT_OK) return v;
-  if (!lines || !kappa) return fail(RT_E_INVAL, "rt_build_kappa_static: lines or kappa is NULL");
-  if (lines->n < 0 || lines->n > (1LL << 31) - 1) return fail(RT_E_INVAL, "lines.n out of range");
-  if (lines->memory != RT_MEM_HOST && lines->memory != RT_MEM_DEVICE)
-    return fail(RT_E_INVAL, "lines.memory must be RT_MEM_HOST or RT_MEM_DEVICE");
-  if (!std::isfinite(lines->T_ref) || !(lines->T_ref > 0) || !std::isfinite(lines->n_T) ||
-      !std::isfinite(lines->q_exp) || !std::isfinite(lines->mass_amu) || !(lines->mass_amu > 0))
-    return fail(RT_E_INVAL, "lines: T_ref, n_T, q_exp, mass_amu must be finite (T_ref, mass > 0)");
-  const long long n = lines->n;
-  if (n > 0 && (!lines->nu0 || !lines->S_ref || !lines->gamma_ref || !lines->E_lower))
-    return fail(RT_E_INVAL, "lines: NULL array");
-  if (lines->memory == RT_MEM_DEVICE && !status)
-    return fail(RT_E_INVAL, "device-resident lines need a device status word");
   // same scratch layout as rt_build_kappa, checked against the fixed array
-  const size_t bytes_lines = (lines->memory == RT_MEM_HOST) ? 4 * (size_t)n * sizeof(double) : 0;
-  const size_t off_R = (bytes_lines + 255) & ~size_t(255);
-  const size_t off_P = (off_R + (size_t)n * sizeof(int4) + 255) & ~size_t(255);
-  const size_t total = off_P + (size_t)spec->nT * (size_t)n * sizeof(float4);
-  if (total > kStaticScratchBytes)
+  const KappaLayout L = kappa_layout(lines, spec);
+  if (L.total > kStaticScratchBytes)
     return fail(RT_E_INVAL,
-                "rt_build_kappa_static: needs %zu bytes of scratch (16 B per line and T node, 16 B "
-                "per line, plus 32 B per line for host-resident lines), the static array holds %zu",
-                total, kStaticScratchBytes);
-  if (lines->memory == RT_MEM_HOST && n > 0) {
+                "rt_build_kappa_static: needs %zu bytes of scratch (16 B per line and T node, 32 B "
+                "for Voigt lines, 16 B per line, 32 B per 256 wavenumbers, plus 32 B per line for "
+                "host-resident lines), the static array holds %zu",
+                L.total, kStaticScratchBytes);
+  if (lines->memory == RT_MEM_HOST && lines->n > 0) {
     v = validate_host_lines(lines, spec);
     if (v != RT_OK) return v;
   }
   const size_t table = (size_t)spec->nT * (size_t)spec->n_nu;
-  if (n == 0) {
+  if (lines->n == 0) {
     if (!spec->accumulate) RT_CUDA_TRY(cudaMemsetAsync(kappa, 0, table * sizeof(float), st));
     return RT_OK;
   }
   void *scratch = nullptr;
   v = static_scratch_address(&scratch);
   if (v != RT_OK) return v;
-  char *base = reinterpret_cast<char *>(scratch);
-  const double *d_nu0 = lines->nu0, *d_S = lines->S_ref, *d_g = lines->gamma_ref, *d_E = lines->E_lower;
-  if (lines->memory == RT_MEM_HOST) {
-    double *d = reinterpret_cast<double *>(base);
-    RT_CUDA_TRY(cudaMemcpyAsync(d, lines->nu0, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    RT_CUDA_TRY(cudaMemcpyAsync(d + n, lines->S_ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    RT_CUDA_TRY(cudaMemcpyAsync(d + 2 * n, lines->gamma_ref, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    RT_CUDA_TRY(cudaMemcpyAsync(d + 3 * n, lines->E_lower, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    d_nu0 = d; d_S = d + n; d_g = d + 2 * n; d_E = d + 3 * n;
-  }
-  int4 *R = reinterpret_cast<int4 *>(base + off_R);
-  float4 *P = reinterpret_cast<float4 *>(base + off_P);
-
-  GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
-               lines->memory == RT_MEM_DEVICE ? 1 : 0, spec->points_per_line};
-  const int tb = 256;
-  k_line_geometry<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d_nu0, d_S, d_g, d_E, G, R,
-                                                                evals_out, status);
-  RT_CUDA_TRY(cudaGetLastError());
-  PrefParams Q;
-  Q.T_min = spec->T_min;
-  Q.T_max = spec->T_max;
-  Q.T_ref = lines->T_ref;
-  const double c2 = 100.0 * kH * kC / kKB;
-  Q.c2.hi = (float)c2;
-  Q.c2.lo = (float)(c2 - (double)Q.c2.hi);
-  Q.u_coef = (float)(spec->x_ref * spec->p_ref_atm * kAtm / kKB * 1e-6);
-  Q.p_ref = (float)spec->p_ref_atm;
-  Q.n_T = (float)lines->n_T;
-  Q.q_exp = (float)lines->q_exp;
-  Q.doppler = (float)(std::sqrt(2.0 * std::log(2.0) * kKB / (lines->mass_amu * kAmu)) / kC);
-  Q.inv_dnu = (float)(1.0 / spec->dnu);
-  Q.dnu = (float)spec->dnu;
-  Q.n_lines = n;
-  Q.nT = spec->nT;
-  Q.profile = spec->profile;
-  dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
-  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P);
-  RT_CUDA_TRY(cudaGetLastError());
-  return launch_kappa(P, R, n, spec, kappa, status, st);
+  return run_build(reinterpret_cast<char *>(scratch), L, lines, spec, kappa, evals_out, status, st);
 }
 
 }  // namespace rt

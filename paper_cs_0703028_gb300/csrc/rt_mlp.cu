@@ -70,9 +70,37 @@ __device__ __forceinline__ void normalise(const float *__restrict__ in, long lon
   }
 }
 
+// FP32 parameters used on the CUDA cores (layer 1, biases, head), staged once
+// per block so that each use is a shared-memory (float4) read.
+struct SmallParams {
+  float4 w1[kH];      // W1 rows
+  float b1[kH];
+  float b[3][kH];     // b2, b3, b4
+  float w5[kH];
+  float b5;
+};
+
+__device__ __forceinline__ void stage_small(SmallParams &S, const float *__restrict__ P) {
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
+    S.w1[c] = make_float4(P[oW1 + 4 * c], P[oW1 + 4 * c + 1], P[oW1 + 4 * c + 2], P[oW1 + 4 * c + 3]);
+    S.b1[c] = P[oB1 + c];
+    S.b[0][c] = P[oB2 + c];
+    S.b[1][c] = P[oB3 + c];
+    S.b[2][c] = P[oB4 + c];
+    S.w5[c] = P[oW5 + c];
+  }
+  if (threadIdx.x == 0) S.b5 = P[oB5];
+}
+
+__device__ __forceinline__ float layer1(const SmallParams &S, int c, const float (&u)[4]) {
+  const float4 w = S.w1[c];
+  return fmaf(w.w, u[3], fmaf(w.z, u[2], fmaf(w.y, u[1], fmaf(w.x, u[0], S.b1[c]))));
+}
+
 struct FwdSmem {
   uint16_t W[3][kTileElems];  // W2..W4, rows = out
   uint16_t A[kTileElems];     // current layer input, rows = samples
+  SmallParams sp;
   uint64_t bar_w, bar_mma;
   uint32_t tmem;
   float red[4];
@@ -96,6 +124,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tc::tmem_alloc(&S.tmem, kH);
+  stage_small(S.sp, P);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -114,9 +143,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int c = c0 + i;
-      float z = __ldg(P + oB1 + c);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) z = fmaf(__ldg(P + oW1 + c * 4 + k), u[k], z);
+      const float z = layer1(S.sp, c, u);
       if (TRAIN && valid) Z[(0 * n + row) * kH + c] = z;
       h[i] = z * sigmoid_fast(z);
     }
@@ -140,7 +167,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)(l & 1), kWaitLimit) ? 0 : 1;
     if (__syncthreads_or(timeout)) break;
     tc::fence_after_sync();
-    const float *bias = P + (l == 0 ? oB2 : (l == 1 ? oB3 : oB4));
+    const float *bias = S.sp.b[l];
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float acc[32];
@@ -151,10 +178,10 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int c = c0 + i + q;
-          const float z = acc[i + q] + __ldg(bias + c);
+          const float z = acc[i + q] + bias[c];
           if (TRAIN && valid) Z[((long long)(l + 1) * n + row) * kH + c] = z;
           h[q] = z * sigmoid_fast(z);
-          if (l == 2) y = fmaf(__ldg(P + oW5 + c), h[q], y);
+          if (l == 2) y = fmaf(S.sp.w5[c], h[q], y);
         }
         if (l < 2) {
           uint4 pk = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
@@ -167,7 +194,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
   if (timeout) {
     if (tid == 0) status_or(status, RT_DEV_TIMEOUT);
   } else {
-    y += __ldg(P + oB5);
+    y += S.sp.b5;
     if (TRAIN) {
       const float ts = valid ? (targets[row] - N.mean) / N.scale : 0.0f;
       const float r = valid ? (y - ts) : 0.0f;
@@ -412,6 +439,7 @@ constexpr int kWalkMlpThreads = 256;  // two 128-ray tiles share the resident we
 struct WalkMlpSmem {
   uint16_t W[3][kTileElems];  // W2..W4 (rows = out)
   uint16_t A[2][kTileElems];  // layer inputs of the two tiles
+  SmallParams sp;
   uint64_t bar_w, bar_mma;
   unsigned long long next;
   uint32_t tmem;
@@ -431,10 +459,7 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
     float h[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const int c = c0 + i;
-      float z = __ldg(P + oB1 + c);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) z = fmaf(__ldg(P + oW1 + c * 4 + k), u[k], z);
+      const float z = layer1(S.sp, c0 + i, u);
       h[i] = z * sigmoid_fast(z);
     }
     *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0)]) =
@@ -458,7 +483,7 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
     phase ^= 1u;
     if (__syncthreads_or(timeout)) return false;
     tc::fence_after_sync();
-    const float *bias = P + (l == 0 ? oB2 : (l == 1 ? oB3 : oB4));
+    const float *bias = S.sp.b[l];
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float acc[32];
@@ -469,9 +494,9 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int c = c0 + i + q;
-          const float z = acc[i + q] + __ldg(bias + c);
+          const float z = acc[i + q] + bias[c];
           h[q] = z * sigmoid_fast(z);
-          if (l == 2) y = fmaf(__ldg(P + oW5 + c), h[q], y);
+          if (l == 2) y = fmaf(S.sp.w5[c], h[q], y);
         }
         if (l < 2)
           *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0 + i)]) =
@@ -480,7 +505,7 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
       }
     }
   }
-  logk = N.mean + N.scale * (y + __ldg(P + oB5));
+  logk = N.mean + N.scale * (y + S.sp.b5);
   return true;
 }
 
@@ -502,6 +527,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
     S.next = begin;
   }
   if (warp == 0) tc::tmem_alloc(&S.tmem, 2 * kH);
+  stage_small(S.sp, P);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
