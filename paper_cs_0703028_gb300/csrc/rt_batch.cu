@@ -80,20 +80,26 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
     double em = 0.0, esc = 0.0;
     unsigned long long nsteps = 0;
     Ray R;
+    float4 cd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // data of the ray's current cell
     bool active = false;
     for (;;) {
       const unsigned idle = __ballot_sync(0xffffffffu, !active);
       if (next < last && (idle == 0xffffffffu || __popc(idle) >= kRefillIdleBatch)) {
         const unsigned rank = __popc(idle & ((1u << lane) - 1u));
         if (!active && next + rank < last) {
-          ray_init(W, cells, tab, next + rank, false, R);
+          ray_init(W, cells, tab, next + rank, false, R, &cd);
           active = true;
         }
         next += __popc(idle);
       }
       if (!__any_sync(0xffffffffu, active)) break;
-      if (active && ray_step(W, cell_kappa_t(cells[R.cell], tab, W.nT, R.j), D.absorbed, D.status,
-                             rec, R)) {
+      if (!active) continue;
+      const float kap = cell_kappa_t(cd, tab, W.nT, R.j);
+      float4 cdn = cd;
+      const bool done = ray_step<false>(W, kap, D.absorbed, D.status, rec, R, true,
+                                        [&](int c) { cdn = __ldg(cells + c); });
+      cd = cdn;
+      if (done) {
         em += (double)R.w;
         esc += (double)(R.w * R.trans);
         nsteps += (unsigned long long)R.nv;

@@ -52,6 +52,7 @@ __global__ void k_transpose(const float *__restrict__ in, int rows, long long co
   }
 }
 
+template <bool REC>
 __global__ void __launch_bounds__(kWalkThreads, 5)
 k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
        double *__restrict__ absorbed, double *__restrict__ scalars,
@@ -61,28 +62,36 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
   const unsigned long long wid = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   unsigned long long next = W.n_rays * wid / nwarps;
   const unsigned long long last = W.n_rays * (wid + 1) / nwarps;
-  const bool record = rec.cells != nullptr;
+  const bool record = REC;
   double em = 0.0, esc = 0.0;
   unsigned long long nsteps = 0;
   Ray R;
+  float4 cd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // data of the ray's current cell
   bool active = false;
   for (;;) {
     const unsigned idle = __ballot_sync(0xffffffffu, !active);
     if (next < last && (idle == 0xffffffffu || __popc(idle) >= kRefillIdle)) {
       const unsigned rank = __popc(idle & ((1u << lane) - 1u));
       if (!active && next + rank < last) {
-        ray_init(W, cells, tab, next + rank, record, R);
+        ray_init(W, cells, tab, next + rank, record, R, &cd);
         active = true;
       }
       next += __popc(idle);
     }
     if (!__any_sync(0xffffffffu, active)) break;
-    if (active && ray_step(W, cell_kappa_t(cells[R.cell], tab, W.nT, R.j), absorbed, status, rec, R)) {
+    if (!active) continue;
+    // the table value of this cell, then the next cell's data, both in flight
+    // while the step's arithmetic runs
+    const float kap = cell_kappa_t(cd, tab, W.nT, R.j);
+    float4 cdn = cd;
+    const bool done = ray_step<REC>(W, kap, absorbed, status, rec, R, true, [&](int c) { cdn = __ldg(cells + c); });
+    cd = cdn;
+    if (done) {
       const float out = R.w * R.trans;
       em += (double)R.w;
       esc += (double)out;
       nsteps += (unsigned long long)R.nv;
-      if (R.row >= 0) {
+      if (REC && R.row >= 0) {
         rec.nvis[R.row] = R.nv;
         if (rec.weight) rec.weight[R.row] = R.w;
         if (rec.escaped) rec.escaped[R.row] = out;
@@ -260,15 +269,21 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   int dev = 0, sms = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const bool rec = rp.cells != nullptr;
   int per_sm = 0;
-  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk, kWalkThreads, 0));
+  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, rec ? k_walk<true> : k_walk<false>, kWalkThreads, 0));
   if (per_sm < 1) per_sm = 1;
   // persistent warps, each with a contiguous ray range of at least 64 rays
   unsigned long long want = (n_rays + 64ull * (kWalkThreads / 32) - 1) / (64ull * (kWalkThreads / 32));
   const unsigned long long cap = (unsigned long long)sms * (unsigned long long)per_sm;
   const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-  k_walk<<<blocks, kWalkThreads, 0, st>>>(cells, tabt, W, tally->absorbed, tally->scalars,
-                                          tally->steps, tally->status, rp);
+  if (rec)
+    k_walk<true><<<blocks, kWalkThreads, 0, st>>>(cells, tabt, W, tally->absorbed, tally->scalars,
+                                                  tally->steps, tally->status, rp);
+  else
+    k_walk<false><<<blocks, kWalkThreads, 0, st>>>(cells, tabt, W, tally->absorbed, tally->scalars,
+                                                   tally->steps, tally->status, rp);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
