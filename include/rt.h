@@ -205,7 +205,7 @@ rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *
  *   __device__ array that every GPU loading the library holds until the process
  *   exits); the call allocates and frees nothing.
  * Limit: 16 B per (T node, line) for Lorentz lines, 32 B for Voigt lines, + 16 B
- *   per line + 32 B per 256 wavenumbers, plus 32 B per line when the lines are
+ *   per line + 48 B per 256 wavenumbers, plus 32 B per line when the lines are
  *   host-resident, at most 32 MiB in all (about 2 million Lorentz or 1 million
  *   Voigt (T node, line) pairs, e.g. 64 T nodes x 15,000 Voigt lines).  Larger
  *   inputs return RT_E_INVAL with the required size before any work is queued.

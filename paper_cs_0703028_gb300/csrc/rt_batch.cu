@@ -56,22 +56,23 @@ __global__ void __launch_bounds__(256, 4)
 k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_off, int n_encl,
              long long n_items, int rays_per_item, const float4 *__restrict__ cells_all,
              const float *__restrict__ tab, unsigned long long *__restrict__ counter) {
-  // the current item's walk parameters, one slot per warp (read like the constant bank)
-  __shared__ __align__(16) WalkParams s_w[8];
+  // the current item's enclosure (walk parameters and tally pointers), one slot
+  // per warp, read like the constant bank
+  __shared__ __align__(16) EnclDev s_e[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const RecordPtrs rec{nullptr, nullptr, nullptr, nullptr, nullptr};
-  const WalkParams &W = s_w[warp];
+  const EnclDev &D = s_e[warp];
+  const WalkParams &W = D.W;
   for (;;) {
     unsigned long long it = 0;
     if (lane == 0) it = atomicAdd(counter, 1ull);
     it = __shfl_sync(0xffffffffu, it, 0);
     if ((long long)it >= n_items) break;
     const int e = find_segment(item_off, n_encl, (long long)it);
-    const EnclDev &D = E[e];
     {
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(&D.W);
-      uint32_t *dst = reinterpret_cast<uint32_t *>(&s_w[warp]);
-      for (int w = lane; w < (int)(sizeof(WalkParams) / 4); w += 32) dst[w] = src[w];
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(E + e);
+      uint32_t *dst = reinterpret_cast<uint32_t *>(&s_e[warp]);
+      for (int w = lane; w < (int)(sizeof(EnclDev) / 4); w += 32) dst[w] = src[w];
       __syncwarp();
     }
     const float4 *cells = cells_all + D.cell_off;

@@ -19,6 +19,7 @@
 //                     Kahan-sums over lines in ascending nu0.
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "rt_common.cuh"
 
@@ -29,7 +30,7 @@ constexpr int kPtsPerThread = 8;
 constexpr int kTilePts = 32 * kPtsPerThread;  // 256 wavenumbers per block, one warp per T node
 constexpr int kMaxTPerBlock = 8;              // warps (T nodes) per block
 constexpr int kChunk = 64;                    // lines per staged chunk
-constexpr int kGroup = 4;                     // fast-path lines summed before one compensated add
+constexpr int kGroup = 8;                     // fast-path lines summed before one compensated add
 constexpr unsigned kWaitLimit = 1u << 22;                // bounded mbarrier waits
 
 // CODATA 2018 (SI); derived quantities are formed on the host in binary64.
@@ -110,12 +111,16 @@ __global__ void k_line_geometry(const double *__restrict__ nu0, const double *__
   }
 }
 
-__global__ void k_prefactor(const double *__restrict__ nu0, const double *__restrict__ S,
-                            const double *__restrict__ g, const double *__restrict__ E,
-                            PrefParams Q, float4 *__restrict__ Pout, float4 *__restrict__ P2out) {
-  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y;
-  if (l >= Q.n_lines) return;
+// Eq. (S) times the number density, and the profile's coefficients, for line l
+// at T node k.  Voigt: P = {c0, s dnu, y^2, c2}, P2 = {c3, c4, near half-width, 0}
+// with the far-wing series c0 t + c1 t^2 + c2 t^3 + c3 t^4 + c4 t^5 (c1 = 1.5 c0).
+// Returns the far-zone distance of the line in grid units (float bits): beyond it
+// the t^4 and t^5 terms are below 2^-24 of the value (27 y^2 t^3 <= 2^-24 with
+// t <= 1/x^2), so a degree-2 series is within one binary32 rounding of the full one.
+__device__ __forceinline__ unsigned prefactor_one(const double *__restrict__ nu0, const double *__restrict__ S,
+                                                  const double *__restrict__ g, const double *__restrict__ E,
+                                                  const PrefParams &Q, float4 *__restrict__ Pout,
+                                                  float4 *__restrict__ P2out, long long l, int k) {
   // T_k = T_min + k (T_max - T_min) / (nT - 1) and 1/T_k in double-float
   df Tk = df_from_double(Q.T_min);
   if (Q.nT > 1) {
@@ -139,6 +144,7 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
   const float A = (Q.u_coef * iTf) * S_T;  // u(T) S(T), cm^-1 per unit profile
   const float gam = __double2float_rn(g[l]) * Q.p_ref * powf(tr, Q.n_T);
   float4 out;
+  unsigned far = 0;
   if (Q.profile == RT_PROFILE_LORENTZ) {
     const float gg = gam * Q.inv_dnu;  // half-width in grid units
     out = make_float4(A * gg * (float)(1.0 / kPi) * Q.inv_dnu, gg * gg, 0.0f, 0.0f);
@@ -152,12 +158,36 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
     const float u_near = sqrtf(fmaxf(400.0f - y2, 0.0f)) / sd;
     // far wing: c0 t (1 + 1.5 t + (3.75 - 2 y^2) t^2 - 15 y^2 t^3 + 12 y^4 t^4), t = 1/|z|^2
     const float c0 = A * s * (float)(1.0 / kPi) * y;
-    out = make_float4(c0, sd, y2, 1.5f * c0);
-    P2out[(long long)k * Q.n_lines + l] =
-        make_float4(__fmaf_rn(-2.0f, y2, 3.75f) * c0, -15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near);
+    out = make_float4(c0, sd, y2, __fmaf_rn(-2.0f, y2, 3.75f) * c0);
+    P2out[(long long)k * Q.n_lines + l] = make_float4(-15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near, 0.0f);
+    // (27 y^2 / 2^-24)^(1/6) = 27.66 y^(1/3), with 5 % margin, in grid units
+    const float dfar = 29.1f * cbrtf(y) / sd;
+    far = (dfar >= 0.0f && dfar < 1e9f) ? __float_as_uint(dfar) : __float_as_uint(1e9f);
   }
   Pout[(long long)k * Q.n_lines + l] = out;
+  return far;
 }
+
+__global__ void k_prefactor(const double *__restrict__ nu0, const double *__restrict__ S,
+                            const double *__restrict__ g, const double *__restrict__ E,
+                            PrefParams Q, float4 *__restrict__ Pout, float4 *__restrict__ P2out,
+                            unsigned *__restrict__ far_bits) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  unsigned fb = 0;  // this line's far-zone distance (grid units, float bits)
+  if (l < Q.n_lines) fb = prefactor_one(nu0, S, g, E, Q, Pout, P2out, l, k);
+  // block maximum, one atomic per block (non-negative floats order like their bits)
+  __shared__ unsigned s_max[32];
+  fb = __reduce_max_sync(0xffffffffu, fb);
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = fb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
+    if (m) atomicMax(far_bits, m);
+  }
+}
+
 
 // ---- bulk asynchronous copies global -> shared, completed on an mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -210,32 +240,70 @@ __device__ __forceinline__ long long lower_bound_c(const int4 *R, long long n, l
   return a;
 }
 
+// Kinds of line ranges within a tile (see k_tile_lines).
+enum SegKind : int { kSegGeneral = 0, kSegFar = 1, kSegFast = 2, kSegFarMasked = 3 };
+constexpr int kMaxSegs = 8;
+
 // Per tile of kTilePts wavenumbers [jw0, jw0 + kTilePts): the lines [lb, ub)
-// whose windows reach it and two fast sub-ranges.  Windows and centres are
-// monotone in the (sorted) line index, so each set is an index range:
+// whose windows reach it, split into ranges by kind.  Windows and centres are
+// monotone in the (sorted) line index, so every set below is an index range:
 //   cover : j_lo <= jw0 and j_hi >= jw0 + kTilePts - 1 (no masking needed);
 //   near  : j_c within W + 4 grid points of the tile, W bounding the near-centre
-//           half-width of every line (lines outside it have no point |z| < 20).
-// Fast = cover minus near; out[2t] = {lb, ub, fa0, fb0}, out[2t+1] = {fa1, fb1}.
+//           half-width of every line (lines outside it have no point |z| < 20);
+//   far   : j_c more than D grid points from the tile, D >= W + 4 bounding every
+//           line's far-zone distance (degree-2 far-wing series).
+// Kinds: covering lines are far, fast (degree-4 series) or, when near, general;
+// partially covering lines are far-masked when far, else general.
+// out[3t] = {lb, ub, nseg, kinds (4 bits each)}, out[3t+1], out[3t+2] = segment ends.
 __global__ void k_tile_lines(const int4 *__restrict__ R, long long n, long long n_nu, int W,
-                             long long n_tiles, int4 *__restrict__ out) {
+                             const unsigned *__restrict__ far_bits, long long n_tiles,
+                             int4 *__restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
+  const float dfar = __uint_as_float(*far_bits);
+  const long long D = max((long long)W + 4, (long long)ceilf(fminf(dfar, 1e9f)) + 2);
   const long long jw0 = t * kTilePts, jw1 = jw0 + kTilePts - 1;
   const long long jend = min(jw0 + (long long)kTilePts, n_nu);
   const long long lb = lower_bound_hi(R, n, (int)jw0);
   const long long ub = max(lb, lower_bound_lo(R, n, (int)jend));
-  const long long ca = lower_bound_hi(R, n, (int)jw1);
-  const long long cb = lower_bound_lo(R, n, (int)(jw0 + 1));
-  const long long na = lower_bound_c(R, n, jw0 - W - 4);
-  const long long nb = lower_bound_c(R, n, jw1 + W + 5);
-  auto clampr = [&](long long v) { return min(max(v, lb), ub); };
-  const long long fa0 = clampr(ca);
-  const long long fb0 = clampr(max(fa0, min(cb, na)));
-  const long long fa1 = clampr(max(fb0, max(ca, nb)));
-  const long long fb1 = clampr(max(fa1, cb));
-  out[2 * t] = make_int4((int)lb, (int)ub, (int)fa0, (int)fb0);
-  out[2 * t + 1] = make_int4((int)fa1, (int)fb1, 0, 0);
+  auto cl = [&](long long v) { return min(max(v, lb), ub); };
+  const long long ca = cl(lower_bound_hi(R, n, (int)jw1));       // cover = [ca, cb)
+  const long long cb = cl(lower_bound_lo(R, n, (int)(jw0 + 1)));
+  const long long fa = cl(lower_bound_c(R, n, jw0 - D));          // far: l < fa or l >= fb
+  const long long na = cl(lower_bound_c(R, n, jw0 - W - 4));      // near: [na, nb)
+  const long long nb = cl(lower_bound_c(R, n, jw1 + W + 5));
+  const long long fb = cl(lower_bound_c(R, n, jw1 + D + 1));
+  auto kind = [&](long long l) -> int {
+    if (l < ca) return l < fa ? kSegFarMasked : kSegGeneral;
+    if (l >= cb) return l >= fb ? kSegFarMasked : kSegGeneral;
+    if (l < fa || l >= fb) return kSegFar;
+    if (l < na || l >= nb) return kSegFast;
+    return kSegGeneral;
+  };
+  // the change points, sorted; one segment per maximal run of equal kind
+  long long b[7] = {ca, cb, fa, na, nb, fb, ub};
+  for (int i = 1; i < 6; ++i)
+    for (int j = i; j > 0 && b[j - 1] > b[j]; --j) {
+      const long long x = b[j - 1]; b[j - 1] = b[j]; b[j] = x;
+    }
+  int ends[kMaxSegs], nseg = 0, kinds = 0;
+  long long start = lb;
+  for (int i = 0; i < 7; ++i) {
+    const long long e = b[i];
+    if (e <= start) continue;
+    const int kd = kind(start);
+    if (nseg > 0 && ((kinds >> (4 * (nseg - 1))) & 15) == kd) {
+      ends[nseg - 1] = (int)e;
+    } else {
+      kinds |= kd << (4 * nseg);
+      ends[nseg++] = (int)e;
+    }
+    start = e;
+  }
+  for (int i = nseg; i < kMaxSegs; ++i) ends[i] = (int)ub;
+  out[3 * t] = make_int4((int)lb, (int)ub, nseg, kinds);
+  out[3 * t + 1] = make_int4(ends[0], ends[1], ends[2], ends[3]);
+  out[3 * t + 2] = make_int4(ends[4], ends[5], ends[6], ends[7]);
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -289,9 +357,16 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
   const int jw0 = (int)j0, jw1 = jw0 + kTilePts - 1;
   const int jt = jw0 + lane * kPtsPerThread;
 
-  const int4 ta = __ldg(tiles + 2 * blockIdx.x), tb = __ldg(tiles + 2 * blockIdx.x + 1);
+  __shared__ int s_end[kMaxSegs];
+  __shared__ unsigned char s_kind[kMaxSegs];
+  const int4 ta = __ldg(tiles + 3 * blockIdx.x);
   const int lb = ta.x, ub = ta.y;
-  const int seg0 = ta.z, seg1 = ta.w, seg2 = tb.x, seg3 = tb.y;  // fast: [seg0, seg1), [seg2, seg3)
+  if (threadIdx.x < kMaxSegs) {
+    const int4 e = __ldg(tiles + 3 * blockIdx.x + 1 + (threadIdx.x >> 2));
+    const int q = threadIdx.x & 3;
+    s_end[threadIdx.x] = q == 0 ? e.x : (q == 1 ? e.y : (q == 2 ? e.z : e.w));
+    s_kind[threadIdx.x] = (unsigned char)((ta.w >> (4 * threadIdx.x)) & 15);
+  }
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -321,6 +396,7 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
     if (nchunks > 1) issue(1);
   }
   const int wsel = min(warp, nk - 1);
+  int seg = 0;  // current segment, carried across chunks
   bool aborted = false;
   for (int c = 0; c < nchunks; ++c) {
     const int b = c & 1;
@@ -341,8 +417,12 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
     const int l0 = lb + c * kChunk;
     const int cnt = min(kChunk, ub - l0);
 
-    // fast path: g[q] += value of line i at the lane's points (or = when first)
-    auto fast_line = [&](int i, float (&g)[kPtsPerThread], bool first) {
+    // fast paths: g[q] += value of line i at the lane's points (or = when first).
+    // DEG 4: full far-wing series; DEG 2: far lines (t^3 and t^4 terms negligible);
+    // MASK: zero outside the line's window.
+    auto fast_line = [&](auto deg, auto mask, int i, float (&g)[kPtsPerThread], bool first) {
+      constexpr int DEG = decltype(deg)::value;
+      constexpr bool MASK = decltype(mask)::value;
       const int4 r = sR[b][i];
       const float4 p = sP[b][0][wsel][i];
       const float ul = (float)(jt - r.z) + __int_as_float(r.w);
@@ -350,36 +430,44 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
 #pragma unroll
         for (int q = 0; q < kPtsPerThread; ++q) {
           const float u = __fadd_rn(ul, (float)q);
-          const float rr = rcp_approx(__fmaf_rn(u, u, p.y));
+          float rr = rcp_approx(__fmaf_rn(u, u, p.y));
+          if (MASK && (jt + q < r.x || jt + q > r.y)) rr = 0.0f;
           g[q] = first ? p.x * rr : __fmaf_rn(p.x, rr, g[q]);
         }
       } else {
-        const float4 p2 = sP[b][kPSets - 1][wsel][i];
+        const float c1 = 1.5f * p.x;
         const float xt = p.y * ul;
+        float4 p2 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (DEG == 4) p2 = sP[b][kPSets - 1][wsel][i];
 #pragma unroll
         for (int q = 0; q < kPtsPerThread; ++q) {
           const float x = __fmaf_rn(p.y, (float)q, xt);
           const float t = rcp_approx(__fmaf_rn(x, x, p.z));
-          const float h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.z, p2.y), p2.x), p.w), p.x);
+          float h;
+          if (DEG == 4)
+            h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.y, p2.x), p.w), c1), p.x);
+          else
+            h = __fmaf_rn(t, __fmaf_rn(t, p.w, c1), p.x);
+          if (MASK && (jt + q < r.x || jt + q > r.y)) h = 0.0f;
           g[q] = first ? t * h : __fmaf_rn(t, h, g[q]);
         }
       }
     };
-    auto run_fast = [&](int i, int i1) {
+    auto run_fast = [&](auto deg, auto mask, int i, int i1) {
 #pragma unroll 1
       for (; i + kGroup <= i1; i += kGroup) {
         float g[kPtsPerThread];
-        fast_line(i, g, true);
+        fast_line(deg, mask, i, g, true);
 #pragma unroll
-        for (int e = 1; e < kGroup; ++e) fast_line(i + e, g, false);
+        for (int e = 1; e < kGroup; ++e) fast_line(deg, mask, i + e, g, false);
 #pragma unroll
         for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], g[q]);
       }
       if (i < i1) {
         float g[kPtsPerThread];
-        fast_line(i, g, true);
+        fast_line(deg, mask, i, g, true);
 #pragma unroll 1
-        for (int e = i + 1; e < i1; ++e) fast_line(e, g, false);
+        for (int e = i + 1; e < i1; ++e) fast_line(deg, mask, e, g, false);
 #pragma unroll
         for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], g[q]);
       }
@@ -406,12 +494,13 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
           for (int q = 0; q < kPtsPerThread; ++q) {
             xs[q] = __fmaf_rn(p.y, (float)q, xt);
             const float t = rcp_approx(__fmaf_rn(xs[q], xs[q], y2));
-            const float h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.z, p2.y), p2.x), p.w), p.x);
+            const float h =
+                __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.y, p2.x), p.w), 1.5f * p.x), p.x);
             v[q] = t * h;
           }
           // warp-uniform: the tile's offsets [fu, fu + kTilePts) meet the near region
           const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);
-          if (fu < p2.w + 1.0f && fu + (float)kTilePts > -p2.w - 1.0f) {
+          if (fu < p2.z + 1.0f && fu + (float)kTilePts > -p2.z - 1.0f) {
             // compact this warp's near-centre points so one pass of the lanes evaluates them
             unsigned nearbits = 0;
 #pragma unroll
@@ -477,16 +566,22 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
       }
     };
 
-    // the chunk [l0, l0 + cnt) split at the fast sub-range boundaries (block-uniform)
+    // the chunk [l0, l0 + cnt) split at the tile's segment ends (block-uniform)
     int i = 0;
 #pragma unroll 1
     while (i < cnt) {
       const int l = l0 + i;
-      // s = number of boundaries at or below l (odd: inside a fast sub-range)
-      const int s = (l >= seg0) + (l >= seg1) + (l >= seg2) + (l >= seg3);
-      const int end = s == 0 ? seg0 : (s == 1 ? seg1 : (s == 2 ? seg2 : (s == 3 ? seg3 : ub)));
-      const int i1 = min(cnt, end - l0);
-      if (s & 1) run_fast(i, i1); else run_general(i, i1);
+      while (s_end[seg] <= l) ++seg;  // the last segment ends at ub > l
+      const int i1 = min(cnt, s_end[seg] - l0);
+      const int kd = s_kind[seg];
+      if (kd == kSegFar)
+        run_fast(std::integral_constant<int, 2>(), std::false_type(), i, i1);
+      else if (kd == kSegFast)
+        run_fast(std::integral_constant<int, 4>(), std::false_type(), i, i1);
+      else if (kd == kSegFarMasked)
+        run_fast(std::integral_constant<int, 2>(), std::true_type(), i, i1);
+      else
+        run_general(i, i1);
       i = i1;
     }
     __syncthreads();  // every warp is done with buffer b
@@ -517,9 +612,10 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
 
 int g_kappa_tpb = kMaxTPerBlock;
 
-rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *tiles, long long n,
-                       const rt_spectral *spec, double nu_abs_max, double mass_amu, float *kappa,
-                       uint32_t *status, cudaStream_t st) {
+rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *tiles,
+                       const unsigned *far_bits, long long n, const rt_spectral *spec,
+                       double nu_abs_max, double mass_amu, float *kappa, uint32_t *status,
+                       cudaStream_t st) {
   static WeidCoef wc;
   static std::once_flag wc_once;
   std::call_once(wc_once, [] { weideman_coefficients(&wc); });
@@ -533,7 +629,8 @@ rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *t
     W = (!(w < (double)(1 << 28))) ? (1 << 28) : (int)std::ceil(w);
   }
   const long long n_tiles = (spec->n_nu + kTilePts - 1) / kTilePts;
-  k_tile_lines<<<(unsigned)((n_tiles + 127) / 128), 128, 0, st>>>(R, n, spec->n_nu, W, n_tiles, tiles);
+  k_tile_lines<<<(unsigned)((n_tiles + 127) / 128), 128, 0, st>>>(R, n, spec->n_nu, W, far_bits,
+                                                                    n_tiles, tiles);
   RT_CUDA_TRY(cudaGetLastError());
   const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
   int want = g_kappa_tpb;
@@ -608,9 +705,9 @@ rt_status launch_line_geometry(const double *nu0, const double *S, const double 
 namespace {
 
 // Scratch of one build: [line arrays if host-resident][R: n int4][P: nT n float4]
-// [P2: nT n float4, Voigt][tile ranges: 2 int4 per 256-point tile]
+// [P2: nT n float4, Voigt][tile segments: 3 int4 per 256-point tile][far-zone bound]
 struct KappaLayout {
-  size_t off_R, off_P, off_P2, off_tiles, total;
+  size_t off_R, off_P, off_P2, off_tiles, off_far, total;
 };
 
 KappaLayout kappa_layout(const rt_lines *lines, const rt_spectral *spec) {
@@ -623,7 +720,8 @@ KappaLayout kappa_layout(const rt_lines *lines, const rt_spectral *spec) {
   L.off_P2 = up(L.off_P + pn);
   L.off_tiles = up(L.off_P2 + (spec->profile == RT_PROFILE_VOIGT ? pn : 0));
   const size_t n_tiles = (size_t)((spec->n_nu + kTilePts - 1) / kTilePts);
-  L.total = L.off_tiles + n_tiles * 2 * sizeof(int4);
+  L.off_far = up(L.off_tiles + n_tiles * 3 * sizeof(int4));
+  L.total = L.off_far + 256;
   return L;
 }
 
@@ -662,6 +760,7 @@ rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, con
   float4 *P = reinterpret_cast<float4 *>(base + L.off_P);
   float4 *P2 = reinterpret_cast<float4 *>(base + L.off_P2);
   int4 *tiles = reinterpret_cast<int4 *>(base + L.off_tiles);
+  unsigned *far_bits = reinterpret_cast<unsigned *>(base + L.off_far);
 
   GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
                lines->memory == RT_MEM_DEVICE ? 1 : 0, spec->points_per_line};
@@ -688,7 +787,8 @@ rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, con
   Q.nT = spec->nT;
   Q.profile = spec->profile;
   dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
-  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P, P2);
+  RT_CUDA_TRY(cudaMemsetAsync(far_bits, 0, sizeof(unsigned), st));
+  k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P, P2, far_bits);
   RT_CUDA_TRY(cudaGetLastError());
 
   // largest |nu0| of a line whose window (cutoff or fixed points) reaches the grid
@@ -696,7 +796,7 @@ rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, con
   const double nu_abs_max =
       std::fmax(std::fabs(spec->nu_min - reach),
                 std::fabs(spec->nu_min + (double)spec->n_nu * spec->dnu + reach));
-  return launch_kappa(P, P2, R, tiles, n, spec, nu_abs_max, lines->mass_amu, kappa, status, st);
+  return launch_kappa(P, P2, R, tiles, far_bits, n, spec, nu_abs_max, lines->mass_amu, kappa, status, st);
 }
 
 }  // namespace
@@ -755,7 +855,7 @@ rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec
   if (L.total > kStaticScratchBytes)
     return fail(RT_E_INVAL,
                 "rt_build_kappa_static: needs %zu bytes of scratch (16 B per line and T node, 32 B "
-                "for Voigt lines, 16 B per line, 32 B per 256 wavenumbers, plus 32 B per line for "
+                "for Voigt lines, 16 B per line, 48 B per 256 wavenumbers, plus 32 B per line for "
                 "host-resident lines), the static array holds %zu",
                 L.total, kStaticScratchBytes);
   if (lines->memory == RT_MEM_HOST && lines->n > 0) {
