@@ -52,6 +52,7 @@ __global__ void k_cell_prep_batch(const EnclDev *__restrict__ E, const long long
 
 constexpr int kRefillIdleBatch = 16;
 
+template <int TAB>
 __global__ void __launch_bounds__(256, 4)
 k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_off, int n_encl,
              long long n_items, int rays_per_item, const float4 *__restrict__ cells_all,
@@ -95,7 +96,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
       }
       if (!__any_sync(0xffffffffu, active)) break;
       if (!active) continue;
-      const float kap = cell_kappa_t(cd, tab, W.nT, R.j);
+      const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
       float4 cdn = cd;
       const bool done = ray_step<false>(W, kap, D.absorbed, D.status, rec, R, true,
                                         [&](int c) { cdn = __ldg(cells + c); });
@@ -134,7 +135,8 @@ struct rt_batch {
   long long *d_item_off = nullptr, *d_cell_off = nullptr;
   unsigned long long *d_counter = nullptr;
   float4 *d_cells = nullptr;
-  float *d_tabt = nullptr;  // wavenumber-major copy of the table
+  float *d_tabt = nullptr;  // the walk's copy of the table (wavenumber-major or node pairs)
+  int layout = 1;
   int nT = 0;
   long long n_nu = 0;
   void *mem = nullptr;
@@ -168,7 +170,7 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
       snprintf(msg, sizeof(msg), "%s", rt_last_error());
       return fail(v, "enclosure %d: %s", e, msg);
     }
-    H[e].W.nu_major = 1;
+    H[e].W.nu_major = walk_table_layout(spec->nT, spec->n_nu);
     H[e].T = encl[e].grid.T;
     H[e].p = encl[e].grid.p_atm;
     H[e].x = encl[e].grid.x;
@@ -192,7 +194,8 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
   const size_t o_cnt = (o_cell + 8 * ((size_t)n_encl + 1) + 255) & ~size_t(255);
   const size_t o_cells = o_cnt + 256;
   const size_t o_tabt = (o_cells + sizeof(float4) * (size_t)cells + 255) & ~size_t(255);
-  const size_t total = o_tabt + sizeof(float) * (size_t)spec->nT * (size_t)spec->n_nu;
+  const int layout = walk_table_layout(spec->nT, spec->n_nu);
+  const size_t total = o_tabt + walk_table_bytes(layout, spec->nT, spec->n_nu);
   rt_batch *B = new rt_batch();
   cudaError_t ce = async ? cudaMallocAsync(&B->mem, total, st) : cudaMalloc(&B->mem, total);
   if (ce != cudaSuccess) {
@@ -210,6 +213,7 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
   B->d_tabt = (float *)(base + o_tabt);
   B->nT = spec->nT;
   B->n_nu = spec->n_nu;
+  B->layout = layout;
   B->n_encl = n_encl;
   B->n_items = items;
   B->total_cells = cells;
@@ -229,7 +233,8 @@ static rt_status batch_build(int32_t n_encl, const rt_enclosure *encl, const rt_
   int dev = 0, sms = 0, per_sm = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_batch, threads, 0));
+  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, layout == 2 ? k_walk_batch<2> : k_walk_batch<1>, threads, 0));
   if (per_sm < 1) per_sm = 1;
   B->blocks = (unsigned)(sms * per_sm);
   *out = B;
@@ -245,10 +250,11 @@ static rt_status batch_run(rt_batch *B, const float *kappa, cudaStream_t st) {
         B->d_encl, B->d_cell_off, B->n_encl, B->total_cells, B->C, B->d_cells);
     RT_CUDA_TRY(cudaGetLastError());
   }
-  v = launch_transpose(kappa, B->nT, B->n_nu, B->d_tabt, st);
+  v = launch_walk_table(B->layout, kappa, B->nT, B->n_nu, B->d_tabt, st);
   if (v != RT_OK) return v;
-  k_walk_batch<<<B->blocks, B->threads, 0, st>>>(B->d_encl, B->d_item_off, B->n_encl, B->n_items,
-                                                 B->rays_per_item, B->d_cells, B->d_tabt, B->d_counter);
+  auto kern = B->layout == 2 ? k_walk_batch<2> : k_walk_batch<1>;
+  kern<<<B->blocks, B->threads, 0, st>>>(B->d_encl, B->d_item_off, B->n_encl, B->n_items,
+                                         B->rays_per_item, B->d_cells, B->d_tabt, B->d_counter);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }

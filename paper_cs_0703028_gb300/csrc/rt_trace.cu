@@ -52,7 +52,27 @@ __global__ void k_transpose(const float *__restrict__ in, int rows, long long co
   }
 }
 
-template <bool REC>
+// [nT][n_nu] -> node pairs out[j * (nT - 1) + k] = {in[k][j], in[k + 1][j]}: each block
+// stages kPairRows + 1 rows of 32 wavenumbers and writes the pairs wavenumber by wavenumber.
+constexpr int kPairRows = 64;
+__global__ void k_pair_table(const float *__restrict__ in, int nT, long long n_nu, float2 *__restrict__ out) {
+  __shared__ float t[kPairRows + 1][33];
+  const long long j0 = (long long)blockIdx.x * 32;
+  const int k0 = blockIdx.y * kPairRows;
+  const int rows = min(kPairRows + 1, nT - k0);
+  for (int idx = threadIdx.x; idx < rows * 32; idx += blockDim.x) {
+    const int r = idx >> 5, c = idx & 31;
+    if (j0 + c < n_nu) t[r][c] = in[(long long)(k0 + r) * n_nu + j0 + c];
+  }
+  __syncthreads();
+  const int np = rows - 1;
+  for (int idx = threadIdx.x; idx < np * 32; idx += blockDim.x) {
+    const int c = idx / np, r = idx - c * np;
+    if (j0 + c < n_nu) out[(j0 + c) * (long long)(nT - 1) + k0 + r] = make_float2(t[r][c], t[r + 1][c]);
+  }
+}
+
+template <bool REC, int TAB>
 __global__ void __launch_bounds__(kWalkThreads, 5)
 k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
        double *__restrict__ absorbed, double *__restrict__ scalars,
@@ -82,7 +102,7 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
     if (!active) continue;
     // the table value of this cell, then the next cell's data, both in flight
     // while the step's arithmetic runs
-    const float kap = cell_kappa_t(cd, tab, W.nT, R.j);
+    const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
     float4 cdn = cd;
     const bool done = ray_step<REC>(W, kap, absorbed, status, rec, R, true, [&](int c) { cdn = __ldg(cells + c); });
     cd = cdn;
@@ -221,6 +241,22 @@ rt_status launch_transpose(const float *tab, int nT, long long n_nu, float *tabt
   return RT_OK;
 }
 
+int walk_table_layout(int nT, long long n_nu) {
+  return (nT >= 2 && (size_t)n_nu * (size_t)(nT - 1) * 8 <= kPairTableBytes) ? 2 : 1;
+}
+
+size_t walk_table_bytes(int layout, int nT, long long n_nu) {
+  return layout == 2 ? (size_t)n_nu * (size_t)(nT - 1) * 8 : (size_t)n_nu * (size_t)nT * 4;
+}
+
+rt_status launch_walk_table(int layout, const float *tab, int nT, long long n_nu, float *out, cudaStream_t st) {
+  if (layout != 2) return launch_transpose(tab, nT, n_nu, out, st);
+  dim3 g((unsigned)((n_nu + 31) / 32), (unsigned)((nT - 1 + kPairRows - 1) / kPairRows));
+  k_pair_table<<<g, 256, 0, st>>>(tab, nT, n_nu, reinterpret_cast<float2 *>(out));
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
 CellParams cell_params(const rt_spectral *spec, long long ncells, int has_px) {
   CellParams C;
   C.ncells = ncells;
@@ -256,34 +292,32 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   if (v != RT_OK) return v;
   if (n_rays == 0) return RT_OK;
   Scratch scr;
+  const int layout = walk_table_layout(spec->nT, spec->n_nu);
   const size_t cbytes = ((size_t)W.ncells * sizeof(float4) + 255) & ~size_t(255);
-  v = scr.alloc(cbytes + (size_t)spec->nT * (size_t)spec->n_nu * sizeof(float), st);
+  v = scr.alloc(cbytes + walk_table_bytes(layout, spec->nT, spec->n_nu), st);
   if (v != RT_OK) return v;
   float4 *cells = scr.as<float4>();
-  float *tabt = reinterpret_cast<float *>(scr.as<char>() + cbytes);
+  float *tabw = reinterpret_cast<float *>(scr.as<char>() + cbytes);
   v = cell_prep(grid, spec, cells, tally->status, st);
   if (v != RT_OK) return v;
-  v = launch_transpose(kappa, spec->nT, spec->n_nu, tabt, st);
+  v = launch_walk_table(layout, kappa, spec->nT, spec->n_nu, tabw, st);
   if (v != RT_OK) return v;
-  W.nu_major = 1;
+  W.nu_major = layout;
   int dev = 0, sms = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const bool rec = rp.cells != nullptr;
+  auto kern = rec ? (layout == 2 ? k_walk<true, 2> : k_walk<true, 1>)
+                  : (layout == 2 ? k_walk<false, 2> : k_walk<false, 1>);
   int per_sm = 0;
-  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, rec ? k_walk<true> : k_walk<false>, kWalkThreads, 0));
+  RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkThreads, 0));
   if (per_sm < 1) per_sm = 1;
   // persistent warps, each with a contiguous ray range of at least 64 rays
   unsigned long long want = (n_rays + 64ull * (kWalkThreads / 32) - 1) / (64ull * (kWalkThreads / 32));
   const unsigned long long cap = (unsigned long long)sms * (unsigned long long)per_sm;
   const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-  if (rec)
-    k_walk<true><<<blocks, kWalkThreads, 0, st>>>(cells, tabt, W, tally->absorbed, tally->scalars,
-                                                  tally->steps, tally->status, rp);
-  else
-    k_walk<false><<<blocks, kWalkThreads, 0, st>>>(cells, tabt, W, tally->absorbed, tally->scalars,
-                                                   tally->steps, tally->status, rp);
+  kern<<<blocks, kWalkThreads, 0, st>>>(cells, tabw, W, tally->absorbed, tally->scalars, tally->steps,
+                                        tally->status, rp);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }

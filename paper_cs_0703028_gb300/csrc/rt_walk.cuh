@@ -47,7 +47,7 @@ struct WalkParams {
   float h[3];
   long long ncells, n_nu;
   int nT, mode, tau_cut, step_cap;
-  int nu_major;  // the walk's table is the wavenumber-major copy
+  int nu_major;  // walk table layout: 0 T-major, 1 wavenumber-major, 2 wavenumber-major node pairs
   unsigned long long ray_begin, n_rays;
   uint32_t seed_lo, seed_hi, enclosure;
   float nu_min, dnu;
@@ -100,6 +100,23 @@ __device__ __forceinline__ float cell_kappa_t(const float4 cd, const float *__re
   if (nT < 2) return cd.y * v0;
   const float v1 = __ldg(c + 1);
   return cd.y * fmaf(cd.x, v1, (1.0f - cd.x) * v0);
+}
+
+// The same from node pairs tabp[j * (nT - 1) + k] = {kappa_k, kappa_k+1}: one 8-byte load.
+__device__ __forceinline__ float cell_kappa_p(const float4 cd, const float *__restrict__ tabp, int nT,
+                                              long long j) {
+  const int k = __float_as_int(cd.w);
+  const float2 v = __ldg(reinterpret_cast<const float2 *>(tabp) + j * (long long)(nT - 1) + k);
+  return cd.y * fmaf(cd.x, v.y, (1.0f - cd.x) * v.x);
+}
+
+// kappa of a cell from the walk table in layout L (0 T-major, 1 wavenumber-major, 2 pairs).
+template <int L>
+__device__ __forceinline__ float cell_kappa_l(const float4 cd, const float *__restrict__ tab, int nT,
+                                              long long n_nu, long long j) {
+  if (L == 2) return cell_kappa_p(cd, tab, nT, j);
+  if (L == 1) return cell_kappa_t(cd, tab, nT, j);
+  return cell_kappa(cd, tab, n_nu, nT, j);
 }
 
 __device__ __forceinline__ float tmax_of(int i, int step, float h, float pos, float invd) {
@@ -165,7 +182,9 @@ __device__ __forceinline__ void ray_init(const WalkParams &W, const float4 *__re
     // emission weight from the table; walks without a table set it at their first step
     if (tab) {
       const float4 cd = cells[c];
-      const float ke = W.nu_major ? cell_kappa_t(cd, tab, W.nT, R.j) : cell_kappa(cd, tab, W.n_nu, W.nT, R.j);
+      const float ke = W.nu_major == 2 ? cell_kappa_p(cd, tab, W.nT, R.j)
+                       : (W.nu_major == 1 ? cell_kappa_t(cd, tab, W.nT, R.j)
+                                          : cell_kappa(cd, tab, W.n_nu, W.nT, R.j));
       R.w = emission_weight(W, R.j, cd.z, ke);
       if (cd_out) *cd_out = cd;
     } else {
@@ -269,6 +288,12 @@ rt_status walk_setup(const rt_grid *grid, const rt_spectral *spec, uint64_t ray_
                      WalkParams *W, RecordPtrs *rp);
 // Host: wavenumber-major copy tabt[j * nT + k] of a T-major table.
 rt_status launch_transpose(const float *tab, int nT, long long n_nu, float *tabt, cudaStream_t st);
+// Host: the walk's copy of a T-major table: node pairs (layout 2) when nT >= 2 and the
+// pair table fits kPairTableBytes (so that it can stay in L2), else wavenumber-major (1).
+constexpr size_t kPairTableBytes = size_t(64) << 20;
+int walk_table_layout(int nT, long long n_nu);
+size_t walk_table_bytes(int layout, int nT, long long n_nu);
+rt_status launch_walk_table(int layout, const float *tab, int nT, long long n_nu, float *out, cudaStream_t st);
 // Host: the CellParams of a spectral spec (table T grid, reference state).
 CellParams cell_params(const rt_spectral *spec, long long ncells, int has_px);
 // Host: per-cell T bracket, density scale and T (float4 per cell).
