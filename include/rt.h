@@ -205,7 +205,7 @@ rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *
  *   __device__ array that every GPU loading the library holds until the process
  *   exits); the call allocates and frees nothing.
  * Limit: 16 B per (T node, line) for Lorentz lines, 32 B for Voigt lines, + 16 B
- *   per line + 48 B per 256 wavenumbers, plus 32 B per line when the lines are
+ *   per line + 80 B per 256 wavenumbers, plus 32 B per line when the lines are
  *   host-resident, at most 32 MiB in all (about 2 million Lorentz or 1 million
  *   Voigt (T node, line) pairs, e.g. 64 T nodes x 15,000 Voigt lines).  Larger
  *   inputs return RT_E_INVAL with the required size before any work is queued.
@@ -283,11 +283,14 @@ rt_status rt_trace_batch(int32_t n_encl, const rt_enclosure *encl, const float *
 
 /*
  * Process-wide launch shapes, set by an autotuner (no effect on results):
- * kappa_t_per_block = temperature nodes per rt_build_kappa block (1..8, 0 = 8).
+ * kappa_t_per_block = temperature nodes per rt_build_kappa block (1..8, 0 = 8);
+ * walk_blocks_per_sm = resident 256-thread blocks per SM the rt_trace walk is
+ *   compiled for (4: 64 registers per thread, 5: 48; 0 = 5).
  */
 typedef struct {
   int32_t kappa_t_per_block;
-  int32_t reserved[7];
+  int32_t walk_blocks_per_sm;
+  int32_t reserved[6];
 } rt_tuning;
 rt_status rt_set_tuning(const rt_tuning *t);
 rt_status rt_get_tuning(rt_tuning *t);

@@ -7,13 +7,14 @@ choice in a JSON file keyed by a signature of the workload's sizes
 
 * ``tune_kappa``: temperature nodes per rt_build_kappa block (1, 2, 4, 8).
 * ``tune_batch``: rays per work item and threads per block of the batched walk.
+* ``tune_walk``: resident blocks per SM the rt_trace walk is compiled for (4 or 5).
 """
 from __future__ import annotations
 
 import json
 import os
 
-from . import Batch, build_kappa, set_tuning
+from . import Batch, Tally, build_kappa, set_tuning, trace
 
 
 def _cache_path():
@@ -65,15 +66,15 @@ def tune_kappa(lines, spec, candidates=(1, 2, 4, 8), reps=3, use_cache=True):
     key = f"kappa:{spec.profile}:{lines.n}:{spec.n_nu}:{spec.nT}:{spec.dnu}:{spec.cutoff}"
     if use_cache and key in _load():
         best = int(_load()[key]["best"])
-        set_tuning(best)
+        set_tuning(kappa_t_per_block=best)
         return best, _load()[key]["ms"]
     out = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
     times = {}
     for c in candidates:
-        set_tuning(c)
+        set_tuning(kappa_t_per_block=c)
         times[int(c)] = _time(lambda: build_kappa(lines, spec, out=out), reps)
     best = min(times, key=times.get)
-    set_tuning(best)
+    set_tuning(kappa_t_per_block=best)
     _store(key, {"best": best, "ms": times})
     return best, times
 
@@ -96,3 +97,21 @@ def tune_batch(grids, n_rays, spec, kappa, candidates=None, reps=2, use_cache=Tr
     rpi, th = (int(v) for v in best.split(","))
     _store(key, {"best": [rpi, th], "ms": times})
     return (rpi, th), times
+
+
+def tune_walk(grid_struct, ncells, spec, kappa, n_rays, candidates=(4, 5), reps=2, use_cache=True):
+    """Pick the walk's resident blocks per SM on the caller's trace; returns (best, {blocks: ms})."""
+    key = f"walk:{ncells}:{spec.n_nu}:{spec.nT}:{int(n_rays)}"
+    if use_cache and key in _load():
+        best = int(_load()[key]["best"])
+        set_tuning(walk_blocks_per_sm=best)
+        return best, _load()[key]["ms"]
+    tally = Tally(ncells)
+    times = {}
+    for c in candidates:
+        set_tuning(walk_blocks_per_sm=c)
+        times[int(c)] = _time(lambda: (tally.zero(), trace(grid_struct, kappa, spec, tally, n_rays)), reps)
+    best = min(times, key=times.get)
+    set_tuning(walk_blocks_per_sm=best)
+    _store(key, {"best": best, "ms": times})
+    return best, times

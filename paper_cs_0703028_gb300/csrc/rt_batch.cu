@@ -98,8 +98,8 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
       if (!active) continue;
       const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
       float4 cdn = cd;
-      const bool done = ray_step<false>(W, kap, D.absorbed, D.status, rec, R, true,
-                                        [&](int c) { cdn = __ldg(cells + c); });
+      const bool done = ray_step<false, false>(W, kap, D.absorbed, D.status, rec, R, true,
+                                               [&](int c) { cdn = __ldg(cells + c); });
       cd = cdn;
       if (done) {
         em += (double)R.w;

@@ -114,13 +114,16 @@ __global__ void k_line_geometry(const double *__restrict__ nu0, const double *__
 // Eq. (S) times the number density, and the profile's coefficients, for line l
 // at T node k.  Voigt: P = {c0, s dnu, y^2, c2}, P2 = {c3, c4, near half-width, 0}
 // with the far-wing series c0 t + c1 t^2 + c2 t^3 + c3 t^4 + c4 t^5 (c1 = 1.5 c0).
-// Returns the far-zone distance of the line in grid units (float bits): beyond it
+// Writes the line's far-zone distances in grid units (float bits): beyond far[0]
 // the t^4 and t^5 terms are below 2^-24 of the value (27 y^2 t^3 <= 2^-24 with
-// t <= 1/x^2), so a degree-2 series is within one binary32 rounding of the full one.
-__device__ __forceinline__ unsigned prefactor_one(const double *__restrict__ nu0, const double *__restrict__ S,
+// t <= 1/x^2), so a degree-2 series is within one binary32 rounding of the full
+// one; beyond far[1] (>= far[0]) also (3.75 + 2 y^2) t^2 <= 2^-25, so the degree-1
+// series drops at most 1.25 * 2^-24 of the value.
+__device__ __forceinline__ void prefactor_one(const double *__restrict__ nu0, const double *__restrict__ S,
                                                   const double *__restrict__ g, const double *__restrict__ E,
                                                   const PrefParams &Q, float4 *__restrict__ Pout,
-                                                  float4 *__restrict__ P2out, long long l, int k) {
+                                                  float4 *__restrict__ P2out, long long l, int k,
+                                                  unsigned (&far)[2]) {
   // T_k = T_min + k (T_max - T_min) / (nT - 1) and 1/T_k in double-float
   df Tk = df_from_double(Q.T_min);
   if (Q.nT > 1) {
@@ -144,7 +147,7 @@ __device__ __forceinline__ unsigned prefactor_one(const double *__restrict__ nu0
   const float A = (Q.u_coef * iTf) * S_T;  // u(T) S(T), cm^-1 per unit profile
   const float gam = __double2float_rn(g[l]) * Q.p_ref * powf(tr, Q.n_T);
   float4 out;
-  unsigned far = 0;
+  far[0] = far[1] = 0;
   if (Q.profile == RT_PROFILE_LORENTZ) {
     const float gg = gam * Q.inv_dnu;  // half-width in grid units
     out = make_float4(A * gg * (float)(1.0 / kPi) * Q.inv_dnu, gg * gg, 0.0f, 0.0f);
@@ -160,12 +163,14 @@ __device__ __forceinline__ unsigned prefactor_one(const double *__restrict__ nu0
     const float c0 = A * s * (float)(1.0 / kPi) * y;
     out = make_float4(c0, sd, y2, __fmaf_rn(-2.0f, y2, 3.75f) * c0);
     P2out[(long long)k * Q.n_lines + l] = make_float4(-15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near, 0.0f);
-    // (27 y^2 / 2^-24)^(1/6) = 27.66 y^(1/3), with 5 % margin, in grid units
-    const float dfar = 29.1f * cbrtf(y) / sd;
-    far = (dfar >= 0.0f && dfar < 1e9f) ? __float_as_uint(dfar) : __float_as_uint(1e9f);
+    // (27 y^2 / 2^-24)^(1/6) = 27.66 y^(1/3) and (2^25 (3.75 + 2 y^2))^(1/4), with 5 %
+    // margin, in grid units
+    const float d2 = 29.1f * cbrtf(y) / sd;
+    const float d1 = fmaxf(1.05f * sqrtf(sqrtf(33554432.0f * (3.75f + 2.0f * y2))) / sd, d2);
+    far[0] = (d2 >= 0.0f && d2 < 1e9f) ? __float_as_uint(d2) : __float_as_uint(1e9f);
+    far[1] = (d1 >= 0.0f && d1 < 1e9f) ? __float_as_uint(d1) : __float_as_uint(1e9f);
   }
   Pout[(long long)k * Q.n_lines + l] = out;
-  return far;
 }
 
 __global__ void k_prefactor(const double *__restrict__ nu0, const double *__restrict__ S,
@@ -174,17 +179,19 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
                             unsigned *__restrict__ far_bits) {
   const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
-  unsigned fb = 0;  // this line's far-zone distance (grid units, float bits)
-  if (l < Q.n_lines) fb = prefactor_one(nu0, S, g, E, Q, Pout, P2out, l, k);
-  // block maximum, one atomic per block (non-negative floats order like their bits)
-  __shared__ unsigned s_max[32];
-  fb = __reduce_max_sync(0xffffffffu, fb);
-  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = fb;
+  unsigned fb[2] = {0, 0};  // this line's far-zone distances (grid units, float bits)
+  if (l < Q.n_lines) prefactor_one(nu0, S, g, E, Q, Pout, P2out, l, k, fb);
+  // block maxima, one atomic each per block (non-negative floats order like their bits)
+  __shared__ unsigned s_max[2][32];
+  for (int d = 0; d < 2; ++d) {
+    const unsigned m = __reduce_max_sync(0xffffffffu, fb[d]);
+    if ((threadIdx.x & 31) == 0) s_max[d][threadIdx.x >> 5] = m;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 2) {
     unsigned m = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
-    if (m) atomicMax(far_bits, m);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[threadIdx.x][w]);
+    if (m) atomicMax(far_bits + threadIdx.x, m);
   }
 }
 
@@ -241,8 +248,16 @@ __device__ __forceinline__ long long lower_bound_c(const int4 *R, long long n, l
 }
 
 // Kinds of line ranges within a tile (see k_tile_lines).
-enum SegKind : int { kSegGeneral = 0, kSegFar = 1, kSegFast = 2, kSegFarMasked = 3 };
-constexpr int kMaxSegs = 8;
+enum SegKind : int {
+  kSegGeneral = 0,   // window masking and near-centre test per line
+  kSegFast = 1,      // covering, degree-4 far-wing series
+  kSegFar2 = 2,      // covering, degree-2 series
+  kSegFar1 = 3,      // covering, degree-1 series
+  kSegFar2Masked = 4,
+  kSegFar1Masked = 5,
+};
+constexpr int kMaxSegs = 12;
+constexpr int kTileInts = 5;  // int4 per tile: {lb, ub, nseg, 0}, 12 ends, 16 kind bytes
 
 // Per tile of kTilePts wavenumbers [jw0, jw0 + kTilePts): the lines [lb, ub)
 // whose windows reach it, split into ranges by kind.  Windows and centres are
@@ -250,18 +265,17 @@ constexpr int kMaxSegs = 8;
 //   cover : j_lo <= jw0 and j_hi >= jw0 + kTilePts - 1 (no masking needed);
 //   near  : j_c within W + 4 grid points of the tile, W bounding the near-centre
 //           half-width of every line (lines outside it have no point |z| < 20);
-//   far   : j_c more than D grid points from the tile, D >= W + 4 bounding every
-//           line's far-zone distance (degree-2 far-wing series).
-// Kinds: covering lines are far, fast (degree-4 series) or, when near, general;
-// partially covering lines are far-masked when far, else general.
-// out[3t] = {lb, ub, nseg, kinds (4 bits each)}, out[3t+1], out[3t+2] = segment ends.
+//   far2 / far1 : j_c more than D2 / D1 grid points from the tile, D1 >= D2 >= W + 4
+//           bounding every line's far-zone distances (degree-2 / degree-1 series).
+// Covering lines are far1, far2, fast or (near) general; partially covering
+// lines are far1-masked, far2-masked or general.
 __global__ void k_tile_lines(const int4 *__restrict__ R, long long n, long long n_nu, int W,
                              const unsigned *__restrict__ far_bits, long long n_tiles,
                              int4 *__restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
-  const float dfar = __uint_as_float(*far_bits);
-  const long long D = max((long long)W + 4, (long long)ceilf(fminf(dfar, 1e9f)) + 2);
+  const long long D2 = max((long long)W + 4, (long long)ceilf(fminf(__uint_as_float(far_bits[0]), 1e9f)) + 2);
+  const long long D1 = max(D2, (long long)ceilf(fminf(__uint_as_float(far_bits[1]), 1e9f)) + 2);
   const long long jw0 = t * kTilePts, jw1 = jw0 + kTilePts - 1;
   const long long jend = min(jw0 + (long long)kTilePts, n_nu);
   const long long lb = lower_bound_hi(R, n, (int)jw0);
@@ -269,41 +283,50 @@ __global__ void k_tile_lines(const int4 *__restrict__ R, long long n, long long 
   auto cl = [&](long long v) { return min(max(v, lb), ub); };
   const long long ca = cl(lower_bound_hi(R, n, (int)jw1));       // cover = [ca, cb)
   const long long cb = cl(lower_bound_lo(R, n, (int)(jw0 + 1)));
-  const long long fa = cl(lower_bound_c(R, n, jw0 - D));          // far: l < fa or l >= fb
+  const long long f1a = cl(lower_bound_c(R, n, jw0 - D1));        // far1: l < f1a or l >= f1b
+  const long long f2a = cl(lower_bound_c(R, n, jw0 - D2));        // far2: l < f2a or l >= f2b
   const long long na = cl(lower_bound_c(R, n, jw0 - W - 4));      // near: [na, nb)
   const long long nb = cl(lower_bound_c(R, n, jw1 + W + 5));
-  const long long fb = cl(lower_bound_c(R, n, jw1 + D + 1));
+  const long long f2b = cl(lower_bound_c(R, n, jw1 + D2 + 1));
+  const long long f1b = cl(lower_bound_c(R, n, jw1 + D1 + 1));
   auto kind = [&](long long l) -> int {
-    if (l < ca) return l < fa ? kSegFarMasked : kSegGeneral;
-    if (l >= cb) return l >= fb ? kSegFarMasked : kSegGeneral;
-    if (l < fa || l >= fb) return kSegFar;
+    const bool far1 = l < f1a || l >= f1b, far2 = l < f2a || l >= f2b;
+    if (l < ca || l >= cb) return far1 ? kSegFar1Masked : (far2 ? kSegFar2Masked : kSegGeneral);
+    if (far1) return kSegFar1;
+    if (far2) return kSegFar2;
     if (l < na || l >= nb) return kSegFast;
     return kSegGeneral;
   };
   // the change points, sorted; one segment per maximal run of equal kind
-  long long b[7] = {ca, cb, fa, na, nb, fb, ub};
-  for (int i = 1; i < 6; ++i)
+  long long b[9] = {ca, cb, f1a, f2a, na, nb, f2b, f1b, ub};
+  for (int i = 1; i < 8; ++i)
     for (int j = i; j > 0 && b[j - 1] > b[j]; --j) {
       const long long x = b[j - 1]; b[j - 1] = b[j]; b[j] = x;
     }
-  int ends[kMaxSegs], nseg = 0, kinds = 0;
+  int ends[kMaxSegs];
+  unsigned char kinds[16] = {};
+  int nseg = 0;
   long long start = lb;
-  for (int i = 0; i < 7; ++i) {
+  for (int i = 0; i < 9; ++i) {
     const long long e = b[i];
     if (e <= start) continue;
     const int kd = kind(start);
-    if (nseg > 0 && ((kinds >> (4 * (nseg - 1))) & 15) == kd) {
+    if (nseg > 0 && kinds[nseg - 1] == kd) {
       ends[nseg - 1] = (int)e;
     } else {
-      kinds |= kd << (4 * nseg);
+      kinds[nseg] = (unsigned char)kd;
       ends[nseg++] = (int)e;
     }
     start = e;
   }
   for (int i = nseg; i < kMaxSegs; ++i) ends[i] = (int)ub;
-  out[3 * t] = make_int4((int)lb, (int)ub, nseg, kinds);
-  out[3 * t + 1] = make_int4(ends[0], ends[1], ends[2], ends[3]);
-  out[3 * t + 2] = make_int4(ends[4], ends[5], ends[6], ends[7]);
+  int4 *o = out + kTileInts * t;
+  o[0] = make_int4((int)lb, (int)ub, nseg, 0);
+  for (int i = 0; i < 3; ++i) o[1 + i] = make_int4(ends[4 * i], ends[4 * i + 1], ends[4 * i + 2], ends[4 * i + 3]);
+  int kw[4];
+  for (int i = 0; i < 4; ++i)
+    kw[i] = kinds[4 * i] | (kinds[4 * i + 1] << 8) | (kinds[4 * i + 2] << 16) | (kinds[4 * i + 3] << 24);
+  o[4] = make_int4(kw[0], kw[1], kw[2], kw[3]);
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -359,13 +382,16 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
 
   __shared__ int s_end[kMaxSegs];
   __shared__ unsigned char s_kind[kMaxSegs];
-  const int4 ta = __ldg(tiles + 3 * blockIdx.x);
+  const int4 *tinfo = tiles + (long long)kTileInts * blockIdx.x;
+  const int4 ta = __ldg(tinfo);
   const int lb = ta.x, ub = ta.y;
   if (threadIdx.x < kMaxSegs) {
-    const int4 e = __ldg(tiles + 3 * blockIdx.x + 1 + (threadIdx.x >> 2));
     const int q = threadIdx.x & 3;
+    const int4 e = __ldg(tinfo + 1 + (threadIdx.x >> 2));
+    const int4 kw = __ldg(tinfo + 4);
+    const int w = (threadIdx.x >> 2) == 0 ? kw.x : ((threadIdx.x >> 2) == 1 ? kw.y : kw.z);
     s_end[threadIdx.x] = q == 0 ? e.x : (q == 1 ? e.y : (q == 2 ? e.z : e.w));
-    s_kind[threadIdx.x] = (unsigned char)((ta.w >> (4 * threadIdx.x)) & 15);
+    s_kind[threadIdx.x] = (unsigned char)((w >> (8 * q)) & 255);
   }
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
@@ -446,8 +472,10 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
           float h;
           if (DEG == 4)
             h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.y, p2.x), p.w), c1), p.x);
-          else
+          else if (DEG == 2)
             h = __fmaf_rn(t, __fmaf_rn(t, p.w, c1), p.x);
+          else
+            h = __fmaf_rn(t, c1, p.x);
           if (MASK && (jt + q < r.x || jt + q > r.y)) h = 0.0f;
           g[q] = first ? t * h : __fmaf_rn(t, h, g[q]);
         }
@@ -574,11 +602,15 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
       while (s_end[seg] <= l) ++seg;  // the last segment ends at ub > l
       const int i1 = min(cnt, s_end[seg] - l0);
       const int kd = s_kind[seg];
-      if (kd == kSegFar)
+      if (kd == kSegFar1)
+        run_fast(std::integral_constant<int, 1>(), std::false_type(), i, i1);
+      else if (kd == kSegFar2)
         run_fast(std::integral_constant<int, 2>(), std::false_type(), i, i1);
       else if (kd == kSegFast)
         run_fast(std::integral_constant<int, 4>(), std::false_type(), i, i1);
-      else if (kd == kSegFarMasked)
+      else if (kd == kSegFar1Masked)
+        run_fast(std::integral_constant<int, 1>(), std::true_type(), i, i1);
+      else if (kd == kSegFar2Masked)
         run_fast(std::integral_constant<int, 2>(), std::true_type(), i, i1);
       else
         run_general(i, i1);
@@ -720,7 +752,7 @@ KappaLayout kappa_layout(const rt_lines *lines, const rt_spectral *spec) {
   L.off_P2 = up(L.off_P + pn);
   L.off_tiles = up(L.off_P2 + (spec->profile == RT_PROFILE_VOIGT ? pn : 0));
   const size_t n_tiles = (size_t)((spec->n_nu + kTilePts - 1) / kTilePts);
-  L.off_far = up(L.off_tiles + n_tiles * 3 * sizeof(int4));
+  L.off_far = up(L.off_tiles + n_tiles * kTileInts * sizeof(int4));
   L.total = L.off_far + 256;
   return L;
 }
@@ -787,7 +819,7 @@ rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, con
   Q.nT = spec->nT;
   Q.profile = spec->profile;
   dim3 gp((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
-  RT_CUDA_TRY(cudaMemsetAsync(far_bits, 0, sizeof(unsigned), st));
+  RT_CUDA_TRY(cudaMemsetAsync(far_bits, 0, 2 * sizeof(unsigned), st));
   k_prefactor<<<gp, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, Q, P, P2, far_bits);
   RT_CUDA_TRY(cudaGetLastError());
 
@@ -855,7 +887,7 @@ rt_status build_kappa_static_impl(const rt_lines *lines, const rt_spectral *spec
   if (L.total > kStaticScratchBytes)
     return fail(RT_E_INVAL,
                 "rt_build_kappa_static: needs %zu bytes of scratch (16 B per line and T node, 32 B "
-                "for Voigt lines, 16 B per line, 48 B per 256 wavenumbers, plus 32 B per line for "
+                "for Voigt lines, 16 B per line, 80 B per 256 wavenumbers, plus 32 B per line for "
                 "host-resident lines), the static array holds %zu",
                 L.total, kStaticScratchBytes);
   if (lines->memory == RT_MEM_HOST && lines->n > 0) {
@@ -886,11 +918,18 @@ extern "C" rt_status rt_build_kappa_static(const rt_lines *lines, const rt_spect
   return rt::build_kappa_static_impl(lines, spec, kappa, evals_out, status, (cudaStream_t)stream);
 }
 
+namespace rt {
+extern int g_walk_blocks;  // rt_trace.cu
+}
+
 extern "C" rt_status rt_set_tuning(const rt_tuning *t) {
   if (!t) return rt::fail(RT_E_INVAL, "rt_set_tuning: NULL");
   if (t->kappa_t_per_block < 0 || t->kappa_t_per_block > 8)
     return rt::fail(RT_E_INVAL, "rt_set_tuning: kappa_t_per_block must be in [0, 8]");
+  if (t->walk_blocks_per_sm != 0 && t->walk_blocks_per_sm != 4 && t->walk_blocks_per_sm != 5)
+    return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_blocks_per_sm must be 0, 4 or 5");
   rt::g_kappa_tpb = t->kappa_t_per_block == 0 ? 8 : t->kappa_t_per_block;
+  rt::g_walk_blocks = t->walk_blocks_per_sm == 0 ? 5 : t->walk_blocks_per_sm;
   return RT_OK;
 }
 
@@ -898,5 +937,6 @@ extern "C" rt_status rt_get_tuning(rt_tuning *t) {
   if (!t) return rt::fail(RT_E_INVAL, "rt_get_tuning: NULL");
   *t = rt_tuning{};
   t->kappa_t_per_block = rt::g_kappa_tpb;
+  t->walk_blocks_per_sm = rt::g_walk_blocks;
   return RT_OK;
 }

@@ -34,6 +34,12 @@ __global__ void k_cell_prep(const float *__restrict__ T, const float *__restrict
 // the warp's next rays together, so ray set-up and stepping stay converged.
 constexpr int kRefillIdle = 16;
 
+}  // namespace
+
+int g_walk_blocks = 5;  // resident walk blocks per SM the launch is compiled for (4 or 5)
+
+namespace {
+
 // [nT][n_nu] -> [n_nu][nT] through 32 x 33 shared tiles
 __global__ void k_transpose(const float *__restrict__ in, int rows, long long cols, float *__restrict__ out) {
   __shared__ float t[32][33];
@@ -72,8 +78,8 @@ __global__ void k_pair_table(const float *__restrict__ in, int nT, long long n_n
   }
 }
 
-template <bool REC, int TAB>
-__global__ void __launch_bounds__(kWalkThreads, 5)
+template <bool REC, int TAB, int MINB>
+__global__ void __launch_bounds__(kWalkThreads, MINB)
 k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
        double *__restrict__ absorbed, double *__restrict__ scalars,
        unsigned long long *__restrict__ steps_out, uint32_t *status, RecordPtrs rec) {
@@ -307,8 +313,11 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const bool rec = rp.cells != nullptr;
-  auto kern = rec ? (layout == 2 ? k_walk<true, 2> : k_walk<true, 1>)
-                  : (layout == 2 ? k_walk<false, 2> : k_walk<false, 1>);
+  auto kern = g_walk_blocks == 4
+                  ? (rec ? (layout == 2 ? k_walk<true, 2, 4> : k_walk<true, 1, 4>)
+                         : (layout == 2 ? k_walk<false, 2, 4> : k_walk<false, 1, 4>))
+                  : (rec ? (layout == 2 ? k_walk<true, 2, 5> : k_walk<true, 1, 5>)
+                         : (layout == 2 ? k_walk<false, 2, 5> : k_walk<false, 1, 5>));
   int per_sm = 0;
   RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkThreads, 0));
   if (per_sm < 1) per_sm = 1;

@@ -225,7 +225,10 @@ struct NoPrefetch {
 // data) before the deposit arithmetic; the visit sequence is that of the
 // binary32 DDA (nearest face, ties to the lowest axis, face distance
 // recomputed from the start point).
-template <bool REC = true, typename Prefetch = NoPrefetch>
+// EARLY_EXIT selects returns at each stop condition (faster in the table walk)
+// or one combined stop flag with an unconditional advance (faster in the
+// batched walk); both give the same visits and deposits.
+template <bool REC = true, bool EARLY_EXIT = true, typename Prefetch = NoPrefetch>
 __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double *__restrict__ absorbed,
                                          uint32_t *status, const RecordPtrs &rec, Ray &R,
                                          bool writes = true, Prefetch pf = Prefetch()) {
@@ -260,13 +263,20 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
     rec.ds[(long long)R.row * W.rec_max + R.nv] = ds;
   }
   ++R.nv;
-  if (tn == INFINITY) return true;
-  if (W.tau_cut && R.tau > 100.0f) return true;
-  if (R.nv >= W.step_cap) {
-    if (writes) status_or(status, RT_DEV_STEPCAP);
-    return true;
+  const bool cut = W.tau_cut && R.tau > 100.0f;
+  const bool capped = R.nv >= W.step_cap;
+  if (EARLY_EXIT) {
+    if (tn == INFINITY || cut) return true;
+    if (capped) {
+      if (writes) status_or(status, RT_DEV_STEPCAP);
+      return true;
+    }
+    if (!inside) return true;
+  } else {
+    // a ray that stops keeps only w, trans, nv and row meaningful, so the advance
+    // below need not be conditional
+    if (writes && capped && tn != INFINITY && !cut) status_or(status, RT_DEV_STEPCAP);
   }
-  if (!inside) return true;
   R.t = tn;
   R.cell = cnext;
   const float h = a0 ? W.h[0] : (a1 ? W.h[1] : W.h[2]);
@@ -278,7 +288,7 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
   R.tx = a0 ? tm : R.tx;
   R.ty = a1 ? tm : R.ty;
   R.tz = (!a0 && !a1) ? tm : R.tz;
-  return false;
+  return !inside || cut || capped;
 }
 
 // Host: validation and walk parameters common to every walk (rt_trace.cu).
