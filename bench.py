@@ -27,10 +27,12 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 FP32_LANES_PER_SM = 128
-# algorithmic binary32 flops of one profile evaluation (FMA = 2, reciprocal = 1):
-# far-wing Voigt (three-term asymptotic series in t = 1/|z|^2, s = y^2 t) and
-# Lorentz, each with its grid coordinate and the Kahan update
-FLOPS_PER_EVAL = {"voigt": 22, "lorentz": 9}
+# algorithmic work of one profile evaluation in lane operations (one binary32
+# arithmetic instruction or one MUFU reciprocal per lane, FMA = 1): a far-wing
+# Voigt evaluation is 1 reciprocal + 6 binary32 operations (grid coordinate,
+# |z|^2, series, accumulation and its share of the Kahan update); Lorentz is
+# 1 reciprocal + 4.  The peak is one lane operation per FP32 lane per clock.
+OPS_PER_EVAL = {"voigt": 7, "lorentz": 5}
 
 
 def _dist():
@@ -257,9 +259,9 @@ def run_gpu(args):
     clocks = _clock_summary(clk_path, local) if sampler else None
     sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     props = torch.cuda.get_device_properties(local)
-    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_clock_mhz * 1e6 / 1e12
-    flops = evals_per_step * FLOPS_PER_EVAL[spec.profile]
-    achieved = flops / (ms_build * 1e-3) / 1e12
+    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_clock_mhz * 1e6 / 1e12
+    ops = evals_per_step * OPS_PER_EVAL[spec.profile]
+    achieved = ops / (ms_build * 1e-3) / 1e12
     traffic = _profiled_traffic("k_kappa_box32_voigt20k.md", ["rt_kappa.cu", "rt_common.cuh"])
     out = {
         "metric": "ray-cell steps/s + line-profile evals/s; surrogate vs plain at <=1% tally err",
@@ -288,11 +290,12 @@ def run_gpu(args):
         "gpu_launches": 9 * args.steps,
         "tuning": {"walk_blocks_per_sm": walk_blocks, "walk_candidates_ms": walk_tune_ms},
         "roofline": {"kernel": "k_kappa (rt_build_kappa)", "bound": "alu", "achieved": achieved,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
                      "traffic": traffic,
-                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                                    f"{sm_clock_mhz:.0f} MHz",
-                     "flops_per_eval": FLOPS_PER_EVAL[spec.profile]},
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
+                                    f"{sm_clock_mhz:.0f} MHz, one lane operation per clock",
+                     "ops_per_eval": OPS_PER_EVAL[spec.profile],
+                     "timed": "rt_build_kappa (k_kappa and its three small set-up kernels)"},
         "e2e": {"value": e2e_value, "unit": "ray-cell steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "clocks": clocks,
