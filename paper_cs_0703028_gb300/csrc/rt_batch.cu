@@ -51,6 +51,7 @@ __global__ void k_cell_prep_batch(const EnclDev *__restrict__ E, const long long
 }
 
 constexpr int kRefillIdleBatch = 16;
+constexpr int kBatchUnroll = 4;
 
 template <int TAB>
 __global__ void __launch_bounds__(256, 4)
@@ -96,11 +97,17 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
       }
       if (!__any_sync(0xffffffffu, active)) break;
       if (!active) continue;
-      const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
-      float4 cdn = cd;
-      const bool done = ray_step<false, false>(W, kap, D.absorbed, D.status, rec, R, true,
-                                               [&](int c) { cdn = __ldg(cells + c); });
-      cd = cdn;
+      bool done = false;
+#pragma unroll
+      for (int u = 0; u < kBatchUnroll; ++u) {  // steps per pass of the loop
+        if (!done) {
+          const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
+          float4 cdn = cd;
+          done = ray_step<false, false>(W, kap, D.absorbed, D.status, rec, R, true,
+                                        [&](int c) { cdn = __ldg(cells + c); });
+          cd = cdn;
+        }
+      }
       if (done) {
         em += (double)R.w;
         esc += (double)(R.w * R.trans);

@@ -33,6 +33,7 @@ __global__ void k_cell_prep(const float *__restrict__ T, const float *__restrict
 // own rays; when half of the warp's lanes are idle (ballot), the idle lanes take
 // the warp's next rays together, so ray set-up and stepping stay converged.
 constexpr int kRefillIdle = 16;
+constexpr int kWalkUnroll = 8;  // steps per pass of the walk loop
 
 }  // namespace
 
@@ -106,12 +107,18 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
     }
     if (!__any_sync(0xffffffffu, active)) break;
     if (!active) continue;
-    // the table value of this cell, then the next cell's data, both in flight
-    // while the step's arithmetic runs
-    const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
-    float4 cdn = cd;
-    const bool done = ray_step<REC>(W, kap, absorbed, status, rec, R, true, [&](int c) { cdn = __ldg(cells + c); });
-    cd = cdn;
+    // kWalkUnroll steps per pass of the loop; each step loads the table value of
+    // its cell and the next cell's data, both in flight while its arithmetic runs
+    bool done = false;
+#pragma unroll
+    for (int u = 0; u < kWalkUnroll; ++u) {
+      if (!done) {
+        const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
+        float4 cdn = cd;
+        done = ray_step<REC>(W, kap, absorbed, status, rec, R, true, [&](int c) { cdn = __ldg(cells + c); });
+        cd = cdn;
+      }
+    }
     if (done) {
       const float out = R.w * R.trans;
       em += (double)R.w;
