@@ -288,7 +288,8 @@ def run_gpu(args):
         # per step: k_line_geometry, k_prefactor, k_tile_lines, k_kappa; k_cell_prep, walk
         # table copy, k_walk; k_reduce, k_final
         "gpu_launches": 9 * args.steps,
-        "tuning": {"walk_blocks_per_sm": walk_blocks, "walk_candidates_ms": walk_tune_ms},
+        "tuning": {"walk_blocks_per_sm": walk_blocks[0], "walk_refill_idle": walk_blocks[1],
+                   "walk_candidates_ms": walk_tune_ms},
         "roofline": {"kernel": "k_kappa (rt_build_kappa)", "bound": "alu", "achieved": achieved,
                      "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
                      "traffic": traffic,
@@ -524,6 +525,9 @@ def run_box128(args):
     torch.cuda.synchronize()
     ev = int(evals.item())
     ms_build = _ev_time(lambda: rt.build_kappa(case.lines, spec, out=kap), reps=args.steps)
+    from paper_cs_0703028_gb300 import autotune
+    walk_shape, walk_ms = autotune.tune_walk(gs, case.grid.ncells, spec, kap, min(n, 10_000_000),
+                                             use_cache=False)
     t = rt.Tally(case.grid.ncells)
     t.zero()
     rt.trace(gs, kap, spec, t, n_rays=min(n, 10_000_000), n_rays_total=n)
@@ -537,7 +541,9 @@ def run_box128(args):
            "config": {"workload": f"box128_voigt100k: 128^3 cells, 100k Voigt lines, 64 T x 400k nu, {n} rays"},
            "build_ms": ms_build, "evals": ev, "line_profile_evals_per_s": ev / (ms_build * 1e-3),
            "trace_ms": ms_trace, "steps": steps, "energy_residual": float(sc[3]),
-           "walk_hbm_frac_at_16B_per_step": steps * 16 / (ms_trace * 1e-3) / (hbm * 1e9)}
+           "walk_hbm_frac_at_16B_per_step": steps * 16 / (ms_trace * 1e-3) / (hbm * 1e9),
+           "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
+                      "walk_candidates_ms_1e7_rays": walk_ms}}
     print(json.dumps(res), flush=True)
 
 

@@ -285,12 +285,15 @@ rt_status rt_trace_batch(int32_t n_encl, const rt_enclosure *encl, const float *
  * Process-wide launch shapes, set by an autotuner (no effect on results):
  * kappa_t_per_block = temperature nodes per rt_build_kappa block (1..8, 0 = 8);
  * walk_blocks_per_sm = resident 256-thread blocks per SM the rt_trace walk is
- *   compiled for (4: 64 registers per thread, 5: 48; 0 = 5).
+ *   compiled for (4: 64 registers per thread, 5: 48; 0 = 5);
+ * walk_refill_idle = idle lanes of a warp that trigger loading new rays in the
+ *   rt_trace walk (8 or 16; 0 = 16).
  */
 typedef struct {
   int32_t kappa_t_per_block;
   int32_t walk_blocks_per_sm;
-  int32_t reserved[6];
+  int32_t walk_refill_idle;
+  int32_t reserved[5];
 } rt_tuning;
 rt_status rt_set_tuning(const rt_tuning *t);
 rt_status rt_get_tuning(rt_tuning *t);

@@ -372,24 +372,28 @@ class rt_batch_opts(ct.Structure):
 
 class rt_tuning(ct.Structure):
     _fields_ = [("kappa_t_per_block", ct.c_int32), ("walk_blocks_per_sm", ct.c_int32),
-                ("reserved", ct.c_int32 * 6)]
+                ("walk_refill_idle", ct.c_int32), ("reserved", ct.c_int32 * 5)]
 
 
-def set_tuning(kappa_t_per_block: int | None = None, walk_blocks_per_sm: int | None = None):
-    """Set process-wide launch shapes; arguments left as None keep their current value."""
+_TUNING_FIELDS = ("kappa_t_per_block", "walk_blocks_per_sm", "walk_refill_idle")
+
+
+def set_tuning(**shapes):
+    """Set process-wide launch shapes by field name (rt_tuning); others keep their value."""
     t = rt_tuning()
     _check(lib().rt_get_tuning(ct.byref(t)), "rt_get_tuning")
-    if kappa_t_per_block is not None:
-        t.kappa_t_per_block = int(kappa_t_per_block)
-    if walk_blocks_per_sm is not None:
-        t.walk_blocks_per_sm = int(walk_blocks_per_sm)
+    for k, v in shapes.items():
+        if k not in _TUNING_FIELDS:
+            raise TypeError(f"unknown tuning field {k!r}")
+        if v is not None:
+            setattr(t, k, int(v))
     _check(lib().rt_set_tuning(ct.byref(t)), "rt_set_tuning")
 
 
 def get_tuning() -> dict:
     t = rt_tuning()
     _check(lib().rt_get_tuning(ct.byref(t)), "rt_get_tuning")
-    return {"kappa_t_per_block": t.kappa_t_per_block, "walk_blocks_per_sm": t.walk_blocks_per_sm}
+    return {k: getattr(t, k) for k in _TUNING_FIELDS}
 
 
 class Batch:

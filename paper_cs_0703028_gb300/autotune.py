@@ -7,7 +7,7 @@ choice in a JSON file keyed by a signature of the workload's sizes
 
 * ``tune_kappa``: temperature nodes per rt_build_kappa block (1, 2, 4, 8).
 * ``tune_batch``: rays per work item and threads per block of the batched walk.
-* ``tune_walk``: resident blocks per SM the rt_trace walk is compiled for (4 or 5).
+* ``tune_walk``: resident blocks per SM (4 or 5) and refill threshold (8 or 16) of the rt_trace walk.
 """
 from __future__ import annotations
 
@@ -99,19 +99,23 @@ def tune_batch(grids, n_rays, spec, kappa, candidates=None, reps=2, use_cache=Tr
     return (rpi, th), times
 
 
-def tune_walk(grid_struct, ncells, spec, kappa, n_rays, candidates=(4, 5), reps=2, use_cache=True):
-    """Pick the walk's resident blocks per SM on the caller's trace; returns (best, {blocks: ms})."""
+def tune_walk(grid_struct, ncells, spec, kappa, n_rays, candidates=None, reps=2, use_cache=True):
+    """Pick the walk's (resident blocks per SM, refill threshold) on the caller's trace;
+    returns ((blocks, refill), {"blocks,refill": ms})."""
+    if candidates is None:
+        candidates = [(b, r) for b in (4, 5) for r in (8, 16)]
     key = f"walk:{ncells}:{spec.n_nu}:{spec.nT}:{int(n_rays)}"
     if use_cache and key in _load():
-        best = int(_load()[key]["best"])
-        set_tuning(walk_blocks_per_sm=best)
-        return best, _load()[key]["ms"]
+        b, r = (int(v) for v in _load()[key]["best"])
+        set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
+        return (b, r), _load()[key]["ms"]
     tally = Tally(ncells)
     times = {}
-    for c in candidates:
-        set_tuning(walk_blocks_per_sm=c)
-        times[int(c)] = _time(lambda: (tally.zero(), trace(grid_struct, kappa, spec, tally, n_rays)), reps)
+    for b, r in candidates:
+        set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
+        times[f"{b},{r}"] = _time(lambda: (tally.zero(), trace(grid_struct, kappa, spec, tally, n_rays)), reps)
     best = min(times, key=times.get)
-    set_tuning(walk_blocks_per_sm=best)
-    _store(key, {"best": best, "ms": times})
-    return best, times
+    b, r = (int(v) for v in best.split(","))
+    set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
+    _store(key, {"best": [b, r], "ms": times})
+    return (b, r), times

@@ -8,6 +8,7 @@
 //   k_reduce / k_final : deterministic two-pass binary64 sum of the absorbed
 //                 power and the energy balance.
 #include <cmath>
+#include <type_traits>
 
 #include "rt_common.cuh"
 #include "rt_walk.cuh"
@@ -32,12 +33,13 @@ __global__ void k_cell_prep(const float *__restrict__ T, const float *__restrict
 // Persistent walk: each warp owns a contiguous range of rays.  Lanes step their
 // own rays; when half of the warp's lanes are idle (ballot), the idle lanes take
 // the warp's next rays together, so ray set-up and stepping stay converged.
-constexpr int kRefillIdle = 16;
+constexpr int kRefillIdleDefault = 16;
 constexpr int kWalkUnroll = 8;  // steps per pass of the walk loop
 
 }  // namespace
 
-int g_walk_blocks = 5;  // resident walk blocks per SM the launch is compiled for (4 or 5)
+int g_walk_blocks = 5;   // resident walk blocks per SM the launch is compiled for (4 or 5)
+int g_walk_refill = 16;  // idle lanes that trigger a refill (8 or 16)
 
 namespace {
 
@@ -79,7 +81,7 @@ __global__ void k_pair_table(const float *__restrict__ in, int nT, long long n_n
   }
 }
 
-template <bool REC, int TAB, int MINB>
+template <bool REC, int TAB, int MINB, int REFILL>
 __global__ void __launch_bounds__(kWalkThreads, MINB)
 k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
        double *__restrict__ absorbed, double *__restrict__ scalars,
@@ -97,7 +99,7 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
   bool active = false;
   for (;;) {
     const unsigned idle = __ballot_sync(0xffffffffu, !active);
-    if (next < last && (idle == 0xffffffffu || __popc(idle) >= kRefillIdle)) {
+    if (next < last && (idle == 0xffffffffu || __popc(idle) >= REFILL)) {
       const unsigned rank = __popc(idle & ((1u << lane) - 1u));
       if (!active && next + rank < last) {
         ray_init(W, cells, tab, next + rank, record, R, &cd);
@@ -320,11 +322,14 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const bool rec = rp.cells != nullptr;
-  auto kern = g_walk_blocks == 4
-                  ? (rec ? (layout == 2 ? k_walk<true, 2, 4> : k_walk<true, 1, 4>)
-                         : (layout == 2 ? k_walk<false, 2, 4> : k_walk<false, 1, 4>))
-                  : (rec ? (layout == 2 ? k_walk<true, 2, 5> : k_walk<true, 1, 5>)
-                         : (layout == 2 ? k_walk<false, 2, 5> : k_walk<false, 1, 5>));
+  // visit recording (a test path) uses one configuration; the tuned shape otherwise
+  auto pick = [&](auto tab) {
+    constexpr int L = decltype(tab)::value;
+    if (rec) return k_walk<true, L, 5, kRefillIdleDefault>;
+    if (g_walk_blocks == 4) return g_walk_refill == 8 ? k_walk<false, L, 4, 8> : k_walk<false, L, 4, 16>;
+    return g_walk_refill == 8 ? k_walk<false, L, 5, 8> : k_walk<false, L, 5, 16>;
+  };
+  auto kern = layout == 2 ? pick(std::integral_constant<int, 2>()) : pick(std::integral_constant<int, 1>());
   int per_sm = 0;
   RT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkThreads, 0));
   if (per_sm < 1) per_sm = 1;
