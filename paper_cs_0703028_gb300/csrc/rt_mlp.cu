@@ -434,18 +434,20 @@ k_tc_selftest(const float *__restrict__ A, const float *__restrict__ B, float *_
 }
 
 // ---------------------------------------------------------------- surrogate walk
-constexpr int kWalkMlpThreads = 256;  // two 128-ray tiles share the resident weights
+constexpr int kWalkTiles = 3;                   // 128-ray tiles sharing the resident weights
+constexpr int kWalkMlpThreads = 128 * kWalkTiles;
+constexpr int kWalkTmemCols = 512;              // power of two >= kWalkTiles * kH
 
 struct WalkMlpSmem {
-  uint16_t W[3][kTileElems];  // W2..W4 (rows = out)
-  uint16_t A[2][kTileElems];  // layer inputs of the two tiles
+  uint16_t W[3][kTileElems];           // W2..W4 (rows = out)
+  uint16_t A[kWalkTiles][kTileElems];  // layer inputs of the tiles
   SmallParams sp;
   uint64_t bar_w, bar_mma;
   unsigned long long next;
   uint32_t tmem;
 };
 
-// Network output (log kappa) for this thread's query, all 256 threads together.
+// Network output (log kappa) for this thread's query, all threads of the block together.
 // Returns false if a bounded tensor-core wait ran out.
 __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__restrict__ P,
                                                uint32_t tmem, const Norm &N, const float (&raw)[4],
@@ -475,8 +477,8 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      tc::mma_128x128x128(tmem, S.A[0], S.W[l]);
-      tc::mma_128x128x128(tmem + kH, S.A[1], S.W[l]);
+#pragma unroll
+      for (int t = 0; t < kWalkTiles; ++t) tc::mma_128x128x128(tmem + (uint32_t)(t * kH), S.A[t], S.W[l]);
       tc::mma_commit(&S.bar_mma);
     }
     timeout = tc::mbar_wait(&S.bar_mma, phase, kWaitLimit) ? 0 : 1;
@@ -526,7 +528,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.next = begin;
   }
-  if (warp == 0) tc::tmem_alloc(&S.tmem, 2 * kH);
+  if (warp == 0) tc::tmem_alloc(&S.tmem, kWalkTmemCols);
   stage_small(S.sp, P);
   tc::fence_before_sync();
   __syncthreads();
@@ -600,7 +602,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 2 * kH);
+    tc::tmem_dealloc(tmem, kWalkTmemCols);
   }
 }
 
@@ -774,7 +776,7 @@ rt_status trace_mlp_impl(const rt_grid *grid, const float *params, const rt_mlp_
   int dev = 0, sms = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned long long want = (n_rays + 2047) / 2048;
+  const unsigned long long want = (n_rays + 8ull * kWalkMlpThreads - 1) / (8ull * kWalkMlpThreads);
   const unsigned blocks = (unsigned)(want < (unsigned long long)sms ? (want > 0 ? want : 1) : sms);
   k_walk_mlp<<<blocks, kWalkMlpThreads, sizeof(WalkMlpSmem), st>>>(
       params, scr.as<uint16_t>(), to_norm(nm), grid->T, grid->p_atm, grid->x, (float)spec->p_ref_atm,
