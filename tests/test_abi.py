@@ -103,3 +103,22 @@ def test_trace_rejects_bad_input_on_host():
     assert L.rt_trace(ct.byref(g), None, ct.byref(spec), 0, 10, 10, 0, 0, 0, ct.byref(t), None, None) == rt.RT_E_INVAL
     assert L.rt_tally(ct.byref(t), 0, None, None, None) == rt.RT_E_INVAL
     assert L.rt_status_read(None, None) == rt.RT_E_INVAL
+
+
+def test_tuning_round_trip_and_validation():
+    # launch shapes only; the calls touch no device
+    before = rt.get_tuning()
+    try:
+        rt.set_tuning(kappa_t_per_block=4, walk_blocks_per_sm=4, walk_refill_idle=8)
+        assert rt.get_tuning() == {"kappa_t_per_block": 4, "walk_blocks_per_sm": 4, "walk_refill_idle": 8}
+        rt.set_tuning(walk_refill_idle=16)  # other fields keep their value
+        assert rt.get_tuning()["walk_blocks_per_sm"] == 4
+        for bad in ({"kappa_t_per_block": 9}, {"walk_blocks_per_sm": 3}, {"walk_refill_idle": 12}):
+            with pytest.raises(rt.RtError):
+                rt.set_tuning(**bad)
+        with pytest.raises(TypeError):
+            rt.set_tuning(rays_per_block=1)
+        rt.set_tuning(kappa_t_per_block=0, walk_blocks_per_sm=0, walk_refill_idle=0)  # defaults
+        assert rt.get_tuning() == {"kappa_t_per_block": 8, "walk_blocks_per_sm": 5, "walk_refill_idle": 16}
+    finally:
+        rt.set_tuning(**before)
