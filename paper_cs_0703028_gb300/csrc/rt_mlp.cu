@@ -442,16 +442,30 @@ struct WalkMlpSmem {
   uint16_t W[3][kTileElems];           // W2..W4 (rows = out)
   uint16_t A[kWalkTiles][kTileElems];  // layer inputs of the tiles
   SmallParams sp;
-  uint64_t bar_w, bar_mma;
+  uint64_t bar_w, bar_mma[kWalkTiles];
   unsigned long long next;
   uint32_t tmem;
 };
 
-// Network output (log kappa) for this thread's query, all threads of the block together.
-// Returns false if a bounded tensor-core wait ran out.
-__device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__restrict__ P,
-                                               uint32_t tmem, const Norm &N, const float (&raw)[4],
-                                               uint32_t &phase, float &logk) {
+// The 128 threads of one tile (4 warps, named barrier 1 + tile) synchronise
+// among themselves only, so the tiles of a block drift apart and one tile's
+// epilogue runs while another tile's products occupy the tensor cores.
+__device__ __forceinline__ void tile_sync(int tile) {
+  asm volatile("barrier.cta.sync %0, 128;" ::"r"(1 + tile) : "memory");
+}
+__device__ __forceinline__ bool tile_or(int tile, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " barrier.cta.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r) : "r"((uint32_t)v), "r"(1 + tile) : "memory");
+  return r != 0;
+}
+
+// Network output (log kappa) for this thread's query, the 128 threads of its tile
+// together.  Returns false if a bounded tensor-core wait ran out.
+__device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, const Norm &N,
+                                              const float (&raw)[4], uint32_t &phase, float &logk) {
   const int tid = threadIdx.x, tile = tid >> 7, r = tid & 127, warp = tid >> 5;
   float u[4];
 #pragma unroll
@@ -469,27 +483,26 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
                    pack_bf16x2(h[6], h[7]));
   }
   float y = 0.0f;
-  int timeout = 0;
+  const uint32_t tcol = tmem + (uint32_t)(tile * kH);
 #pragma unroll 1
   for (int l = 0; l < 3; ++l) {
     tc::fence_smem_to_async();
     tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
+    tile_sync(tile);
+    if (r == 0) {
       tc::fence_after_sync();
-#pragma unroll
-      for (int t = 0; t < kWalkTiles; ++t) tc::mma_128x128x128(tmem + (uint32_t)(t * kH), S.A[t], S.W[l]);
-      tc::mma_commit(&S.bar_mma);
+      tc::mma_128x128x128(tcol, S.A[tile], S.W[l]);
+      tc::mma_commit(&S.bar_mma[tile]);
     }
-    timeout = tc::mbar_wait(&S.bar_mma, phase, kWaitLimit) ? 0 : 1;
+    const int timeout = tc::mbar_wait(&S.bar_mma[tile], phase, kWaitLimit) ? 0 : 1;
     phase ^= 1u;
-    if (__syncthreads_or(timeout)) return false;
+    if (tile_or(tile, timeout)) return false;
     tc::fence_after_sync();
     const float *bias = S.sp.b[l];
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float acc[32];
-      tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * kH + c0), acc);
+      tc::tmem_ld32(tcol + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, acc);
 #pragma unroll
       for (int i = 0; i < 32; i += 8) {
         float h[8];
@@ -507,6 +520,8 @@ __device__ __forceinline__ bool mlp_eval_tiles(WalkMlpSmem &S, const float *__re
       }
     }
   }
+  // this tile's accumulators are read before its next products overwrite them
+  tc::fence_before_sync();
   logk = N.mean + N.scale * (y + S.sp.b5);
   return true;
 }
@@ -524,7 +539,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   const unsigned long long end = W.n_rays * (blockIdx.x + 1) / gridDim.x;
   if (tid == 0) {
     tc::mbar_init(&S.bar_w, 1);
-    tc::mbar_init(&S.bar_mma, 1);
+    for (int t = 0; t < kWalkTiles; ++t) tc::mbar_init(&S.bar_mma[t], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     S.next = begin;
   }
@@ -545,6 +560,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   uint32_t phase = 0;
   Ray R;
   bool active = false;
+  const int tile = tid >> 7;
   if (!__syncthreads_or(timeout)) {
     for (;;) {
       if (!active) {
@@ -554,7 +570,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
           active = true;
         }
       }
-      if (!__syncthreads_or(active)) break;
+      if (!tile_or(tile, active)) break;  // this tile has no ray left
       float raw[4] = {N.lo[0], N.lo[1], N.lo[2], N.lo[3]};
       float Tc = 1.0f;
       if (active) {
@@ -565,7 +581,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
         raw[3] = Xf ? Xf[R.cell] : x_ref;
       }
       float logk = 0.0f;
-      if (!mlp_eval_tiles(S, P, tmem, N, raw, phase, logk)) {
+      if (!mlp_eval_tile(S, tmem, N, raw, phase, logk)) {
         timeout = 1;
         break;
       }
