@@ -42,6 +42,18 @@ __device__ __forceinline__ float tanh_approx(float x) {
 }
 __device__ __forceinline__ float sigmoid_fast(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
 
+// SiLU of two pre-activations, packed as the BF16 pair the next layer reads:
+// z rounded to BF16, then z (1/2 + tanh(z/2)/2) in packed BF16 arithmetic (the
+// surrogate walk's inference epilogue; training keeps its SiLU in binary32).
+__device__ __forceinline__ uint32_t silu_bf16x2(float lo, float hi) {
+  uint32_t z, r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(hi), "f"(lo));
+  asm("{\n .reg .b32 c, h, s;\n mov.b32 c, 0x3F003F00;\n mul.rn.bf16x2 h, %1, c;\n"
+      " tanh.approx.bf16x2 s, h;\n fma.rn.bf16x2 s, s, c, c;\n mul.rn.bf16x2 %0, %1, s;\n}"
+      : "=r"(r) : "r"(z));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
   const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
@@ -472,15 +484,12 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
   for (int i = 0; i < 4; ++i) u[i] = 2.0f * (raw[i] - N.lo[i]) / (N.hi[i] - N.lo[i]) - 1.0f;
 #pragma unroll 1
   for (int c0 = 0; c0 < kH; c0 += 8) {
-    float h[8];
+    float z[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float z = layer1(S.sp, c0 + i, u);
-      h[i] = z * sigmoid_fast(z);
-    }
+    for (int i = 0; i < 8; ++i) z[i] = layer1(S.sp, c0 + i, u);
     *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0)]) =
-        make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
-                   pack_bf16x2(h[6], h[7]));
+        make_uint4(silu_bf16x2(z[0], z[1]), silu_bf16x2(z[2], z[3]), silu_bf16x2(z[4], z[5]),
+                   silu_bf16x2(z[6], z[7]));
   }
   float y = 0.0f;
   const uint32_t tcol = tmem + (uint32_t)(tile * kH);
@@ -503,20 +512,23 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float acc[32];
       tc::tmem_ld32(tcol + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, acc);
+      if (l < 2) {  // next layer's BF16 input
 #pragma unroll
-      for (int i = 0; i < 32; i += 8) {
-        float h[8];
+        for (int i = 0; i < 32; i += 8) {
+          float z[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int c = c0 + i + q;
-          const float z = acc[i + q] + bias[c];
-          h[q] = z * sigmoid_fast(z);
-          if (l == 2) y = fmaf(S.sp.w5[c], h[q], y);
-        }
-        if (l < 2)
+          for (int q = 0; q < 8; ++q) z[q] = acc[i + q] + bias[c0 + i + q];
           *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0 + i)]) =
-              make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
-                         pack_bf16x2(h[6], h[7]));
+              make_uint4(silu_bf16x2(z[0], z[1]), silu_bf16x2(z[2], z[3]), silu_bf16x2(z[4], z[5]),
+                         silu_bf16x2(z[6], z[7]));
+        }
+      } else {  // last hidden layer: binary32 SiLU into the head
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int c = c0 + q;
+          const float z = acc[q] + bias[c];
+          y = fmaf(S.sp.w5[c], z * sigmoid_fast(z), y);
+        }
       }
     }
   }
