@@ -29,7 +29,7 @@ namespace {
 constexpr int kPtsPerThread = 8;
 constexpr int kTilePts = 32 * kPtsPerThread;  // 256 wavenumbers per block, one warp per T node
 constexpr int kMaxTPerBlock = 8;              // warps (T nodes) per block
-constexpr int kChunk = 64;                    // lines per staged chunk
+constexpr int kChunk = 96;                    // lines per staged chunk
 constexpr int kGroup = 8;                     // fast-path lines summed before one compensated add
 constexpr unsigned kWaitLimit = 1u << 22;                // bounded mbarrier waits
 
