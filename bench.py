@@ -263,6 +263,11 @@ def run_gpu(args):
     ops = evals_per_step * OPS_PER_EVAL[spec.profile]
     achieved = ops / (ms_build * 1e-3) / 1e12
     traffic = _profiled_traffic("k_kappa_box32_voigt20k.md", ["rt_kappa.cu", "rt_common.cuh"])
+    # the walk, second kernel of the step: algorithmic 12 B per ray-cell step (the cell's
+    # 4-byte T bracket and two 4-byte kappa gathers) against HBM
+    hbm_peak = _peaks().get("hbm_gbs", 6771.5)
+    walk_gbs = steps_per_step * 12 / (ms_trace * 1e-3) / 1e9
+    walk_traffic = _profiled_traffic("k_walk_box32_voigt20k.md", ["rt_trace.cu", "rt_walk.cuh", "rt_common.cuh"])
     out = {
         "metric": "ray-cell steps/s + line-profile evals/s; surrogate vs plain at <=1% tally err",
         "value": value,
@@ -299,6 +304,10 @@ def run_gpu(args):
                      "timed": "rt_build_kappa (k_kappa and its three small set-up kernels)"},
         "e2e": {"value": e2e_value, "unit": "ray-cell steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "walk_roofline": {"kernel": "k_walk (rt_trace)", "bound": "hbm", "achieved": walk_gbs,
+                          "peak": hbm_peak, "unit": "GB/s", "frac": walk_gbs / hbm_peak,
+                          "traffic": walk_traffic, "bytes_per_step": 12,
+                          "note": "tables L2-resident; latency- and issue-bound (profiles/)"},
         "clocks": clocks,
     }
     if world == 1 and not args.no_surrogate:
