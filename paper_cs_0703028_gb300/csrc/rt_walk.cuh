@@ -246,9 +246,8 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
 
   const float ds = __fsub_rn(tn, R.t);
   const float a = kap > 0.0f ? __fmul_rn(__fmul_rn(kap, 100.0f), ds) : 0.0f;
-  const float dep = R.w * R.trans * one_minus_exp_neg(a);
-  if (writes && dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
-  // compensated optical depth, transmission exp(-tau)
+  const float trans0 = R.trans;
+  // compensated optical depth
   {
     const float y = __fsub_rn(a, R.tc);
     const float sum = __fadd_rn(R.tau, y);
@@ -256,7 +255,13 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
     const bool opaque = a == INFINITY;
     R.tau = opaque ? INFINITY : sum;
     R.tc = opaque ? R.tc : tcn;
-    R.trans = opaque ? 0.0f : __expf(__fsub_rn(R.tc, R.tau));
+  }
+  // deposit and transmission exp(-tau); once the transmission has underflowed to
+  // zero it stays zero (tau only grows), so a dark ray skips both exponentials
+  if (trans0 != 0.0f) {
+    const float dep = R.w * trans0 * one_minus_exp_neg(a);
+    if (writes && dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
+    R.trans = a == INFINITY ? 0.0f : __expf(__fsub_rn(R.tc, R.tau));
   }
   if (REC && writes && R.row >= 0 && R.nv < W.rec_max) {
     rec.cells[(long long)R.row * W.rec_max + R.nv] = R.cell;
