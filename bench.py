@@ -250,6 +250,24 @@ def run_gpu(args):
         e_ms += e0.elapsed_time(e1)
     e2e_value = steps_per_step * world / (e_ms / args.steps * 1e-3)
 
+    # for context (not the metric): the same trace with the optical-depth cut, which
+    # stops rays once tau > 100 (lost fraction < 4e-44) and so counts fewer visits
+    cut = rt.Tally(grid.ncells)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    for rep in range(2):
+        cut.zero()
+        c0.record(stream)
+        st = L.rt_trace(ct.byref(gs), ct.c_void_p(kappa.data_ptr()), ct.byref(S), ray_begin, n_rays,
+                        n_total, case.seed, 0, rt.RT_TAU_CUT, ct.byref(cut.buf), None, sp)
+        c1.record(stream)
+        if st:
+            raise rt.RtError(st, "rt_trace (tau cut)", L.rt_last_error().decode())
+    torch.cuda.synchronize()
+    _, cut_sc, _ = cut.read()
+    cut_info = {"trace_ms": c0.elapsed_time(c1), "ray_cell_steps": int(cut.steps.item()),
+                "absorbed_total_rel_diff": abs(float(cut_sc[1]) - float(host_sc[1])) / float(host_sc[1])}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -308,6 +326,7 @@ def run_gpu(args):
                           "peak": hbm_peak, "unit": "GB/s", "frac": walk_gbs / hbm_peak,
                           "traffic": walk_traffic, "bytes_per_step": 12,
                           "note": "tables L2-resident; latency- and issue-bound (profiles/)"},
+        "trace_with_tau_cut": cut_info,
         "clocks": clocks,
     }
     if world == 1 and not args.no_surrogate:
