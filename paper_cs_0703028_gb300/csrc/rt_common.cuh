@@ -110,12 +110,11 @@ __device__ __forceinline__ df df_from_double(double v) {
 //                                    + 105 t^4 (9 - 120s + 432s^2 - 576s^3 + 256s^4)/16 + ...]
 //             (Im z^(2n+1) expanded with x^2 t = 1 - s); three terms for |z| >= 20,
 //             five for 8 <= |z| < 20;
-//  5 <= |z| < 8 : Laplace's continued fraction for w, depth 6 (the imaginary parts
-//             of its partial denominators add without cancellation);
-//  |z| < 5  : Weideman's (1994) rational series in Z = (L + iz)/(L - iz), N = 24,
+//  |z| < 8  : Weideman's (1994) rational series in Z = (L + iz)/(L - iz), N = 24,
 //             coefficients from the Fourier series of exp(-t^2)(L^2 + t^2) on the
-//             tan-mapped line (computed on the host in binary64).
-// Measured relative error against binary64: <= 5.3e-7 for |z| >= 8, <= 7e-7 for
+//             tan-mapped line (computed on the host in binary64); its method error
+//             is below 2e-9 relative there, the rest is binary32 rounding.
+// Measured relative error against binary64: <= 5.3e-7 for |z| >= 8, <= 2.2e-6 for
 // 5 <= |z| < 8, <= 1.5e-6 for |z| < 5 with y >= 0.5 (degrading toward 1e-4 as y -> 0).
 constexpr int kWeidN = 24;
 struct WeidCoef {
@@ -139,17 +138,6 @@ __device__ __forceinline__ float faddeeva_series5(float t, float s) {
   return fmaf(t, fmaf(t, fmaf(t, fmaf(t, c4, c3), c2), c1), 1.0f);
 }
 
-__device__ __forceinline__ float faddeeva_re_cf(float x, float y) {
-  float dr = x, di = y;
-#pragma unroll
-  for (int k = 6; k >= 1; --k) {
-    const float t = __fdividef(0.5f * (float)k, dr * dr + di * di);
-    dr = x - t * dr;
-    di = y + t * di;
-  }
-  return __fdividef(di, dr * dr + di * di);
-}
-
 __device__ __forceinline__ float faddeeva_re_core(float x, float y, const WeidCoef &c) {
   // iz = -y + i x;  d = L - iz = (L + y) - i x;  n = L + iz = (L - y) + i x
   const float dr = c.L + y, di = -x;
@@ -171,13 +159,12 @@ __device__ __forceinline__ float faddeeva_re_core(float x, float y, const WeidCo
   return vr * qr - vi * qi;
 }
 
-// sqrt(pi) Re w(x + iy) for |z|^2 = r2 below 400 (the five-term, fraction and core regions)
+// sqrt(pi) Re w(x + iy) for |z|^2 = r2 below 400 (the five-term and rational-series regions)
 __device__ __forceinline__ float faddeeva_re_near(float x, float y, float r2, const WeidCoef &c) {
   if (r2 >= 64.0f) {
     const float t = __fdividef(1.0f, r2);
     return y * t * faddeeva_series5(t, y * y * t);
   }
-  if (r2 >= 25.0f) return faddeeva_re_cf(x, y);
   return faddeeva_re_core(x, y, c);
 }
 
