@@ -257,7 +257,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
           const float *__restrict__ dy, float *__restrict__ G, uint32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const long long row = (long long)blockIdx.x * kH + tid;
   const bool valid = row < n;
 
