@@ -570,6 +570,9 @@ def run_box128(args):
            "build_ms": ms_build, "evals": ev, "line_profile_evals_per_s": ev / (ms_build * 1e-3),
            "trace_ms": ms_trace, "steps": steps, "energy_residual": float(sc[3]),
            "walk_hbm_frac_at_16B_per_step": steps * 16 / (ms_trace * 1e-3) / (hbm * 1e9),
+           "build_alu_frac": ev * OPS_PER_EVAL[spec.profile] / (ms_build * 1e-3)
+           / (torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM
+              * _peaks().get("sm_max_mhz", 2070.0) * 1e6),
            "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
                       "walk_candidates_ms_1e7_rays": walk_ms}}
     print(json.dumps(res), flush=True)

@@ -376,8 +376,9 @@ rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
  * (p_cell = p_ref, x_cell = x_ref where the grid has no p / x field; no table,
  * no interpolation, no density scaling).  The rays, walk, deposits and tallies
  * are those of rt_trace; the emission weight uses the network's kappa of the
- * emitting cell.  Rays are processed 256 per block, the queries of all live
- * rays evaluated together on the tensor cores at every step.
+ * emitting cell.  Rays are processed in 128-ray tiles, several tiles per block
+ * sharing the resident weights; each tile's live rays' queries are evaluated
+ * together on the tensor cores at every step.
  */
 rt_status rt_trace_mlp(const rt_grid *grid, const float *params, const rt_mlp_norm *norm,
                        const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays,
