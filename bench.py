@@ -27,12 +27,30 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 FP32_LANES_PER_SM = 128
-# algorithmic work of one profile evaluation in lane operations (one binary32
-# arithmetic instruction or one MUFU reciprocal per lane, FMA = 1): a far-wing
-# Voigt evaluation is 1 reciprocal + 6 binary32 operations (grid coordinate,
-# |z|^2, series, accumulation and its share of the Kahan update); Lorentz is
-# 1 reciprocal + 4.  The peak is one lane operation per FP32 lane per clock.
-OPS_PER_EVAL = {"voigt": 7, "lorentz": 5}
+MUFU_LANES_PER_SM = 16
+# algorithmic work of one profile evaluation, per pipe, in lane operations (FMA = 1):
+# a far-wing Voigt evaluation is 1 MUFU reciprocal + 6 binary32 operations (grid
+# coordinate, |z|^2, series, accumulation and its share of the Kahan update);
+# Lorentz is 1 reciprocal + 4.  The roofline is set by the pipe with the larger
+# (count / measured rate): max(FP32 ops / FP32 rate, MUFU ops / MUFU rate).
+OPS_PER_EVAL = {"voigt": {"mufu": 1, "fp32": 6}, "lorentz": {"mufu": 1, "fp32": 4}}
+
+
+def alu_roofline(evals_per_s, profile, probe, n_sm, clock_mhz):
+    """Roofline of the line sum from the measured FP32 and MUFU ceilings (rt_alu_probe)."""
+    ops = OPS_PER_EVAL[profile]
+    rate = {"fp32": probe["fma_lane_ops_per_s"], "mufu": probe["rcp_lane_ops_per_s"]}
+    pipe = max(ops, key=lambda k: ops[k] / rate[k])
+    other = "fp32" if pipe == "mufu" else "mufu"
+    achieved = evals_per_s * ops[pipe] / 1e12
+    peak = rate[pipe] / 1e12
+    return {"bound": "alu", "pipe": {"mufu": "MUFU reciprocal", "fp32": "FP32"}[pipe],
+            "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "other_pipe_frac": evals_per_s * ops[other] / rate[other],
+            "ops_per_eval": ops,
+            "peak_source": "measured by rt_alu_probe (independent chains on every SM)",
+            "derived_peaks_tops": {"fp32": n_sm * FP32_LANES_PER_SM * clock_mhz * 1e6 / 1e12,
+                                   "mufu": n_sm * MUFU_LANES_PER_SM * clock_mhz * 1e6 / 1e12}}
 
 
 def _dist():
@@ -277,9 +295,9 @@ def run_gpu(args):
     clocks = _clock_summary(clk_path, local) if sampler else None
     sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     props = torch.cuda.get_device_properties(local)
-    alu_peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_clock_mhz * 1e6 / 1e12
-    ops = evals_per_step * OPS_PER_EVAL[spec.profile]
-    achieved = ops / (ms_build * 1e-3) / 1e12
+    probe = rt.alu_probe()  # measured FP32 and MUFU ceilings
+    roof = alu_roofline(evals_per_step / (ms_build * 1e-3), spec.profile, probe,
+                        props.multi_processor_count, sm_clock_mhz)
     traffic = _profiled_traffic("k_kappa_box32_voigt20k.md", ["rt_kappa.cu", "rt_common.cuh"])
     # the walk, second kernel of the step: algorithmic 12 B per ray-cell step (the cell's
     # 4-byte T bracket and two 4-byte kappa gathers) against HBM
@@ -313,12 +331,7 @@ def run_gpu(args):
         "gpu_launches": 9 * args.steps,
         "tuning": {"walk_blocks_per_sm": walk_blocks[0], "walk_refill_idle": walk_blocks[1],
                    "walk_candidates_ms": walk_tune_ms},
-        "roofline": {"kernel": "k_kappa (rt_build_kappa)", "bound": "alu", "achieved": achieved,
-                     "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-                     "traffic": traffic,
-                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
-                                    f"{sm_clock_mhz:.0f} MHz, one lane operation per clock",
-                     "ops_per_eval": OPS_PER_EVAL[spec.profile],
+        "roofline": {"kernel": "k_kappa (rt_build_kappa)", **roof, "traffic": traffic,
                      "timed": "rt_build_kappa (k_kappa and its three small set-up kernels)"},
         "e2e": {"value": e2e_value, "unit": "ray-cell steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -444,6 +457,7 @@ def surrogate_summary(args):
             "speedup_vs_lbl": r["speedup_vs_lbl"],
             "tally_error_vs_table_median": r["tally_error_vs_table"]["median"],
             "meets_1pct_target": r["tally_error_vs_table"]["max"] <= 0.01,
+            "tensor_roofline": r["tensor_roofline"],
             "training": r["training"]}
 
 
@@ -496,6 +510,17 @@ def run_surrogate(args):
                                     "total": float(tallies["mlp"].sum() / ref.sum() - 1.0)},
            "training": {"seconds": train_s, "samples": args.samples, "epochs": args.epochs,
                         "loss_first": hist[0][1], "loss_last": hist[-1][1]}}
+    # tensor-core work: three 128x128 layers, 2 * 128 * 128 flops each per network evaluation
+    # (one per ray-cell step in the walk; forward + two backward products per training sample)
+    peak = _peaks().get("bf16_tflops", 1978.3)
+    eval_flops = 3 * 2 * 128 * 128
+    walk_tf = out["mlp"]["ray_cell_steps_per_s"] * eval_flops / 1e12
+    train_tf = args.samples * args.epochs * 3 * eval_flops / train_s / 1e12
+    res["tensor_roofline"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                              "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)",
+                              "walk_achieved": walk_tf, "walk_frac": walk_tf / peak,
+                              "training_achieved": train_tf, "training_frac": train_tf / peak,
+                              "training_note": "wall clock incl. sampling and Adam; 8192-sample batches"}
     print(json.dumps(res), flush=True)
 
 
@@ -570,9 +595,9 @@ def run_box128(args):
            "build_ms": ms_build, "evals": ev, "line_profile_evals_per_s": ev / (ms_build * 1e-3),
            "trace_ms": ms_trace, "steps": steps, "energy_residual": float(sc[3]),
            "walk_hbm_frac_at_16B_per_step": steps * 16 / (ms_trace * 1e-3) / (hbm * 1e9),
-           "build_alu_frac": ev * OPS_PER_EVAL[spec.profile] / (ms_build * 1e-3)
-           / (torch.cuda.get_device_properties(0).multi_processor_count * FP32_LANES_PER_SM
-              * _peaks().get("sm_max_mhz", 2070.0) * 1e6),
+           "build_roofline": alu_roofline(ev / (ms_build * 1e-3), spec.profile, rt.alu_probe(),
+                                          torch.cuda.get_device_properties(0).multi_processor_count,
+                                          _peaks().get("sm_max_mhz", 2070.0)),
            "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
                       "walk_candidates_ms_1e7_rays": walk_ms}}
     print(json.dumps(res), flush=True)

@@ -412,6 +412,15 @@ rt_status rt_trace_lbl(const rt_grid *grid, const rt_lines *lines, const rt_spec
  * (rounded to BF16), D FP32 row-major [128][128].  Asynchronous. */
 rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream);
 
+/*
+ * rt_alu_probe -- measured ALU ceilings of the current GPU, for the line sum's
+ * roofline: out[0] = binary32 FMA lane operations per second, out[1] = MUFU
+ * reciprocal (rcp.approx) lane operations per second, each from a kernel of
+ * independent chains filling every SM, best of three timed launches (CUDA
+ * events).  Synchronises the stream.
+ */
+rt_status rt_alu_probe(double *out, void *stream);
+
 /* Synchronise the stream and translate a device status word into an rt_status. */
 rt_status rt_status_read(const uint32_t *status, void *stream);
 

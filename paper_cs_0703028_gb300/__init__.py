@@ -89,6 +89,7 @@ _SIGNATURES = {
     "rt_mlp_train_step": ([_P, _P, _P, _P, _P, _P, ct.c_int64, _P, ct.c_float, ct.c_int32, ct.c_int32,
                            _P, _P, _P], ct.c_int),
     "rt_tc_selftest": ([_P, _P, _P, _P, _P], ct.c_int),
+    "rt_alu_probe": ([_P, _P], ct.c_int),
     "rt_trace_mlp": ([_P, _P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
                       ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_mlp_make_samples": ([_P, ct.c_int32, _P, _P, ct.c_float, ct.c_float, ct.c_uint64, ct.c_int64,
@@ -446,3 +447,11 @@ def march(grid_struct, kappa, spec, pos, dirs, I_in=None, want_I=True, stream=No
                         _ptr(I_in), _ptr(I_out), _ptr(power), None, _stream_ptr(stream))
     _check(st, "rt_march")
     return I_out, power
+
+
+def alu_probe(stream=None) -> dict:
+    """rt_alu_probe: measured binary32 FMA and MUFU reciprocal lane operations per second."""
+    import numpy as np
+    out = np.zeros(2, dtype=np.float64)
+    _check(lib().rt_alu_probe(out.ctypes.data, _stream_ptr(stream)), "rt_alu_probe")
+    return {"fma_lane_ops_per_s": float(out[0]), "rcp_lane_ops_per_s": float(out[1])}
