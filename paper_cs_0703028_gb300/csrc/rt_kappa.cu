@@ -9,9 +9,10 @@
 //                     arithmetic for the Boltzmann exponent; for Voigt lines
 //                     also the far-wing polynomial coefficients.
 //   k_tile_lines    : per 256-point wavenumber tile, the range of lines whose
-//                     windows reach it and the sub-ranges of lines that cover
-//                     the whole tile far from their centres (no masking and no
-//                     near-centre points: the fast path).
+//                     windows reach it, split into segments by kind: far lines
+//                     (degree-1 or degree-2 far-wing series, masked where the
+//                     window ends inside the tile), covering lines with the
+//                     degree-4 series, and the general path (near-centre zone).
 //   k_kappa         : per (tile, up to 8 T nodes), the line sum.  The tile's
 //                     lines are staged in shared memory by bulk asynchronous
 //                     copies (cp.async.bulk + mbarrier), double buffered; each
@@ -31,7 +32,7 @@ constexpr int kTilePts = 32 * kPtsPerThread;  // 256 wavenumbers per block, one 
 constexpr int kMaxTPerBlock = 8;              // warps (T nodes) per block
 constexpr int kChunk = 96;                    // lines per staged chunk
 constexpr int kGroup = 8;                     // fast-path lines summed before one compensated add
-constexpr unsigned kWaitLimit = 1u << 22;                // bounded mbarrier waits
+constexpr unsigned kWaitLimit = 1u << 22;     // bounded mbarrier waits
 
 // CODATA 2018 (SI); derived quantities are formed on the host in binary64.
 constexpr double kH = 6.62607015e-34, kC = 299792458.0, kKB = 1.380649e-23;
