@@ -92,6 +92,12 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
   unsigned long long next = W.n_rays * wid / nwarps;
   const unsigned long long last = W.n_rays * (wid + 1) / nwarps;
   const bool record = REC;
+  __shared__ int4 s_axes[3];  // per axis {n, cell stride, h bits}
+  if (threadIdx.x < 3) {
+    const int a = threadIdx.x;
+    s_axes[a] = make_int4(W.n[a], a == 0 ? 1 : (a == 1 ? W.n[0] : W.n[0] * W.n[1]), __float_as_int(W.h[a]), 0);
+  }
+  __syncthreads();
   double em = 0.0, esc = 0.0;
   unsigned long long nsteps = 0;
   Ray R;
@@ -117,7 +123,8 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
       if (!done) {
         const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
         float4 cdn = cd;
-        done = ray_step<REC>(W, kap, absorbed, status, rec, R, true, [&](int c) { cdn = __ldg(cells + c); });
+        done = ray_step<REC, true, true>(W, kap, absorbed, status, rec, R, true,
+                                         [&](int c) { cdn = __ldg(cells + c); }, s_axes);
         cd = cdn;
       }
     }

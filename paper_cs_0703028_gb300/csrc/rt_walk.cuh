@@ -228,18 +228,32 @@ struct NoPrefetch {
 // EARLY_EXIT selects returns at each stop condition (faster in the table walk)
 // or one combined stop flag with an unconditional advance (faster in the
 // batched walk); both give the same visits and deposits.
-template <bool REC = true, bool EARLY_EXIT = true, typename Prefetch = NoPrefetch>
+// AXES: the chosen axis's {n, cell stride, h bits} come from one 16-byte load of
+// axes[axis] (a per-block shared-memory copy of the grid) instead of selects
+// among constant-bank values.
+template <bool REC = true, bool EARLY_EXIT = true, bool AXES = false, typename Prefetch = NoPrefetch>
 __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double *__restrict__ absorbed,
                                          uint32_t *status, const RecordPtrs &rec, Ray &R,
-                                         bool writes = true, Prefetch pf = Prefetch()) {
+                                         bool writes = true, Prefetch pf = Prefetch(),
+                                         const int4 *axes = nullptr) {
   const bool a0 = R.tx <= R.ty && R.tx <= R.tz;
   const bool a1 = !a0 && R.ty <= R.tz;
   const float tn = a0 ? R.tx : (a1 ? R.ty : R.tz);
   const float iv = a0 ? R.ivx : (a1 ? R.ivy : R.ivz);
   const int st = iv > 0.0f ? 1 : -1;
   const int inew = (a0 ? R.ix : (a1 ? R.iy : R.iz)) + st;
-  const int nax = a0 ? W.n[0] : (a1 ? W.n[1] : W.n[2]);
-  const int stride = a0 ? 1 : (a1 ? W.n[0] : W.n[0] * W.n[1]);
+  int nax, stride;
+  float h;
+  if (AXES) {
+    const int4 c = axes[a0 ? 0 : (a1 ? 1 : 2)];
+    nax = c.x;
+    stride = c.y;
+    h = __int_as_float(c.z);
+  } else {
+    nax = a0 ? W.n[0] : (a1 ? W.n[1] : W.n[2]);
+    stride = a0 ? 1 : (a1 ? W.n[0] : W.n[0] * W.n[1]);
+    h = a0 ? W.h[0] : (a1 ? W.h[1] : W.h[2]);
+  }
   const bool inside = tn != INFINITY && inew >= 0 && inew < nax;
   const int cnext = R.cell + st * stride;
   if (inside) pf(cnext);
@@ -284,7 +298,6 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
   }
   R.t = tn;
   R.cell = cnext;
-  const float h = a0 ? W.h[0] : (a1 ? W.h[1] : W.h[2]);
   const float ps = a0 ? R.px : (a1 ? R.py : R.pz);
   const float tm = tmax_of(inew, st, h, ps, iv);
   R.ix = a0 ? inew : R.ix;
