@@ -61,6 +61,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
   // the current item's enclosure (walk parameters and tally pointers), one slot
   // per warp, read like the constant bank
   __shared__ __align__(16) EnclDev s_e[8];
+  __shared__ int4 s_axes[8][3];  // per warp slot: per axis {n, cell stride, h bits}
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const RecordPtrs rec{nullptr, nullptr, nullptr, nullptr, nullptr};
   const EnclDev &D = s_e[warp];
@@ -75,6 +76,10 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
       const uint32_t *src = reinterpret_cast<const uint32_t *>(E + e);
       uint32_t *dst = reinterpret_cast<uint32_t *>(&s_e[warp]);
       for (int w = lane; w < (int)(sizeof(EnclDev) / 4); w += 32) dst[w] = src[w];
+      __syncwarp();
+      if (lane < 3)
+        s_axes[warp][lane] = make_int4(W.n[lane], lane == 0 ? 1 : (lane == 1 ? W.n[0] : W.n[0] * W.n[1]),
+                                       __float_as_int(W.h[lane]), 0);
       __syncwarp();
     }
     const float4 *cells = cells_all + D.cell_off;
@@ -103,8 +108,8 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
         if (!done) {
           const float kap = cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
           float4 cdn = cd;
-          done = ray_step<false, false>(W, kap, D.absorbed, D.status, rec, R, true,
-                                        [&](int c) { cdn = __ldg(cells + c); });
+          done = ray_step<false, false, true>(W, kap, D.absorbed, D.status, rec, R, true,
+                                              [&](int c) { cdn = __ldg(cells + c); }, s_axes[warp]);
           cd = cdn;
         }
       }
