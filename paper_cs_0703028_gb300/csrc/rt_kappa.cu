@@ -113,7 +113,7 @@ __global__ void k_line_geometry(const double *__restrict__ nu0, const double *__
 }
 
 // Eq. (S) times the number density, and the profile's coefficients, for line l
-// at T node k.  Voigt: P = {c0, s dnu, y^2, c2}, P2 = {c3, c4, near half-width, 0}
+// at T node k.  Voigt: P = {c0, s dnu, y^2, c2}, P2 = {c3, c4, half-widths of |z| < 20 and < 10}
 // with the far-wing series c0 t + c1 t^2 + c2 t^3 + c3 t^4 + c4 t^5 (c1 = 1.5 c0).
 // Writes the line's far-zone distances in grid units (float bits): beyond far[0]
 // the t^4 and t^5 terms are below 2^-24 of the value (27 y^2 t^3 <= 2^-24 with
@@ -163,7 +163,9 @@ __device__ __forceinline__ void prefactor_one(const double *__restrict__ nu0, co
     // far wing: c0 t (1 + 1.5 t + (3.75 - 2 y^2) t^2 - 15 y^2 t^3 + 12 y^4 t^4), t = 1/|z|^2
     const float c0 = A * s * (float)(1.0 / kPi) * y;
     out = make_float4(c0, sd, y2, __fmaf_rn(-2.0f, y2, 3.75f) * c0);
-    P2out[(long long)k * Q.n_lines + l] = make_float4(-15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near, 0.0f);
+    // half-width (grid units) of |z| < 10, inside which the general path queues points
+    const float u_core = sqrtf(fmaxf(100.0f - y2, 0.0f)) / sd;
+    P2out[(long long)k * Q.n_lines + l] = make_float4(-15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near, u_core);
     // (27 y^2 / 2^-24)^(1/6) = 27.66 y^(1/3) and (2^25 (3.75 + 2 y^2))^(1/4), with 5 %
     // margin, in grid units
     const float d2 = 29.1f * cbrtf(y) / sd;
@@ -518,23 +520,30 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
           const float4 p2 = sP[b][kPSets - 1][wsel][i];
           const float y2 = p.z;
           const float xt = p.y * ul;
+          // four-term series, valid for |z| >= 10: the degree-4 polynomial plus the
+          // fourth term 15 t^3 (7 - 56 s + 112 s^2 - 64 s^3) / 8, s = y^2 t, in t
+          const float q1 = y2 * p.x, q2 = q1 * y2;
+          const float c3 = __fmaf_rn(13.125f, p.x, p2.x), c4 = __fmaf_rn(-105.0f, q1, p2.y);
+          const float c5 = 210.0f * q2, c6 = -120.0f * q2 * y2;
           float xs[kPtsPerThread];
 #pragma unroll
           for (int q = 0; q < kPtsPerThread; ++q) {
             xs[q] = __fmaf_rn(p.y, (float)q, xt);
             const float t = rcp_approx(__fmaf_rn(xs[q], xs[q], y2));
-            const float h =
-                __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.y, p2.x), p.w), 1.5f * p.x), p.x);
+            const float h = __fmaf_rn(
+                t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, c6, c5), c4), c3), p.w),
+                             1.5f * p.x),
+                p.x);
             v[q] = t * h;
           }
-          // warp-uniform: the tile's offsets [fu, fu + kTilePts) meet the near region
+          // warp-uniform: the tile's offsets [fu, fu + kTilePts) meet the region |z| < 10
           const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);
-          if (fu < p2.z + 1.0f && fu + (float)kTilePts > -p2.z - 1.0f) {
-            // compact this warp's near-centre points so one pass of the lanes evaluates them
+          if (fu < p2.w + 1.0f && fu + (float)kTilePts > -p2.w - 1.0f) {
+            // compact this warp's points with |z| < 10 so one pass of the lanes evaluates them
             unsigned nearbits = 0;
 #pragma unroll
             for (int q = 0; q < kPtsPerThread; ++q)
-              nearbits |= (__fmaf_rn(xs[q], xs[q], y2) < 400.0f ? 1u : 0u) << q;
+              nearbits |= (__fmaf_rn(xs[q], xs[q], y2) < 100.0f ? 1u : 0u) << q;
             const int cnt_n = __popc(nearbits);
             int pre = cnt_n;
 #pragma unroll
