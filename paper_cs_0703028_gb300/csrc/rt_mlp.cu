@@ -450,14 +450,62 @@ constexpr int kWalkTiles = 3;                   // 128-ray tiles sharing the res
 constexpr int kWalkMlpThreads = 128 * kWalkTiles;
 constexpr int kWalkTmemCols = 512;              // power of two >= kWalkTiles * kH
 
+// Layer 1 (K = 4) on the tensor cores as one K = 16 product: each input u_i and
+// weight w_i split into BF16 high and low parts, u w ~ u_hi w_hi + u_hi w_lo + u_lo w_hi
+// (the dropped u_lo w_lo is below 2^-16 of the term), and the bias as b_hi + b_lo
+// against two constant-one columns: the products are exact in the FP32
+// accumulator, so z keeps about 16 significant bits.
+constexpr int kL1K = 16;
+constexpr int kL1Elems = kH * kL1K;
+
+// column k of the layer-1 operands: 3i + {0, 1, 2} for input i, 12 and 13 the bias
+__device__ __forceinline__ int l1_index(int r, int k) { return (int)(tc::kmajor_offset(r, k, kL1K) >> 1); }
+
+struct WalkSmall {
+  float b[4][kH];  // zeros (layer 1's bias is in its product), b2, b3, b4
+  float w5[kH];
+  float b5;
+};
+
 struct WalkMlpSmem {
   uint16_t W[3][kTileElems];           // W2..W4 (rows = out)
   uint16_t A[kWalkTiles][kTileElems];  // layer inputs of the tiles
-  SmallParams sp;
+  uint16_t A1[kWalkTiles][kL1Elems];   // layer-1 inputs (hi/lo split, K = 16)
+  uint16_t B1[kL1Elems];               // layer-1 weights and bias (hi/lo split, rows = out)
+  WalkSmall sp;
   uint64_t bar_w, bar_mma[kWalkTiles];
   unsigned long long next;
   uint32_t tmem;
 };
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float bf16_value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+
+// the walk's parameters in shared memory: layer-1 operand B, biases and head
+__device__ __forceinline__ void stage_walk(WalkMlpSmem &S, const float *__restrict__ P) {
+  for (int e = threadIdx.x; e < kL1Elems; e += blockDim.x) {
+    const int n = e / kL1K, k = e % kL1K;
+    uint16_t bits = 0;
+    if (k < 12) {
+      const float w = P[oW1 + 4 * n + k / 3];
+      const uint16_t hi = bf16_bits(w);
+      bits = (k % 3 == 1) ? bf16_bits(w - bf16_value(hi)) : hi;
+    } else if (k < 14) {
+      const float b = P[oB1 + n];
+      const uint16_t hi = bf16_bits(b);
+      bits = (k == 13) ? bf16_bits(b - bf16_value(hi)) : hi;
+    }
+    S.B1[l1_index(n, k)] = bits;
+  }
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
+    S.sp.b[0][c] = 0.0f;
+    S.sp.b[1][c] = P[oB2 + c];
+    S.sp.b[2][c] = P[oB3 + c];
+    S.sp.b[3][c] = P[oB4 + c];
+    S.sp.w5[c] = P[oW5 + c];
+  }
+  if (threadIdx.x == 0) S.sp.b5 = P[oB5];
+}
 
 // The 128 threads of one tile (4 warps, named barrier 1 + tile) synchronise
 // among themselves only, so the tiles of a block drift apart and one tile's
@@ -479,28 +527,39 @@ __device__ __forceinline__ bool tile_or(int tile, bool v) {
 __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, const Norm &N,
                                               const float (&raw)[4], uint32_t &phase, float &logk) {
   const int tid = threadIdx.x, tile = tid >> 7, r = tid & 127, warp = tid >> 5;
-  float u[4];
+  {  // this row of the layer-1 operand A: {u_hi, u_hi, u_lo} per input, then 1, 1, 0, 0
+    uint16_t e[kL1K];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) u[i] = 2.0f * (raw[i] - N.lo[i]) / (N.hi[i] - N.lo[i]) - 1.0f;
-#pragma unroll 1
-  for (int c0 = 0; c0 < kH; c0 += 8) {
-    float z[8];
+    for (int i = 0; i < 4; ++i) {
+      const float u = 2.0f * (raw[i] - N.lo[i]) / (N.hi[i] - N.lo[i]) - 1.0f;
+      const uint16_t hi = bf16_bits(u);
+      e[3 * i] = hi;
+      e[3 * i + 1] = hi;
+      e[3 * i + 2] = bf16_bits(u - bf16_value(hi));
+    }
+    e[12] = e[13] = 0x3F80u;  // 1.0
+    e[14] = e[15] = 0u;
+    uint32_t w[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) z[i] = layer1(S.sp, c0 + i, u);
-    *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0)]) =
-        make_uint4(silu_bf16x2(z[0], z[1]), silu_bf16x2(z[2], z[3]), silu_bf16x2(z[4], z[5]),
-                   silu_bf16x2(z[6], z[7]));
+    for (int i = 0; i < 8; ++i) w[i] = (uint32_t)e[2 * i] | ((uint32_t)e[2 * i + 1] << 16);
+    *reinterpret_cast<uint4 *>(&S.A1[tile][l1_index(r, 0)]) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(&S.A1[tile][l1_index(r, 8)]) = make_uint4(w[4], w[5], w[6], w[7]);
   }
   float y = 0.0f;
   const uint32_t tcol = tmem + (uint32_t)(tile * kH);
+  // l = 0: layer 1 (K = 16); l = 1..3: W2..W4 (K = 128)
 #pragma unroll 1
-  for (int l = 0; l < 3; ++l) {
+  for (int l = 0; l < 4; ++l) {
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     tile_sync(tile);
     if (r == 0) {
       tc::fence_after_sync();
-      tc::mma_128x128x128(tcol, S.A[tile], S.W[l]);
+      if (l == 0)
+        tc::mma_bf16(tcol, tc::smem_desc(tc::smem_addr(S.A1[tile]), 128u, 256u),
+                     tc::smem_desc(tc::smem_addr(S.B1), 128u, 256u), tc::idesc_bf16_f32(128, 128), 0u);
+      else
+        tc::mma_128x128x128(tcol, S.A[tile], S.W[l - 1]);
       tc::mma_commit(&S.bar_mma[tile]);
     }
     const int timeout = tc::mbar_wait(&S.bar_mma[tile], phase, kWaitLimit) ? 0 : 1;
@@ -512,7 +571,7 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float acc[32];
       tc::tmem_ld32(tcol + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, acc);
-      if (l < 2) {  // next layer's BF16 input
+      if (l < 3) {  // next layer's BF16 input
 #pragma unroll
         for (int i = 0; i < 32; i += 8) {
           float z[8];
@@ -556,7 +615,8 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
     S.next = begin;
   }
   if (warp == 0) tc::tmem_alloc(&S.tmem, kWalkTmemCols);
-  stage_small(S.sp, P);
+  stage_walk(S, P);
+  tc::fence_smem_to_async();  // B1 is read by the tensor cores of every tile
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();

@@ -91,3 +91,38 @@ def test_mlp_walk_with_constant_network_matches_table_walk(rt):
     _close(ab_m, ab_t, sc_t[0], 1e-5)
     assert sc_m[0] == pytest.approx(sc_t[0], rel=1e-5)
     assert sc_m[3] < 1e-5
+
+
+def test_mlp_walk_matches_table_of_the_same_network(rt):
+    # A random network tabulated with rt_mlp_forward (binary32 first layer and SiLU) at
+    # the T nodes: on cells whose temperatures are nodes (p, x at the reference), the
+    # surrogate walk (first layer as a split-BF16 tensor-core product, packed-BF16 SiLU)
+    # must reproduce the table walk's tallies to within the BF16 activation rounding.
+    import torch
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.02, n_nu=2000, cutoff=25.0, profile="voigt", nT=13,
+                          T_min=800.0, T_max=2000.0, p_ref_atm=1.0, x_ref=0.1)
+    g = _node_grid(4)
+    params = synth.mlp_init(3)
+    lo = [math.log(2000.0), 600.0, 0.5, 0.01]
+    hi = [math.log(3000.0), 2200.0, 5.0, 0.3]
+    norm = rt.make_norm(lo, hi, -3.0, 1.0)
+    P = torch.from_numpy(params).cuda()
+    j = np.arange(spec.n_nu, dtype=np.float32)
+    nu = (j * np.float32(spec.dnu) + np.float32(spec.nu_min)).astype(np.float32)
+    T_nodes = np.asarray(spec.T_nodes(), dtype=np.float32)
+    raw = np.zeros((spec.nT, spec.n_nu, 4), np.float32)
+    raw[..., 0] = np.log(nu)[None, :]
+    raw[..., 1] = T_nodes[:, None]
+    raw[..., 2] = 1.0
+    raw[..., 3] = 0.1
+    logk = rt.mlp_forward(P, norm, torch.from_numpy(raw.reshape(-1, 4)).cuda())
+    tab = torch.exp(logk).reshape(spec.nT, spec.n_nu).contiguous()
+    gs, keep = rt.make_grid(g)
+    n = 40000
+    ab_m, sc_m, st_m = _tally(rt, lambda t: rt.trace_mlp(gs, P, norm, spec, t, n_rays=n, seed=5), g.ncells)
+    ab_t, sc_t, st_t = _tally(rt, lambda t: rt.trace(gs, tab, spec, t, n_rays=n, seed=5), g.ncells)
+    assert st_m == st_t  # the same rays and visits
+    big = ab_t >= 1e-3 * ab_t.max()
+    rel = np.abs(ab_m[big] - ab_t[big]) / ab_t[big]
+    assert np.median(rel) < 1e-2 and rel.max() < 5e-2, (np.median(rel), rel.max())
+    assert sc_m[0] == pytest.approx(sc_t[0], rel=1e-2)
