@@ -338,10 +338,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v) {
-  const float y = __fsub_rn(v, c);
-  const float t = __fadd_rn(s, y);
-  c = __fsub_rn(__fsub_rn(t, s), y);
+// Paired binary32 arithmetic (one f32x2 instruction for two lanes' worth of
+// work): each component is rounded exactly as the scalar __fmaf_rn /
+// __fadd_rn, so the paired forms give the same bits as the scalar ones.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 rcp2(float2 d) { return make_float2(rcp_approx(d.x), rcp_approx(d.y)); }
+
+// compensated (Kahan) add of v into s with running compensation c, per component
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 v) {
+  const float2 y = __fadd2_rn(v, neg2(c));
+  const float2 t = __fadd2_rn(s, y);
+  c = __fadd2_rn(__fadd2_rn(t, neg2(s)), neg2(y));
   s = t;
 }
 
@@ -369,9 +377,7 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
   __shared__ __align__(16) int4 sR[2][kChunk];
   __shared__ __align__(16) float4 sP[2][kPSets][kMaxTPerBlock][kChunk];
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ float s_qx[kMaxTPerBlock][kTilePts];           // near-centre queue: x
-  __shared__ unsigned char s_qs[kMaxTPerBlock][kTilePts];   // near-centre queue: owner slot
-  __shared__ float s_res[kMaxTPerBlock][kTilePts];          // near-centre values by slot
+  __shared__ float s_res[kMaxTPerBlock][kTilePts];          // near-centre values by tile point
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tpb = blockDim.x >> 5;
@@ -382,6 +388,11 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
   const long long jend = min(j0 + (long long)kTilePts, n_nu);
   const int jw0 = (int)j0, jw1 = jw0 + kTilePts - 1;
   const int jt = jw0 + lane * kPtsPerThread;
+  // offset of point j from a line centre j_c with sub-grid offset dg: the exact
+  // integer difference, then one rounding
+  auto point_offset = [&](int j, int jc, int dg_bits) -> float {
+    return __fadd_rn((float)(j - jc), __int_as_float(dg_bits));
+  };
 
   __shared__ int s_end[kMaxSegs];
   __shared__ unsigned char s_kind[kMaxSegs];
@@ -417,9 +428,11 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
     }
   };
 
-  float acc[kPtsPerThread], cmp[kPtsPerThread];
+  // compensated sums for the lane's points, as pairs (2h, 2h + 1)
+  constexpr int kPairs = kPtsPerThread / 2;
+  float2 acc[kPairs], cmp[kPairs];
 #pragma unroll
-  for (int q = 0; q < kPtsPerThread; ++q) acc[q] = cmp[q] = 0.0f;
+  for (int h = 0; h < kPairs; ++h) acc[h] = cmp[h] = make_float2(0.0f, 0.0f);
   if (threadIdx.x == 0) {
     if (nchunks > 0) issue(0);
     if (nchunks > 1) issue(1);
@@ -449,140 +462,133 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
     // fast paths: g[q] += value of line i at the lane's points (or = when first).
     // DEG 4: full far-wing series; DEG 2: far lines (t^3 and t^4 terms negligible);
     // MASK: zero outside the line's window.
-    auto fast_line = [&](auto deg, auto mask, int i, float (&g)[kPtsPerThread], bool first) {
+    auto fast_line = [&](auto deg, auto mask, int i, float2 (&g)[kPairs], bool first) {
       constexpr int DEG = decltype(deg)::value;
       constexpr bool MASK = decltype(mask)::value;
       const int4 r = sR[b][i];
       const float4 p = sP[b][0][wsel][i];
-      const float ul = (float)(jt - r.z) + __int_as_float(r.w);
+      const float ul = point_offset(jt, r.z, r.w);
       if (!kVoigt) {
+        const float2 u0 = dup2(ul), g2 = dup2(p.y), a2 = dup2(p.x);
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) {
-          const float u = __fadd_rn(ul, (float)q);
-          float rr = rcp_approx(__fmaf_rn(u, u, p.y));
-          if (MASK && (jt + q < r.x || jt + q > r.y)) rr = 0.0f;
-          g[q] = first ? p.x * rr : __fmaf_rn(p.x, rr, g[q]);
+        for (int h = 0; h < kPairs; ++h) {
+          const float2 u = __fadd2_rn(u0, make_float2((float)(2 * h), (float)(2 * h + 1)));
+          float2 rr = rcp2(__ffma2_rn(u, u, g2));
+          if (MASK) {
+            if (jt + 2 * h < r.x || jt + 2 * h > r.y) rr.x = 0.0f;
+            if (jt + 2 * h + 1 < r.x || jt + 2 * h + 1 > r.y) rr.y = 0.0f;
+          }
+          g[h] = first ? __fmul2_rn(a2, rr) : __ffma2_rn(a2, rr, g[h]);
         }
       } else {
-        const float c1 = 1.5f * p.x;
-        const float xt = p.y * ul;
+        const float2 c0 = dup2(p.x), c1 = dup2(1.5f * p.x), sd = dup2(p.y), y2 = dup2(p.z);
+        const float2 xt = dup2(p.y * ul);
         float4 p2 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (DEG == 4) p2 = sP[b][kPSets - 1][wsel][i];
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) {
-          const float x = __fmaf_rn(p.y, (float)q, xt);
-          const float t = rcp_approx(__fmaf_rn(x, x, p.z));
-          float h;
+        for (int h = 0; h < kPairs; ++h) {
+          const float2 x = __ffma2_rn(sd, make_float2((float)(2 * h), (float)(2 * h + 1)), xt);
+          const float2 t = rcp2(__ffma2_rn(x, x, y2));
+          float2 v;
           if (DEG == 4)
-            h = __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, p2.y, p2.x), p.w), c1), p.x);
+            v = __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, dup2(p2.y), dup2(p2.x)), dup2(p.w)), c1), c0);
           else if (DEG == 2)
-            h = __fmaf_rn(t, __fmaf_rn(t, p.w, c1), p.x);
+            v = __ffma2_rn(t, __ffma2_rn(t, dup2(p.w), c1), c0);
           else
-            h = __fmaf_rn(t, c1, p.x);
-          if (MASK && (jt + q < r.x || jt + q > r.y)) h = 0.0f;
-          g[q] = first ? t * h : __fmaf_rn(t, h, g[q]);
+            v = __ffma2_rn(t, c1, c0);
+          if (MASK) {
+            if (jt + 2 * h < r.x || jt + 2 * h > r.y) v.x = 0.0f;
+            if (jt + 2 * h + 1 < r.x || jt + 2 * h + 1 > r.y) v.y = 0.0f;
+          }
+          g[h] = first ? __fmul2_rn(t, v) : __ffma2_rn(t, v, g[h]);
         }
       }
     };
     auto run_fast = [&](auto deg, auto mask, int i, int i1) {
 #pragma unroll 1
       for (; i + kGroup <= i1; i += kGroup) {
-        float g[kPtsPerThread];
+        float2 g[kPairs];
         fast_line(deg, mask, i, g, true);
 #pragma unroll
         for (int e = 1; e < kGroup; ++e) fast_line(deg, mask, i + e, g, false);
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], g[q]);
+        for (int h = 0; h < kPairs; ++h) kahan_add2(acc[h], cmp[h], g[h]);
       }
       if (i < i1) {
-        float g[kPtsPerThread];
+        float2 g[kPairs];
         fast_line(deg, mask, i, g, true);
 #pragma unroll 1
         for (int e = i + 1; e < i1; ++e) fast_line(deg, mask, e, g, false);
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], g[q]);
+        for (int h = 0; h < kPairs; ++h) kahan_add2(acc[h], cmp[h], g[h]);
       }
     };
 
     // general path: the value of line i at the lane's points, with masking
     // outside the window and near-centre points
-    auto line_vals = [&](int i, float (&v)[kPtsPerThread]) {
+    auto line_vals = [&](int i, float2 (&v)[kPairs]) {
         const int4 r = sR[b][i];
         const float4 p = sP[b][0][wsel][i];
-        const float ul = (float)(jt - r.z) + __int_as_float(r.w);
+        const float ul = point_offset(jt, r.z, r.w);
         if (!kVoigt) {
+          const float2 u0 = dup2(ul), g2 = dup2(p.y), a2 = dup2(p.x);
 #pragma unroll
-          for (int q = 0; q < kPtsPerThread; ++q) {
-            const float u = __fadd_rn(ul, (float)q);
-            v[q] = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
+          for (int h = 0; h < kPairs; ++h) {
+            const float2 u = __fadd2_rn(u0, make_float2((float)(2 * h), (float)(2 * h + 1)));
+            v[h] = __fmul2_rn(a2, rcp2(__ffma2_rn(u, u, g2)));
           }
         } else {
           const float4 p2 = sP[b][kPSets - 1][wsel][i];
           const float y2 = p.z;
-          const float xt = p.y * ul;
+          const float2 y22 = dup2(y2), sd = dup2(p.y), xt = dup2(p.y * ul);
           // four-term series, valid for |z| >= 10: the degree-4 polynomial plus the
           // fourth term 15 t^3 (7 - 56 s + 112 s^2 - 64 s^3) / 8, s = y^2 t, in t
           const float q1 = y2 * p.x, q2 = q1 * y2;
-          const float c3 = __fmaf_rn(13.125f, p.x, p2.x), c4 = __fmaf_rn(-105.0f, q1, p2.y);
-          const float c5 = 210.0f * q2, c6 = -120.0f * q2 * y2;
-          float xs[kPtsPerThread];
+          const float2 c3 = dup2(__fmaf_rn(13.125f, p.x, p2.x)), c4 = dup2(__fmaf_rn(-105.0f, q1, p2.y));
+          const float2 c5 = dup2(210.0f * q2), c6 = dup2(-120.0f * q2 * y2);
+          const float2 c0 = dup2(p.x), c1 = dup2(1.5f * p.x), c2 = dup2(p.w);
 #pragma unroll
-          for (int q = 0; q < kPtsPerThread; ++q) {
-            xs[q] = __fmaf_rn(p.y, (float)q, xt);
-            const float t = rcp_approx(__fmaf_rn(xs[q], xs[q], y2));
-            const float h = __fmaf_rn(
-                t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, __fmaf_rn(t, c6, c5), c4), c3), p.w),
-                             1.5f * p.x),
-                p.x);
-            v[q] = t * h;
+          for (int h = 0; h < kPairs; ++h) {
+            const float2 x = __ffma2_rn(sd, make_float2((float)(2 * h), (float)(2 * h + 1)), xt);
+            const float2 t = rcp2(__ffma2_rn(x, x, y22));
+            const float2 w = __ffma2_rn(
+                t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, c6, c5), c4), c3), c2), c1),
+                c0);
+            v[h] = __fmul2_rn(t, w);
           }
-          // warp-uniform: the tile's offsets [fu, fu + kTilePts) meet the region |z| < 10
+          // warp-uniform: the tile's offsets [fu, fu + kTilePts) meet the region |z| < 10,
+          // |u| < u_core in grid units; its points are the contiguous tile indices [ea, eb]
+          // (one point of margin each side: the near form holds at any |z|), evaluated
+          // one per lane and handed to their owners through shared memory
           const float fu = (float)(jw0 - r.z) + __int_as_float(r.w);
           if (fu < p2.w + 1.0f && fu + (float)kTilePts > -p2.w - 1.0f) {
-            // compact this warp's points with |z| < 10 so one pass of the lanes evaluates them
-            unsigned nearbits = 0;
-#pragma unroll
-            for (int q = 0; q < kPtsPerThread; ++q)
-              nearbits |= (__fmaf_rn(xs[q], xs[q], y2) < 100.0f ? 1u : 0u) << q;
-            const int cnt_n = __popc(nearbits);
-            int pre = cnt_n;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-              const int t = __shfl_up_sync(0xffffffffu, pre, o);
-              if (lane >= o) pre += t;
+            const int ea = (int)fmaxf(floorf(-p2.w - 1.0f - fu), 0.0f);
+            const int eb = (int)fminf(ceilf(p2.w + 1.0f - fu), (float)(kTilePts - 1));
+            float *res = s_res[warp];
+            const float y = sqrtf(y2);
+            const float coef = __fdividef(p.x, y);
+            for (int e = ea + lane; e <= eb; e += 32) {
+              const float xe = p.y * point_offset(jw0 + e, r.z, r.w);
+              res[e] = coef * faddeeva_re_near(xe, y, __fmaf_rn(xe, xe, y2), wc);
             }
-            const int total = __shfl_sync(0xffffffffu, pre, 31);
-            if (total > 0) {
-              float *qx = s_qx[warp];
-              unsigned char *qs = s_qs[warp];
-              float *res = s_res[warp];
-              int pos = pre - cnt_n;
+            __syncwarp();
+            const int p0 = lane * kPtsPerThread;
+            if (p0 + kPtsPerThread > ea && p0 <= eb) {
 #pragma unroll
-              for (int q = 0; q < kPtsPerThread; ++q)
-                if ((nearbits >> q) & 1u) {
-                  qx[pos] = xs[q];
-                  qs[pos] = (unsigned char)(lane * kPtsPerThread + q);
-                  ++pos;
-                }
-              __syncwarp();
-              const float y = sqrtf(y2);
-              const float coef = __fdividef(p.x, y);
-              for (int e = lane; e < total; e += 32) {
-                const float xe = qx[e];
-                res[qs[e]] = coef * faddeeva_re_near(xe, y, __fmaf_rn(xe, xe, y2), wc);
+              for (int h = 0; h < kPairs; ++h) {
+                if (p0 + 2 * h >= ea && p0 + 2 * h <= eb) v[h].x = res[p0 + 2 * h];
+                if (p0 + 2 * h + 1 >= ea && p0 + 2 * h + 1 <= eb) v[h].y = res[p0 + 2 * h + 1];
               }
-              __syncwarp();
-#pragma unroll
-              for (int q = 0; q < kPtsPerThread; ++q)
-                if ((nearbits >> q) & 1u) v[q] = res[lane * kPtsPerThread + q];
-              __syncwarp();
             }
+            __syncwarp();
           }
         }
         if (r.x > jw0 || r.y < jw1) {  // warp-uniform: the window ends inside this block's points
 #pragma unroll
-          for (int q = 0; q < kPtsPerThread; ++q)
-            if (jt + q < r.x || jt + q > r.y) v[q] = 0.0f;
+          for (int h = 0; h < kPairs; ++h) {
+            if (jt + 2 * h < r.x || jt + 2 * h > r.y) v[h].x = 0.0f;
+            if (jt + 2 * h + 1 < r.x || jt + 2 * h + 1 > r.y) v[h].y = 0.0f;
+          }
         }
     };
     // lines enter the compensated sum in pairs: the sum of two positive line
@@ -590,17 +596,17 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
     auto run_general = [&](int i, int i1) {
 #pragma unroll 1
       for (; i + 1 < i1; i += 2) {
-        float va[kPtsPerThread], vb[kPtsPerThread];
+        float2 va[kPairs], vb[kPairs];
         line_vals(i, va);
         line_vals(i + 1, vb);
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], __fadd_rn(va[q], vb[q]));
+        for (int h = 0; h < kPairs; ++h) kahan_add2(acc[h], cmp[h], __fadd2_rn(va[h], vb[h]));
       }
       if (i < i1) {
-        float va[kPtsPerThread];
+        float2 va[kPairs];
         line_vals(i, va);
 #pragma unroll
-        for (int q = 0; q < kPtsPerThread; ++q) kahan_add(acc[q], cmp[q], va[q]);
+        for (int h = 0; h < kPairs; ++h) kahan_add2(acc[h], cmp[h], va[h]);
       }
     };
 
@@ -634,7 +640,10 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
   float *row = kappa + (long long)k * n_nu;
   float out[kPtsPerThread];
 #pragma unroll
-  for (int q = 0; q < kPtsPerThread; ++q) out[q] = __fsub_rn(acc[q], cmp[q]);
+  for (int h = 0; h < kPairs; ++h) {
+    out[2 * h] = __fsub_rn(acc[h].x, cmp[h].x);
+    out[2 * h + 1] = __fsub_rn(acc[h].y, cmp[h].y);
+  }
   if ((long long)jt + kPtsPerThread <= jend && vec_ok) {
 #pragma unroll
     for (int q4 = 0; q4 < kPtsPerThread; q4 += 4) {
@@ -679,12 +688,9 @@ rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *t
   if (want < 1 || want > kMaxTPerBlock) want = kMaxTPerBlock;
   const int tpb = spec->nT < want ? spec->nT : want;
   dim3 gk((unsigned)n_tiles, (unsigned)((spec->nT + tpb - 1) / tpb));
-  if (spec->profile == RT_PROFILE_LORENTZ)
-    k_kappa<RT_PROFILE_LORENTZ><<<gk, 32 * tpb, 0, st>>>(P, P2, R, tiles, n, spec->n_nu, spec->nT, wc,
-                                                         vec_ok, spec->accumulate ? 1 : 0, kappa, status);
-  else
-    k_kappa<RT_PROFILE_VOIGT><<<gk, 32 * tpb, 0, st>>>(P, P2, R, tiles, n, spec->n_nu, spec->nT, wc,
-                                                       vec_ok, spec->accumulate ? 1 : 0, kappa, status);
+  auto kernel = spec->profile == RT_PROFILE_LORENTZ ? k_kappa<RT_PROFILE_LORENTZ> : k_kappa<RT_PROFILE_VOIGT>;
+  kernel<<<gk, 32 * tpb, 0, st>>>(P, P2, R, tiles, n, spec->n_nu, spec->nT, wc, vec_ok,
+                                  spec->accumulate ? 1 : 0, kappa, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }

@@ -165,3 +165,18 @@ def test_two_gas_mixture_accumulates(rt):
     ref = okappa.kappa_table(co2, s1) + okappa.kappa_table(h2o, replace(s2, accumulate=0))
     got = out.cpu().numpy().astype(np.float64)
     assert _rel(got, ref).max() <= TOL
+
+
+def test_offsets_of_millions_of_grid_points(rt):
+    # A 50 cm^-1 cutoff on a 1e-5 cm^-1 grid: offsets of a point from a line centre
+    # reach 4.5e6 grid points (binary32 offsets with an ulp of 0.5 grid point).
+    rng = synth.rng_for(9, 82)
+    lines = synth.make_lines(60, 1955.0, 2045.0, rng)
+    spec = synth.Spectral(nu_min=2000.0, dnu=1e-5, n_nu=3000, cutoff=50.0, profile="voigt", nT=2,
+                          T_min=800.0, T_max=1600.0)
+    got, ev, st = _gpu_table(rt, lines, spec)
+    ref = okappa.kappa_table(lines, spec)
+    assert st == 0
+    assert ev == okappa.profile_evals(lines, spec)
+    assert np.all(ref > 0)
+    assert _rel(got, ref).max() <= TOL
