@@ -180,3 +180,19 @@ def test_offsets_of_millions_of_grid_points(rt):
     assert ev == okappa.profile_evals(lines, spec)
     assert np.all(ref > 0)
     assert _rel(got, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("profile,memory", [("voigt", "host"), ("voigt", "device"), ("lorentz", "host")])
+def test_odd_line_count(rt, profile, memory):
+    # the line sum takes lines in pairs; an odd count adds a padding line that must add nothing
+    rng = synth.rng_for(9, 83)
+    lines = synth.make_lines(401, 1985.0, 2075.0, rng)
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.01, n_nu=5000, cutoff=25.0, profile=profile, nT=3,
+                          T_min=700.0, T_max=1900.0)
+    got, ev, st = _gpu_table(rt, lines, spec, memory=memory)
+    ref = okappa.kappa_table(lines, spec)
+    assert st == 0
+    assert ev == okappa.profile_evals(lines, spec)
+    nz = ref > 0
+    assert np.array_equal(got > 0, nz)
+    assert _rel(got[nz], ref[nz]).max() <= TOL
