@@ -564,6 +564,38 @@ def run_batched(args):
     print(json.dumps(res), flush=True)
 
 
+def pressure_reading_error(rt, case, kap, n_rays=1_000_000):
+    """Per-cell tally error of the table walk (T-node table at p_ref, kappa scaled by the
+    cell's density p x / (p_ref x_ref); the widths' pressure dependence is not tabulated)
+    against the on-the-fly line-by-line walk at each cell's own (T, p, x), same rays, on the
+    16^3 version of the 128^3 fields; and with p = p_ref everywhere, which leaves only the
+    linear-in-T interpolation, so that the pressure reading's share shows."""
+    import torch
+    from dataclasses import replace
+    g16 = synth.multi_gaussian_grid(16, 1.0, synth.rng_for(4, 1))
+    out = {"grid": "16^3, same recipe and seed as the 128^3 fields", "rays": n_rays}
+    for name, grid in (("p_field_1_3_atm", g16),
+                       ("p_ref_everywhere", replace(g16, p_atm=np.full_like(g16.p_atm, case.spec.p_ref_atm)))):
+        gs, keep = rt.make_grid(grid)
+        tallies = {}
+        for walk in ("table", "lbl"):
+            t = rt.Tally(grid.ncells)
+            t.zero()
+            if walk == "table":
+                rt.trace(gs, kap, case.spec, t, n_rays=n_rays, n_rays_total=n_rays)
+            else:
+                rt.trace_lbl(gs, case.lines, case.spec, t, n_rays=n_rays, n_rays_total=n_rays)
+            tallies[walk] = t.read()[0]
+        ref, got = tallies["lbl"], tallies["table"]
+        big = ref >= 1e-3 * ref.max()
+        err = np.abs(got[big] - ref[big]) / ref[big]
+        out[name] = {"median": float(np.median(err)), "p90": float(np.percentile(err, 90)),
+                     "max": float(err.max()), "cells": int(big.sum()),
+                     "total": float(got.sum() / ref.sum() - 1.0)}
+    torch.cuda.synchronize()
+    return out
+
+
 def run_box128(args):
     """The 128^3 workload: 100k lines, 64 T x 400k nu table, and the walk."""
     import torch
@@ -599,7 +631,8 @@ def run_box128(args):
                                           torch.cuda.get_device_properties(0).multi_processor_count,
                                           _peaks().get("sm_max_mhz", 2070.0)),
            "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
-                      "walk_candidates_ms_1e7_rays": walk_ms}}
+                      "walk_candidates_ms_1e7_rays": walk_ms},
+           "pressure_reading_error_vs_lbl": pressure_reading_error(rt, case, kap)}
     print(json.dumps(res), flush=True)
 
 

@@ -110,6 +110,12 @@ __device__ __forceinline__ float cell_kappa_p(const float4 cd, const float *__re
   return cd.y * fmaf(cd.x, v.y, (1.0f - cd.x) * v.x);
 }
 
+// The same from the ray's row of node pairs, row = tabp + j (nT - 1).
+__device__ __forceinline__ float cell_kappa_row(const float4 cd, const float2 *__restrict__ row) {
+  const float2 v = __ldg(row + __float_as_int(cd.w));
+  return cd.y * fmaf(cd.x, v.y, (1.0f - cd.x) * v.x);
+}
+
 // kappa of a cell from the walk table in layout L (0 T-major, 1 wavenumber-major, 2 pairs).
 template <int L>
 __device__ __forceinline__ float cell_kappa_l(const float4 cd, const float *__restrict__ tab, int nT,
