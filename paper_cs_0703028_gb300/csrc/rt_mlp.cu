@@ -27,6 +27,7 @@ constexpr int kH = 128;
 constexpr int kNParam = 50305;
 constexpr int oW1 = 0, oB1 = 512, oW2 = 640, oB2 = 17024, oW3 = 17152, oB3 = 33536, oW4 = 33664,
               oB4 = 50048, oW5 = 50176, oB5 = 50304;
+constexpr int kGradStride = (kNParam + 15) & ~15;  // per-tile gradient partials, 64-byte rows
 constexpr int kTileElems = kH * kH;           // 16384 bf16 = 32 KB
 constexpr uint32_t kTileBytes = kTileElems * 2;
 constexpr uint32_t kWaitLimit = 1u << 24;
@@ -41,6 +42,12 @@ __device__ __forceinline__ float tanh_approx(float x) {
   return y;
 }
 __device__ __forceinline__ float sigmoid_fast(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
+
+// Training pre-activations Z[layer][unit][sample] (n samples): the 32 lanes of a
+// warp hold consecutive samples, so their accesses to one unit are coalesced.
+__device__ __forceinline__ long long zidx(long long layer, int c, long long n, long long row) {
+  return (layer * kH + c) * n + row;
+}
 
 // SiLU of two pre-activations, packed as the BF16 pair the next layer reads:
 // z rounded to BF16, then z (1/2 + tanh(z/2)/2) in packed BF16 arithmetic (the
@@ -156,7 +163,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     for (int i = 0; i < 8; ++i) {
       const int c = c0 + i;
       const float z = layer1(S.sp, c, u);
-      if (TRAIN && valid) Z[(0 * n + row) * kH + c] = z;
+      if (TRAIN && valid) Z[zidx(0, c, n, row)] = z;
       h[i] = z * sigmoid_fast(z);
     }
     uint4 pk = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
@@ -191,7 +198,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
         for (int q = 0; q < 8; ++q) {
           const int c = c0 + i + q;
           const float z = acc[i + q] + bias[c];
-          if (TRAIN && valid) Z[((long long)(l + 1) * n + row) * kH + c] = z;
+          if (TRAIN && valid) Z[zidx(l + 1, c, n, row)] = z;
           h[q] = z * sigmoid_fast(z);
           if (l == 2) y = fmaf(S.sp.w5[c], h[q], y);
         }
@@ -254,9 +261,12 @@ __device__ __forceinline__ float column_sum(const BwdSmem &S, int c) {
 __global__ void __launch_bounds__(128)
 k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
           const float *__restrict__ inputs, long long n, const float *__restrict__ Z,
-          const float *__restrict__ dy, float *__restrict__ G, uint32_t *status) {
+          const float *__restrict__ dy, float *__restrict__ Gpart, uint32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
+  // this tile's gradient partial (every parameter written exactly once; summed over
+  // the tiles in a fixed order by k_grad_reduce)
+  float *G = Gpart + (long long)blockIdx.x * kGradStride;
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long row = (long long)blockIdx.x * kH + tid;
   const bool valid = row < n;
@@ -282,36 +292,48 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
   const float dyv = valid ? dy[row] : 0.0f;
   S.dyv[tid] = dyv;
 
-  // head: dw5 = sum_s dy h4, db5 = sum_s dy
-#pragma unroll 4
-  for (int c = 0; c < kH; ++c) {
-    const float z4 = valid ? Z[(3 * n + row) * kH + c] : 0.0f;
-    S.buf[tid][c] = dyv * z4 * sigmoid_fast(z4);
+  // head: dw5 = sum_s dy h4, db5 = sum_s dy (loads issued 32 at a time)
+#pragma unroll 1
+  for (int c0 = 0; c0 < kH; c0 += 32) {
+    float z4[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z4[i] = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) S.buf[tid][c0 + i] = dyv * z4[i] * sigmoid_fast(z4[i]);
   }
   __syncthreads();
-  atomicAdd(G + oW5 + tid, column_sum(S, tid));
+  G[oW5 + tid] = column_sum(S, tid);
   if (tid == 0) {
     float d5 = 0.0f;
     for (int r = 0; r < kH; ++r) d5 += S.dyv[r];
-    atomicAdd(G + oB5, d5);
+    G[oB5] = d5;
   }
   __syncthreads();
   // dz4 = dy w5 silu'(z4) -> dZ, dZ^T, buf (for db4); h3 -> H^T (for dW4)
-#pragma unroll 4
-  for (int c = 0; c < kH; ++c) {
-    const float z4 = valid ? Z[(3 * n + row) * kH + c] : 0.0f;
-    const float s4 = sigmoid_fast(z4);
-    const float dz = dyv * __ldg(P + oW5 + c) * (s4 * (1.0f + z4 * (1.0f - s4)));
-    S.buf[tid][c] = dz;
-    put_bf16(S.dZ, tid, c, dz);
-    put_bf16(S.dZt, c, tid, dz);
-    const float z3 = valid ? Z[(2 * n + row) * kH + c] : 0.0f;
-    put_bf16(S.Ht, c, tid, z3 * sigmoid_fast(z3));
+#pragma unroll 1
+  for (int c0 = 0; c0 < kH; c0 += 16) {
+    float z4[16], z3[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      z4[i] = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
+      z3[i] = valid ? Z[zidx(2, c0 + i, n, row)] : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int c = c0 + i;
+      const float s4 = sigmoid_fast(z4[i]);
+      const float dz = dyv * __ldg(P + oW5 + c) * (s4 * (1.0f + z4[i] * (1.0f - s4)));
+      S.buf[tid][c] = dz;
+      put_bf16(S.dZ, tid, c, dz);
+      put_bf16(S.dZt, c, tid, dz);
+      put_bf16(S.Ht, c, tid, z3[i] * sigmoid_fast(z3[i]));
+    }
   }
   __syncthreads();
-  atomicAdd(G + oB4 + tid, column_sum(S, tid));
+  G[oB4 + tid] = column_sum(S, tid);
 
   int timeout = 0;
+  bool aborted = false;
   uint32_t wphase = 0;
 #pragma unroll 1
   for (int l = 4; l >= 2; --l) {
@@ -320,7 +342,10 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     wphase ^= 1u;
     tc::fence_smem_to_async();
     tc::fence_before_sync();
-    if (__syncthreads_or(timeout)) break;
+    if (__syncthreads_or(timeout)) {
+      aborted = true;
+      break;
+    }
     if (tid == 0) {
       tc::fence_after_sync();
       tc::mma_128x128x128(tmem, S.dZt, S.Ht);        // dW_l[out][in]
@@ -328,7 +353,10 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
       tc::mma_commit(&S.bar_mma);
     }
     timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)((4 - l) & 1), kWaitLimit) ? 0 : 1;
-    if (__syncthreads_or(timeout)) break;
+    if (__syncthreads_or(timeout)) {
+      aborted = true;
+      break;
+    }
     tc::fence_after_sync();
     if (tid == 0 && l > 2) {  // next transposed weights into the now free buffer
       tc::mbar_arrive_expect_tx(&S.bar_w, kTileBytes);
@@ -338,30 +366,37 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     const long long zl = (long long)(l - 2);  // block of z_{l-1}
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
+      // this chunk's pre-activations first, so that their loads overlap the
+      // tensor-memory reads below
+      float z[32], zp[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        z[i] = valid ? Z[zidx(zl, c0 + i, n, row)] : 0.0f;
+        zp[i] = (valid && l > 2) ? Z[zidx(zl - 1, c0 + i, n, row)] : 0.0f;
+      }
       float acc[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) atomicAdd(gW + tid * kH + c0 + i, acc[i]);
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4 *>(gW + tid * kH + c0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kH + c0), acc);
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int c = c0 + i;
-        const float z = valid ? Z[(zl * n + row) * kH + c] : 0.0f;
-        const float s = sigmoid_fast(z);
-        const float dz = acc[i] * (s * (1.0f + z * (1.0f - s)));
+        const float s = sigmoid_fast(z[i]);
+        const float dz = acc[i] * (s * (1.0f + z[i] * (1.0f - s)));
         S.buf[tid][c] = dz;
         if (l > 2) {
           put_bf16(S.dZ, tid, c, dz);
           put_bf16(S.dZt, c, tid, dz);
-          const float zp = valid ? Z[((zl - 1) * n + row) * kH + c] : 0.0f;
-          put_bf16(S.Ht, c, tid, zp * sigmoid_fast(zp));
+          put_bf16(S.Ht, c, tid, zp[i] * sigmoid_fast(zp[i]));
         }
       }
     }
     tc::fence_before_sync();
     __syncthreads();
     const int ob = (l == 4 ? oB3 : (l == 3 ? oB2 : oB1));
-    atomicAdd(G + ob + tid, column_sum(S, tid));
+    G[ob + tid] = column_sum(S, tid);
     if (l == 2) {  // first layer: dW1[c][k] = sum_s dz1[s][c] u[s][k]
       float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
@@ -370,18 +405,28 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
 #pragma unroll
         for (int k = 0; k < 4; ++k) g[k] = fmaf(d, S.u[r][k], g[k]);
       }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) atomicAdd(G + oW1 + tid * 4 + k, g[k]);
+      *reinterpret_cast<float4 *>(G + oW1 + tid * 4) = make_float4(g[0], g[1], g[2], g[3]);
     }
     __syncthreads();  // buf is rewritten by the next layer
   }
   if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
+  if (aborted)  // block-uniform: the partial holds no gradient of this tile
+    for (int i = tid; i < kNParam; i += kH) G[i] = 0.0f;
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, 2 * kH);
   }
+}
+
+// gradient = sum of the tiles' partials, in tile order (deterministic)
+__global__ void k_grad_reduce(const float *__restrict__ part, int nparts, float *__restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNParam) return;
+  float s = 0.0f;
+  for (int t = 0; t < nparts; ++t) s += part[(long long)t * kGradStride + i];
+  grad[i] = s;
 }
 
 __global__ void k_mlp_adam(float *__restrict__ P, float *__restrict__ m, float *__restrict__ v,
@@ -778,22 +823,26 @@ rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const f
   });
   if (attr != RT_OK) return attr;
   Scratch scr;
+  const unsigned grid = (unsigned)((n + kH - 1) / kH);
   const size_t zbytes = (size_t)4 * (size_t)n * kH * sizeof(float);
-  s = scr.alloc(6 * (size_t)kTileBytes + zbytes + (size_t)n * sizeof(float), st);
+  const size_t pbytes = (size_t)grid * kGradStride * sizeof(float);
+  s = scr.alloc(6 * (size_t)kTileBytes + zbytes + (size_t)n * sizeof(float) + pbytes + 64, st);
   if (s != RT_OK) return s;
   uint16_t *tiles = scr.as<uint16_t>();
   float *Z = reinterpret_cast<float *>(scr.as<char>() + 6 * (size_t)kTileBytes);
   float *dy = Z + (size_t)4 * n * kH;
-  RT_CUDA_TRY(cudaMemsetAsync(grad, 0, kNParam * sizeof(float), st));
+  float *gpart = reinterpret_cast<float *>(
+      (reinterpret_cast<uintptr_t>(dy + n) + 63) & ~uintptr_t(63));  // 64-byte aligned rows
   RT_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
   s = mlp_prep_tiles(params, tiles, st);
   if (s != RT_OK) return s;
   const Norm N = to_norm(nm);
-  const unsigned grid = (unsigned)((n + kH - 1) / kH);
   k_mlp_fwd<true><<<grid, kH, sizeof(FwdSmem), st>>>(params, tiles, N, inputs, targets, n, Z, dy, loss,
                                                      nullptr, status);
   RT_CUDA_TRY(cudaGetLastError());
-  k_mlp_bwd<<<grid, kH, sizeof(BwdSmem), st>>>(params, tiles, N, inputs, n, Z, dy, grad, status);
+  k_mlp_bwd<<<grid, kH, sizeof(BwdSmem), st>>>(params, tiles, N, inputs, n, Z, dy, gpart, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  k_grad_reduce<<<(kNParam + 255) / 256, 256, 0, st>>>(gpart, (int)grid, grad);
   RT_CUDA_TRY(cudaGetLastError());
   if (!(flags & RT_MLP_GRAD_ONLY)) {
     const float b1 = 0.9f, b2 = 0.999f;
