@@ -179,9 +179,12 @@ __device__ __forceinline__ void ray_init(const WalkParams &W, const float4 *__re
       if (!ok) ok = marsaglia(v.z, v.w, dx, dy, dz);
     }
     if (!ok) { dx = 0.0f; dy = 0.0f; dz = 1.0f; }
-    R.ix = (int)(c % W.n[0]);
-    R.iy = (int)((c / W.n[0]) % W.n[1]);
-    R.iz = (int)(c / nxy);
+    // cell index -> (ix, iy, iz) in 32-bit unsigned arithmetic (c < ncells < 2^31)
+    const uint32_t cu = (uint32_t)c, n0 = (uint32_t)W.n[0], n1 = (uint32_t)W.n[1];
+    const uint32_t q0 = cu / n0, q1 = q0 / n1;
+    R.ix = (int)(cu - q0 * n0);
+    R.iy = (int)(q0 - q1 * n1);
+    R.iz = (int)q1;
     R.px = W.fin[0] ? __fmul_rn(__fadd_rn((float)R.ix, fx), W.h[0]) : 0.0f;
     R.py = W.fin[1] ? __fmul_rn(__fadd_rn((float)R.iy, fy), W.h[1]) : 0.0f;
     R.pz = W.fin[2] ? __fmul_rn(__fadd_rn((float)R.iz, fz), W.h[2]) : 0.0f;
