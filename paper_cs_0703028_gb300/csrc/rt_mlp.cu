@@ -50,13 +50,14 @@ __device__ __forceinline__ long long zidx(long long layer, int c, long long n, l
 }
 
 // SiLU of two pre-activations, packed as the BF16 pair the next layer reads:
-// z rounded to BF16, then z (1/2 + tanh(z/2)/2) in packed BF16 arithmetic (the
+// z rounded to BF16, then with u = z/2 (exact), SiLU(z) = z (1 + tanh(z/2)) / 2
+// = u tanh(u) + u, one fused multiply-add, in packed BF16 arithmetic (the
 // surrogate walk's inference epilogue; training keeps its SiLU in binary32).
 __device__ __forceinline__ uint32_t silu_bf16x2(float lo, float hi) {
   uint32_t z, r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(hi), "f"(lo));
-  asm("{\n .reg .b32 c, h, s;\n mov.b32 c, 0x3F003F00;\n mul.rn.bf16x2 h, %1, c;\n"
-      " tanh.approx.bf16x2 s, h;\n fma.rn.bf16x2 s, s, c, c;\n mul.rn.bf16x2 %0, %1, s;\n}"
+  asm("{\n .reg .b32 c, u, t;\n mov.b32 c, 0x3F003F00;\n mul.rn.bf16x2 u, %1, c;\n"
+      " tanh.approx.bf16x2 t, u;\n fma.rn.bf16x2 %0, u, t, u;\n}"
       : "=r"(r) : "r"(z));
   return r;
 }
@@ -506,8 +507,7 @@ constexpr int kL1Elems = kH * kL1K;
 // column k of the layer-1 operands: 3i + {0, 1, 2} for input i, 12 and 13 the bias
 __device__ __forceinline__ int l1_index(int r, int k) { return (int)(tc::kmajor_offset(r, k, kL1K) >> 1); }
 
-struct WalkSmall {
-  float b[4][kH];  // zeros (layer 1's bias is in its product), b2, b3, b4
+struct WalkSmall {  // the head; every hidden layer's bias is in its tensor-core product
   float w5[kH];
   float b5;
 };
@@ -517,11 +517,13 @@ struct WalkMlpSmem {
   uint16_t A[kWalkTiles][kTileElems];  // layer inputs of the tiles
   uint16_t A1[kWalkTiles][kL1Elems];   // layer-1 inputs (hi/lo split, K = 16)
   uint16_t B1[kL1Elems];               // layer-1 weights and bias (hi/lo split, rows = out)
+  uint16_t Bb[3][kL1Elems];            // biases of layers 2..4 against A1's constant-one columns
   WalkSmall sp;
   uint64_t bar_w, bar_mma[kWalkTiles];
   unsigned long long next;
   uint32_t tmem;
 };
+static_assert(sizeof(WalkMlpSmem) <= 227 * 1024, "surrogate walk shared memory exceeds 227 KB per block");
 
 __device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float bf16_value(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
@@ -542,13 +544,18 @@ __device__ __forceinline__ void stage_walk(WalkMlpSmem &S, const float *__restri
     }
     S.B1[l1_index(n, k)] = bits;
   }
-  for (int c = threadIdx.x; c < kH; c += blockDim.x) {
-    S.sp.b[0][c] = 0.0f;
-    S.sp.b[1][c] = P[oB2 + c];
-    S.sp.b[2][c] = P[oB3 + c];
-    S.sp.b[3][c] = P[oB4 + c];
-    S.sp.w5[c] = P[oW5 + c];
+  // layers 2..4: K = 16 operands with b_hi, b_lo in rows 12, 13 (A1's 1.0 columns), zeros elsewhere
+  for (int e = threadIdx.x; e < 3 * kL1Elems; e += blockDim.x) {
+    const int l = e / kL1Elems, n = (e % kL1Elems) / kL1K, k = e % kL1K;
+    uint16_t bits = 0;
+    if (k == 12 || k == 13) {
+      const float b = P[(l == 0 ? oB2 : (l == 1 ? oB3 : oB4)) + n];
+      const uint16_t hi = bf16_bits(b);
+      bits = (k == 13) ? bf16_bits(b - bf16_value(hi)) : hi;
+    }
+    S.Bb[l][l1_index(n, k)] = bits;
   }
+  for (int c = threadIdx.x; c < kH; c += blockDim.x) S.sp.w5[c] = P[oW5 + c];
   if (threadIdx.x == 0) S.sp.b5 = P[oB5];
 }
 
@@ -600,39 +607,33 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
     tile_sync(tile);
     if (r == 0) {
       tc::fence_after_sync();
-      if (l == 0)
-        tc::mma_bf16(tcol, tc::smem_desc(tc::smem_addr(S.A1[tile]), 128u, 256u),
-                     tc::smem_desc(tc::smem_addr(S.B1), 128u, 256u), tc::idesc_bf16_f32(128, 128), 0u);
-      else
+      const uint64_t a1 = tc::smem_desc(tc::smem_addr(S.A1[tile]), 128u, 256u);
+      if (l == 0) {
+        tc::mma_bf16(tcol, a1, tc::smem_desc(tc::smem_addr(S.B1), 128u, 256u), tc::idesc_bf16_f32(128, 128), 0u);
+      } else {
         tc::mma_128x128x128(tcol, S.A[tile], S.W[l - 1]);
+        tc::mma_bf16(tcol, a1, tc::smem_desc(tc::smem_addr(S.Bb[l - 1]), 128u, 256u),
+                     tc::idesc_bf16_f32(128, 128), 1u);  // + bias
+      }
       tc::mma_commit(&S.bar_mma[tile]);
     }
     const int timeout = tc::mbar_wait(&S.bar_mma[tile], phase, kWaitLimit) ? 0 : 1;
     phase ^= 1u;
     if (tile_or(tile, timeout)) return false;
     tc::fence_after_sync();
-    const float *bias = S.sp.b[l];
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
-      float acc[32];
-      tc::tmem_ld32(tcol + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, acc);
+      float z[32];  // pre-activations, biases included
+      tc::tmem_ld32(tcol + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, z);
       if (l < 3) {  // next layer's BF16 input
 #pragma unroll
-        for (int i = 0; i < 32; i += 8) {
-          float z[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) z[q] = acc[i + q] + bias[c0 + i + q];
+        for (int i = 0; i < 32; i += 8)
           *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0 + i)]) =
-              make_uint4(silu_bf16x2(z[0], z[1]), silu_bf16x2(z[2], z[3]), silu_bf16x2(z[4], z[5]),
-                         silu_bf16x2(z[6], z[7]));
-        }
+              make_uint4(silu_bf16x2(z[i], z[i + 1]), silu_bf16x2(z[i + 2], z[i + 3]),
+                         silu_bf16x2(z[i + 4], z[i + 5]), silu_bf16x2(z[i + 6], z[i + 7]));
       } else {  // last hidden layer: binary32 SiLU into the head
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int c = c0 + q;
-          const float z = acc[q] + bias[c];
-          y = fmaf(S.sp.w5[c], z * sigmoid_fast(z), y);
-        }
+        for (int q = 0; q < 32; ++q) y = fmaf(S.sp.w5[c0 + q], z[q] * sigmoid_fast(z[q]), y);
       }
     }
   }
