@@ -33,7 +33,14 @@ MUFU_LANES_PER_SM = 16
 # coordinate, |z|^2, series, accumulation and its share of the Kahan update);
 # Lorentz is 1 reciprocal + 4.  The roofline is set by the pipe with the larger
 # (count / measured rate): max(FP32 ops / FP32 rate, MUFU ops / MUFU rate).
-OPS_PER_EVAL = {"voigt": {"mufu": 1, "fp32": 6}, "lorentz": {"mufu": 1, "fp32": 4}}
+OPS_PER_EVAL = {"voigt": {"mufu": 1, "fp32": 6}, "lorentz": {"mufu": 1, "fp32": 4},
+                # one (cell, nu) update of Eq. I: two exponentials and a reciprocal
+                # (attenuation and Planck), interpolation, scale, the update itself
+                "march": {"mufu": 3, "fp32": 10},
+                # a near-centre Voigt value (fixed points per line): Weideman's N = 24
+                # rational series (23 complex multiply-adds, one division), the square
+                # root and reciprocal of the width, the compensated add
+                "voigt_near": {"mufu": 3, "fp32": 110}}
 
 
 def alu_roofline(evals_per_s, profile, probe, n_sm, clock_mhz):
@@ -44,7 +51,8 @@ def alu_roofline(evals_per_s, profile, probe, n_sm, clock_mhz):
     other = "fp32" if pipe == "mufu" else "mufu"
     achieved = evals_per_s * ops[pipe] / 1e12
     peak = rate[pipe] / 1e12
-    return {"bound": "alu", "pipe": {"mufu": "MUFU reciprocal", "fp32": "FP32"}[pipe],
+    mufu_name = "MUFU (ex2, rcp)" if profile == "march" else "MUFU reciprocal"
+    return {"bound": "alu", "pipe": {"mufu": mufu_name, "fp32": "FP32"}[pipe],
             "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "other_pipe_frac": evals_per_s * ops[other] / rate[other],
             "ops_per_eval": ops,
@@ -596,6 +604,99 @@ def pressure_reading_error(rt, case, kap, n_rays=1_000_000):
     return out
 
 
+def _resident_build(rt, lines):
+    """A kappa build of device-resident lines (inputs already in HBM, as in the timed
+    step of the 32^3 workload): returns build(spec, out, evals=None)."""
+    import ctypes as ct
+    import torch
+    Ld, keep = rt.make_lines(lines, memory="device")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L = rt.lib()
+
+    def build(spec, out, evals=None):
+        S = rt.make_spectral(spec)
+        st = L.rt_build_kappa(ct.byref(Ld), ct.byref(S), ct.c_void_p(out.data_ptr()),
+                              None if evals is None else ct.c_void_p(evals.data_ptr()),
+                              ct.c_void_p(status.data_ptr()),
+                              ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if st:
+            raise rt.RtError(st, "rt_build_kappa", L.rt_last_error().decode())
+    build.keep = (Ld, keep, status)
+    return build
+
+
+def run_next(args):
+    """The rows after the hot path, on the 32^3 workload's line list and table: the
+    paper's spectrally resolved marching (Eq. I per wavenumber along 4096 straight
+    paths), the fixed 16 points per line, and a second gas accumulated into the table."""
+    import torch
+    from dataclasses import replace
+    import paper_cs_0703028_gb300 as rt
+    case = synth.config(1)
+    spec = case.spec
+    probe = rt.alu_probe()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    clock = _peaks().get("sm_max_mhz", 2070.0)
+    kap = rt.build_kappa(case.lines, spec)
+    gs, keep = rt.make_grid(case.grid)
+    rng = np.random.default_rng(7)
+    n = 4096
+    pos = torch.from_numpy((rng.uniform(0.02, 0.98, (n, 3)) * 1.0).astype(np.float32)).cuda()
+    d = rng.normal(size=(n, 3))
+    d = torch.from_numpy((d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)).cuda()
+    nvis = torch.zeros(n, dtype=torch.int32, device="cuda")
+    march = lambda: rt.march(gs, kap, spec, pos, d, want_I=False, nvis=nvis)
+    for _ in range(args.warmup):
+        march()
+    ms_march = _ev_time(march, reps=args.steps)
+    updates = int(nvis.sum().item()) * spec.n_nu
+    out = {"march": {"paths": n, "cells_crossed": int(nvis.sum().item()), "updates": updates,
+                     "ms": ms_march, "updates_per_s": updates / (ms_march * 1e-3),
+                     "roofline": alu_roofline(updates / (ms_march * 1e-3), "march", probe, n_sm, clock),
+                     "note": "per call: cell preparation, the paths' walk and the marching kernel"}}
+    # fixed 16 points per line (lines resident in HBM)
+    co2 = _resident_build(rt, case.lines)
+    s16 = replace(spec, points_per_line=16)
+    ev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    k16 = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    co2(s16, k16, ev)
+    torch.cuda.synchronize()
+    ev16 = int(ev.item())
+    for _ in range(args.warmup):
+        co2(s16, k16)
+    ms16 = _ev_time(lambda: co2(s16, k16), reps=args.steps)
+    out["points_per_line_16"] = {"evals": ev16, "ms": ms16, "evals_per_s": ev16 / (ms16 * 1e-3),
+                                 "roofline": alu_roofline(ev16 / (ms16 * 1e-3), "voigt_near", probe, n_sm,
+                                                          clock),
+                                 "note": "per call: line geometry, prefactors and the gather kernel"}
+    # a second gas (an H2O-like list: 10k lines, mass 18 u) accumulated into the CO2 table
+    h2o = replace(synth.make_lines(10000, 2000.0, 3000.0, synth.rng_for(1, 9), S_lo=1e-23, S_hi=1e-20),
+                  mass_amu=18.0, n_T=0.6, q_exp=1.5)
+    s2 = replace(spec, x_ref=0.05, accumulate=1)
+    h2o_build = _resident_build(rt, h2o)
+    tab = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    e1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    e2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    co2(spec, tab, e1)
+    h2o_build(s2, tab, e2)
+    torch.cuda.synchronize()
+    ev2 = int(e1.item()) + int(e2.item())
+
+    def two_gas():
+        co2(spec, tab)
+        h2o_build(s2, tab)
+    for _ in range(args.warmup):
+        two_gas()
+    ms2 = _ev_time(two_gas, reps=args.steps)
+    out["two_gases"] = {"evals": ev2, "ms": ms2, "evals_per_s": ev2 / (ms2 * 1e-3),
+                        "roofline": alu_roofline(ev2 / (ms2 * 1e-3), "voigt", probe, n_sm, clock)}
+    res = {"metric": "Eq. I updates/s (marching), line-profile evals/s (variants)",
+           "value": out["march"]["updates_per_s"], "unit": "(cell, nu) updates/s", "higher_is_better": True,
+           "config": {"workload": "next32: 32^3 box, 20k Voigt lines, 64 T x 100k nu; 4096 paths"},
+           **out}
+    print(json.dumps(res), flush=True)
+
+
 def run_box128(args):
     """The 128^3 workload: 100k lines, 64 T x 400k nu table, and the walk."""
     import torch
@@ -606,10 +707,13 @@ def run_box128(args):
     gs, keep = rt.make_grid(case.grid)
     kap = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
     evals = torch.zeros(1, dtype=torch.int64, device="cuda")
-    rt.build_kappa(case.lines, spec, out=kap, evals=evals)
+    build = _resident_build(rt, case.lines)  # lines resident in HBM
+    build(spec, kap, evals)
     torch.cuda.synchronize()
     ev = int(evals.item())
-    ms_build = _ev_time(lambda: rt.build_kappa(case.lines, spec, out=kap), reps=args.steps)
+    for _ in range(args.warmup):
+        build(spec, kap)
+    ms_build = _ev_time(lambda: build(spec, kap), reps=args.steps)
     from paper_cs_0703028_gb300 import autotune
     walk_shape, walk_ms = autotune.tune_walk(gs, case.grid.ncells, spec, kap, min(n, 10_000_000),
                                              use_cache=False)
@@ -645,7 +749,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--workload", default="box32", choices=["box32", "surrogate", "batched", "box128"])
+    ap.add_argument("--workload", default="box32", choices=["box32", "surrogate", "batched", "box128", "next"])
     ap.add_argument("--samples", type=int, default=20_000_000)
     ap.add_argument("--epochs", type=int, default=1)
     ap.add_argument("--rays", type=int, default=2_000_000)
@@ -657,6 +761,8 @@ def main():
         return run_batched(args)
     if args.workload == "box128":
         return run_box128(args)
+    if args.workload == "next":
+        return run_next(args)
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":

@@ -310,12 +310,14 @@ rt_status rt_get_tuning(rt_tuning *t);
  *   I_out   optional device [n_paths][n_nu]: the intensity leaving the grid.
  *   power   device [n_paths] (binary64, overwritten): sum_j (I_in - I_out) dnu [m^-1],
  *           W m^-2 sr^-1 lost by the beam along the path.
+ *   nvis    optional device [n_paths] (overwritten): the number of cells each path
+ *           crosses (each crossing is n_nu updates of Eq. I).
  *   status  optional device status word (RT_DEV_NONFINITE, RT_DEV_STEPCAP).
  * n_paths <= 65535 per call.  Asynchronous.
  */
 rt_status rt_march(const rt_grid *grid, const float *kappa, const rt_spectral *spec,
                    int64_t n_paths, const float *pos, const float *dir, const float *I_in,
-                   float *I_out, double *power, uint32_t *status, void *stream);
+                   float *I_out, double *power, int32_t *nvis, uint32_t *status, void *stream);
 
 /* Zero a tally buffer of ncells cells (asynchronous). */
 rt_status rt_tally_zero(const rt_tally_buf *tally, int64_t ncells, void *stream);

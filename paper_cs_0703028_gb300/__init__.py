@@ -100,7 +100,7 @@ _SIGNATURES = {
     "rt_batch_trace": ([_P, _P, _P], ct.c_int),
     "rt_batch_destroy": ([_P], ct.c_int),
     "rt_trace_batch": ([ct.c_int32, _P, _P, _P, ct.c_uint64, ct.c_int32, _P, _P], ct.c_int),
-    "rt_march": ([_P, _P, _P, ct.c_int64, _P, _P, _P, _P, _P, _P, _P], ct.c_int),
+    "rt_march": ([_P, _P, _P, ct.c_int64, _P, _P, _P, _P, _P, _P, _P, _P], ct.c_int),
     "rt_set_tuning": ([_P], ct.c_int),
     "rt_get_tuning": ([_P], ct.c_int),
 }
@@ -436,15 +436,16 @@ class Batch:
             pass
 
 
-def march(grid_struct, kappa, spec, pos, dirs, I_in=None, want_I=True, stream=None):
-    """rt_march on CUDA tensors pos, dirs [n, 3]; returns (I_out [n, n_nu] or None, power [n])."""
+def march(grid_struct, kappa, spec, pos, dirs, I_in=None, want_I=True, nvis=None, stream=None):
+    """rt_march on CUDA tensors pos, dirs [n, 3]; returns (I_out [n, n_nu] or None, power [n]).
+    ``nvis`` (optional int32 CUDA tensor [n]) receives the number of cells each path crosses."""
     import torch
     n = int(pos.shape[0])
     S = make_spectral(spec)
     I_out = torch.empty((n, int(spec.n_nu)), dtype=torch.float32, device="cuda") if want_I else None
     power = torch.zeros(n, dtype=torch.float64, device="cuda")
     st = lib().rt_march(ct.byref(grid_struct), _ptr(kappa), ct.byref(S), n, _ptr(pos), _ptr(dirs),
-                        _ptr(I_in), _ptr(I_out), _ptr(power), None, _stream_ptr(stream))
+                        _ptr(I_in), _ptr(I_out), _ptr(power), _ptr(nvis), None, _stream_ptr(stream))
     _check(st, "rt_march")
     return I_out, power
 

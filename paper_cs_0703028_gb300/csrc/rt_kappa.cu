@@ -661,6 +661,62 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
   }
 }
 
+// Fixed points per line (each line on the few grid points around its centre):
+// one thread per (point j, T node); the lines whose windows hold j are a
+// contiguous index range (windows are monotone in the sorted line index), found
+// by binary search within the block's range, and summed in ascending nu0 with
+// compensation.  Every point is near its lines' centres, so each value is the
+// near-centre form (faddeeva_re_near) rather than a far-wing series.
+template <int PROFILE>
+__global__ void __launch_bounds__(kTilePts)
+k_kappa_ppl(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_lines, long long n_nu,
+            WeidCoef wc, int accumulate, float *__restrict__ kappa) {
+  __shared__ long long s_range[2];
+  const long long jw0 = (long long)blockIdx.x * kTilePts;
+  const long long jend = min(jw0 + (long long)kTilePts, n_nu);
+  const int k = blockIdx.y;
+  if (threadIdx.x == 0) {
+    s_range[0] = lower_bound_hi(R, n_lines, (int)jw0);
+    s_range[1] = max(s_range[0], lower_bound_lo(R, n_lines, (int)jend));
+  }
+  __syncthreads();
+  const long long j = jw0 + threadIdx.x;
+  if (j >= n_nu) return;
+  // lines [a, b) of the block's range with hi >= j and lo <= j
+  long long a = s_range[0], hi_end = s_range[1];
+  while (a < hi_end) {
+    const long long m = (a + hi_end) >> 1;
+    if (__ldg(&R[m].y) < (int)j) a = m + 1; else hi_end = m;
+  }
+  long long b = a, b_end = s_range[1];
+  while (b < b_end) {
+    const long long m = (b + b_end) >> 1;
+    if (__ldg(&R[m].x) <= (int)j) b = m + 1; else b_end = m;
+  }
+  const float4 *Pk = P + (long long)k * n_lines;
+  float acc = 0.0f, cmp = 0.0f;
+  for (long long l = a; l < b; ++l) {
+    const int4 r = __ldg(R + l);
+    const float4 p = __ldg(Pk + l);
+    const float u = __fadd_rn((float)((int)j - r.z), __int_as_float(r.w));
+    float v;
+    if (PROFILE == RT_PROFILE_LORENTZ) {
+      v = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
+    } else {
+      const float x = p.y * u;
+      const float y = sqrtf(p.z);
+      v = __fdividef(p.x, y) * faddeeva_re_near(x, y, __fmaf_rn(x, x, p.z), wc);
+    }
+    const float yk = __fsub_rn(v, cmp);
+    const float t = __fadd_rn(acc, yk);
+    cmp = __fsub_rn(__fsub_rn(t, acc), yk);
+    acc = t;
+  }
+  float *dst = kappa + (long long)k * n_nu + j;
+  const float out = __fsub_rn(acc, cmp);
+  *dst = accumulate ? *dst + out : out;
+}
+
 int g_kappa_tpb = kMaxTPerBlock;
 
 rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *tiles,
@@ -680,6 +736,17 @@ rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *t
     W = (!(w < (double)(1 << 28))) ? (1 << 28) : (int)std::ceil(w);
   }
   const long long n_tiles = (spec->n_nu + kTilePts - 1) / kTilePts;
+  if (spec->points_per_line > 0) {  // fixed points per line: the gather kernel
+    dim3 g((unsigned)n_tiles, (unsigned)spec->nT);
+    if (spec->profile == RT_PROFILE_LORENTZ)
+      k_kappa_ppl<RT_PROFILE_LORENTZ><<<g, kTilePts, 0, st>>>(P, R, n, spec->n_nu, wc,
+                                                              spec->accumulate ? 1 : 0, kappa);
+    else
+      k_kappa_ppl<RT_PROFILE_VOIGT><<<g, kTilePts, 0, st>>>(P, R, n, spec->n_nu, wc,
+                                                            spec->accumulate ? 1 : 0, kappa);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+  }
   k_tile_lines<<<(unsigned)((n_tiles + 127) / 128), 128, 0, st>>>(R, n, spec->n_nu, W, far_bits,
                                                                     n_tiles, tiles);
   RT_CUDA_TRY(cudaGetLastError());
