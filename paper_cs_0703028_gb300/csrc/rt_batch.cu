@@ -90,6 +90,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
     Ray R;
     float4 cd = make_float4(0.0f, 0.0f, 0.0f, 0.0f);  // data of the ray's current cell
     const float2 *krow = nullptr;  // node-pair table: the ray's wavenumber row
+    const float *krow1 = nullptr;  // wavenumber-major table: the ray's row
     bool active = false;
     for (;;) {
       const unsigned idle = __ballot_sync(0xffffffffu, !active);
@@ -98,6 +99,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
         if (!active && next + rank < last) {
           ray_init(W, cells, tab, next + rank, false, R, &cd);
           if (TAB == 2) krow = reinterpret_cast<const float2 *>(tab) + (long long)R.j * (W.nT - 1);
+          if (TAB == 1) krow1 = tab + (long long)R.j * W.nT;
           active = true;
         }
         next += __popc(idle);
@@ -108,7 +110,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
 #pragma unroll
       for (int u = 0; u < kBatchUnroll; ++u) {  // steps per pass of the loop
         if (!done) {
-          const float kap = TAB == 2 ? cell_kappa_row(cd, krow) : cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j);
+          const float kap = TAB == 2 ? cell_kappa_row(cd, krow) : (TAB == 1 ? cell_kappa_row1(cd, krow1, W.nT) : cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j));
           float4 cdn = cd;
           done = ray_step<false, false, true>(W, kap, D.absorbed, D.status, rec, R, true,
                                               [&](int c) { cdn = __ldg(cells + c); }, s_axes[warp]);

@@ -116,6 +116,14 @@ __device__ __forceinline__ float cell_kappa_row(const float4 cd, const float2 *_
   return cd.y * fmaf(cd.x, v.y, (1.0f - cd.x) * v.x);
 }
 
+// The same from the ray's row of a wavenumber-major table, row = tabt + j nT.
+__device__ __forceinline__ float cell_kappa_row1(const float4 cd, const float *__restrict__ row, int nT) {
+  const float *c = row + __float_as_int(cd.w);
+  const float v0 = __ldg(c);
+  if (nT < 2) return cd.y * v0;
+  return cd.y * fmaf(cd.x, __ldg(c + 1), (1.0f - cd.x) * v0);
+}
+
 // kappa of a cell from the walk table in layout L (0 T-major, 1 wavenumber-major, 2 pairs).
 template <int L>
 __device__ __forceinline__ float cell_kappa_l(const float4 cd, const float *__restrict__ tab, int nT,
