@@ -4,11 +4,11 @@
 //   I_out = I_in exp(-kappa l) + I_b(nu_j, T_cell) (1 - exp(-kappa l)),
 // cell after cell, and the power lost by the beam is sum_j (I_in - I_out) dnu.
 // The paper runs one full-screen pass per crossed cell over the spectral
-// samples; here one block owns a slice of 512 wavenumbers of one ray (two per
+// samples; here one block owns a slice of 1024 wavenumbers of one ray (four per
 // thread) and loops over the ray's cells, so consecutive threads read consecutive
 // table entries.
 //   k_march_path : per ray, the binary32 walk (cells and lengths), as rt_trace.
-//   k_march      : per (512-wavenumber slice, ray), Eq. (I) over the cells, two
+//   k_march      : per (1024-wavenumber slice, ray), Eq. (I) over the cells, four
 //                  wavenumbers per thread, and a binary64 block sum of
 //                  (I_in - I_out) dnu.
 #include <cmath>
@@ -109,17 +109,18 @@ __device__ __forceinline__ float2 expm1_pos2(float2 x) {
   return make_float2(x.x < 0.25f ? s.x : __expf(x.x) - 1.0f, x.y < 0.25f ? s.y : __expf(x.y) - 1.0f);
 }
 
-// Block = 512 wavenumbers (two per thread) of one path.  The path's cells are
-// staged in shared memory with their per-cell constants folded: the optical
-// depth of a crossing is a = A kappa_k + B kappa_k+1 with A = 100 l s (1 - frac),
-// B = 100 l s frac (l the length in m, s the density scale), so one crossing
-// costs two table loads, two paired multiply-adds for a, the two exponentials of
-// Eq. I and Eq. planck, and the update I <- I + (1 - e^-a)(I_b - I).
-// VEC2: n_nu even and the table 8-byte aligned, so both wavenumbers come in one
-// 8-byte load per table row.
-constexpr int kMarchPts = 2;
+// Block = 1024 wavenumbers (four per thread, as two pairs) of one path.  The
+// path's cells are staged in shared memory with their per-cell constants folded:
+// the optical depth of a crossing is a = A kappa_k + B kappa_k+1 with
+// A = 100 l s (1 - frac), B = 100 l s frac (l the length in m, s the density
+// scale), so one crossing costs the table loads, two paired multiply-adds for a,
+// the two exponentials of Eq. I and Eq. planck, and the update
+// I <- I + (1 - e^-a)(I_b - I), for each pair.
+// VEC: 4 when n_nu is a multiple of 4 and the table 16-byte aligned (one 16-byte
+// load per table row), 2 when n_nu is even and the table 8-byte aligned, else 1.
+constexpr int kMarchPts = 4;
 
-template <bool VEC2>
+template <int VEC>
 __global__ void __launch_bounds__(kMarchThreads)
 k_march(const float4 *__restrict__ cells, const float *__restrict__ tab, MarchParams M,
         const int *__restrict__ vis_cell, const float *__restrict__ vis_len, const int *__restrict__ nvis,
@@ -129,14 +130,21 @@ k_march(const float4 *__restrict__ cells, const float *__restrict__ tab, MarchPa
   __shared__ double s_red[kMarchThreads / 32];
   const long long r = blockIdx.y;
   const long long j0 = ((long long)blockIdx.x * kMarchThreads + threadIdx.x) * kMarchPts;
-  const bool ok0 = j0 < M.n_nu, ok1 = j0 + 1 < M.n_nu;
+  bool ok[kMarchPts];
+#pragma unroll
+  for (int q = 0; q < kMarchPts; ++q) ok[q] = j0 + q < M.n_nu;
   const int nv = nvis[r];
-  const float2 nu_m = make_float2(100.0f * fmaf((float)j0, M.dnu, M.nu_min),
-                                  100.0f * fmaf((float)(j0 + 1), M.dnu, M.nu_min));
-  const float2 pre = __fmul2_rn(__fmul2_rn(__fmul2_rn(dup2(M.two_hc2), nu_m), nu_m), nu_m);
-  const float2 c2nu = __fmul2_rn(dup2(M.c2_m), nu_m);
-  const float2 I0 = make_float2((ok0 && I_in) ? I_in[j0] : 0.0f, (ok1 && I_in) ? I_in[j0 + 1] : 0.0f);
-  float2 I = I0;
+  float2 pre[2], c2nu[2], I0[2], I[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float2 nu_m = make_float2(100.0f * fmaf((float)(j0 + 2 * h), M.dnu, M.nu_min),
+                                    100.0f * fmaf((float)(j0 + 2 * h + 1), M.dnu, M.nu_min));
+    pre[h] = __fmul2_rn(__fmul2_rn(__fmul2_rn(dup2(M.two_hc2), nu_m), nu_m), nu_m);
+    c2nu[h] = __fmul2_rn(dup2(M.c2_m), nu_m);
+    I0[h] = make_float2((ok[2 * h] && I_in) ? I_in[j0 + 2 * h] : 0.0f,
+                        (ok[2 * h + 1] && I_in) ? I_in[j0 + 2 * h + 1] : 0.0f);
+    I[h] = I0[h];
+  }
   for (int v0 = 0; v0 < nv; v0 += kMarchMaxVis) {
     const int cnt = min(kMarchMaxVis, nv - v0);
     __syncthreads();
@@ -147,31 +155,57 @@ k_march(const float4 *__restrict__ cells, const float *__restrict__ tab, MarchPa
       s_row[v] = (long long)__float_as_int(cd.w) * M.n_nu;
     }
     __syncthreads();
-    if (ok0) {
+    if (ok[0]) {
       for (int v = 0; v < cnt; ++v) {
         const float4 c = s_c[v];
         const float *p0 = tab + s_row[v] + j0;
-        float2 t0, t1 = make_float2(0.0f, 0.0f);
-        if (VEC2) {
-          t0 = __ldg(reinterpret_cast<const float2 *>(p0));
-          if (M.nT >= 2) t1 = __ldg(reinterpret_cast<const float2 *>(p0 + M.n_nu));
+        float2 t0[2], t1[2];
+        if (VEC == 4) {
+          const float4 a0 = __ldg(reinterpret_cast<const float4 *>(p0));
+          t0[0] = make_float2(a0.x, a0.y);
+          t0[1] = make_float2(a0.z, a0.w);
+          float4 a1 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (M.nT >= 2) a1 = __ldg(reinterpret_cast<const float4 *>(p0 + M.n_nu));
+          t1[0] = make_float2(a1.x, a1.y);
+          t1[1] = make_float2(a1.z, a1.w);
         } else {
-          t0 = make_float2(__ldg(p0), ok1 ? __ldg(p0 + 1) : 0.0f);
-          if (M.nT >= 2) t1 = make_float2(__ldg(p0 + M.n_nu), ok1 ? __ldg(p0 + M.n_nu + 1) : 0.0f);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            t1[h] = make_float2(0.0f, 0.0f);
+            if (VEC == 2 && ok[2 * h]) {  // n_nu even: both points of the pair or neither
+              t0[h] = __ldg(reinterpret_cast<const float2 *>(p0 + 2 * h));
+              if (M.nT >= 2) t1[h] = __ldg(reinterpret_cast<const float2 *>(p0 + M.n_nu + 2 * h));
+            } else {
+              t0[h] = make_float2(ok[2 * h] ? __ldg(p0 + 2 * h) : 0.0f, ok[2 * h + 1] ? __ldg(p0 + 2 * h + 1) : 0.0f);
+              if (M.nT >= 2)
+                t1[h] = make_float2(ok[2 * h] ? __ldg(p0 + M.n_nu + 2 * h) : 0.0f,
+                                    ok[2 * h + 1] ? __ldg(p0 + M.n_nu + 2 * h + 1) : 0.0f);
+            }
+          }
         }
-        const float2 a = __ffma2_rn(dup2(c.y), t1, __fmul2_rn(dup2(c.x), t0));  // optical depth
-        const float2 att = one_minus_exp_neg2(a);                                // 1 - exp(-kappa l)
-        const float2 em1 = expm1_pos2(__fmul2_rn(c2nu, dup2(c.z)));
-        const float2 ib = make_float2(__fdividef(pre.x, em1.x), __fdividef(pre.y, em1.y));  // Eq. (planck)
-        I = __ffma2_rn(att, __fadd2_rn(ib, neg2(I)), I);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 a = __ffma2_rn(dup2(c.y), t1[h], __fmul2_rn(dup2(c.x), t0[h]));  // optical depth
+          const float2 att = one_minus_exp_neg2(a);                                      // 1 - exp(-kappa l)
+          const float2 em1 = expm1_pos2(__fmul2_rn(c2nu[h], dup2(c.z)));
+          const float2 ib = make_float2(__fdividef(pre[h].x, em1.x), __fdividef(pre[h].y, em1.y));  // Eq. (planck)
+          I[h] = __ffma2_rn(att, __fadd2_rn(ib, neg2(I[h])), I[h]);
+        }
       }
     }
   }
-  if (I_out) {
-    if (ok0) I_out[r * M.n_nu + j0] = I.x;
-    if (ok1) I_out[r * M.n_nu + j0 + 1] = I.y;
+  double d = 0.0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (ok[2 * h]) {
+      if (I_out) I_out[r * M.n_nu + j0 + 2 * h] = I[h].x;
+      d += (double)(I0[h].x - I[h].x);
+    }
+    if (ok[2 * h + 1]) {
+      if (I_out) I_out[r * M.n_nu + j0 + 2 * h + 1] = I[h].y;
+      d += (double)(I0[h].y - I[h].y);
+    }
   }
-  double d = (ok0 ? (double)(I0.x - I.x) : 0.0) + (ok1 ? (double)(I0.y - I.y) : 0.0);
   d *= (double)M.dnu_m;
   for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
   if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = d;
@@ -232,11 +266,10 @@ rt_status march_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   RT_CUDA_TRY(cudaGetLastError());
   const long long per_block = (long long)kMarchThreads * kMarchPts;
   dim3 g((unsigned)((spec->n_nu + per_block - 1) / per_block), (unsigned)n_paths);
-  const bool vec2 = spec->n_nu % 2 == 0 && (reinterpret_cast<uintptr_t>(kappa) & 7u) == 0;
-  if (vec2)
-    k_march<true><<<g, kMarchThreads, 0, st>>>(cells, kappa, M, vis_cell, vis_len, nvis, I_in, I_out, power);
-  else
-    k_march<false><<<g, kMarchThreads, 0, st>>>(cells, kappa, M, vis_cell, vis_len, nvis, I_in, I_out, power);
+  const uintptr_t ka = reinterpret_cast<uintptr_t>(kappa);
+  const int vec = (spec->n_nu % 4 == 0 && (ka & 15u) == 0) ? 4 : ((spec->n_nu % 2 == 0 && (ka & 7u) == 0) ? 2 : 1);
+  auto kernel = vec == 4 ? k_march<4> : (vec == 2 ? k_march<2> : k_march<1>);
+  kernel<<<g, kMarchThreads, 0, st>>>(cells, kappa, M, vis_cell, vis_len, nvis, I_in, I_out, power);
   RT_CUDA_TRY(cudaGetLastError());
   if (nvis_out)
     RT_CUDA_TRY(cudaMemcpyAsync(nvis_out, nvis, sizeof(int32_t) * (size_t)n_paths, cudaMemcpyDeviceToDevice, st));

@@ -58,9 +58,10 @@ def _cells_crossed(g, pos, d):
     return out
 
 
-@pytest.mark.parametrize("kind,n_nu", [("box", 3000), ("slab", 3000), ("box", 2999)])
+@pytest.mark.parametrize("kind,n_nu", [("box", 3000), ("slab", 3000), ("box", 3002), ("box", 2999)])
 def test_march_matches_oracle(rt, kind, n_nu):
-    # n_nu odd: the kernel's scalar-load variant and a ragged last wavenumber pair
+    # the kernel loads 4, 2 or 1 table entries at a time as n_nu is a multiple of 4,
+    # even or odd; 3002 and 2999 also leave a ragged last group of wavenumbers
     import torch
     rng = synth.rng_for(9, 70)
     lines = synth.make_lines(300, 2000.0, 2070.0, rng)
