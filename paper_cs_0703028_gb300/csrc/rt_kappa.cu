@@ -1,6 +1,6 @@
 // Absorption-coefficient table on a temperature grid: Eqs. (S) and (tau) of
 // Section 3, for one absorbing gas, with Lorentz or Voigt line shapes and a
-// wing cutoff.  Four kernels:
+// wing cutoff.  Five kernels:
 //   k_line_geometry : per line, the binary64 grid decisions (cutoff window
 //                     [j_lo, j_hi], nearest grid index j_c and offset) and the
 //                     profile-evaluation count; validates device-resident lists.
@@ -18,6 +18,8 @@
 //                     copies (cp.async.bulk + mbarrier), double buffered; each
 //                     lane owns 8 consecutive points (two float4 stores) and
 //                     Kahan-sums over lines in ascending nu0.
+//   k_kappa_ppl     : with a fixed number of points per line, one thread per
+//                     (point, T node) over the few lines whose windows hold it.
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -163,7 +165,7 @@ __device__ __forceinline__ void prefactor_one(const double *__restrict__ nu0, co
     // far wing: c0 t (1 + 1.5 t + (3.75 - 2 y^2) t^2 - 15 y^2 t^3 + 12 y^4 t^4), t = 1/|z|^2
     const float c0 = A * s * (float)(1.0 / kPi) * y;
     out = make_float4(c0, sd, y2, __fmaf_rn(-2.0f, y2, 3.75f) * c0);
-    // half-width (grid units) of |z| < 10, inside which the general path queues points
+    // half-width (grid units) of |z| < 10, inside which the general path takes the near form
     const float u_core = sqrtf(fmaxf(100.0f - y2, 0.0f)) / sd;
     P2out[(long long)k * Q.n_lines + l] = make_float4(-15.0f * y2 * c0, 12.0f * y2 * y2 * c0, u_near, u_core);
     // (27 y^2 / 2^-24)^(1/6) = 27.66 y^(1/3) and (2^25 (3.75 + 2 y^2))^(1/4), with 5 %
@@ -362,10 +364,12 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 v) {
 // rounding error is relative to the distance itself.
 // Voigt far wing (|z| >= 20): with t = 1/|z|^2 the three-term series is the
 // polynomial c0 t + c1 t^2 + c2 t^3 + c3 t^4 + c4 t^5 (coefficients from
-// k_prefactor).  Fast-path lines (whole tile covered, no near-centre point) add
-// kGroup lines per compensated add; the other lines take a warp-uniform interval
-// test that sends near-centre points, compacted across the warp, to
-// faddeeva_re_near, mask the ends of their windows, and add in pairs.
+// k_prefactor).  The binary32 arithmetic runs on pairs of a lane's points (f32x2
+// instructions).  Fast-path lines (whole tile covered, no near-centre point, or
+// far lines with masked window ends) add kGroup lines per compensated add; the
+// general-path lines evaluate a four-term series, replace the points of their
+// contiguous near-centre range by faddeeva_re_near (one point per lane, handed
+// back through shared memory), mask the ends of their windows, and add in pairs.
 // Lorentz: P = {A g / (pi dnu), g^2}.
 template <int PROFILE>
 __global__ void __launch_bounds__(32 * kMaxTPerBlock, 3)

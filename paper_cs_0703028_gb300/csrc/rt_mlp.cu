@@ -9,8 +9,12 @@
 //                pre-activations, the output gradient and the loss.
 //   k_mlp_bwd  : per 128-row tile, for each of layers 4..2 two tcgen05 products
 //                (dW = dZ^T H, dH = dZ W), SiLU derivative epilogues, bias and
-//                first-layer gradients; gradients accumulate in FP32.
+//                first-layer gradients, written to the tile's own FP32 partial.
+//   k_grad_reduce : the gradient, the tiles' partials summed in tile order.
 //   k_mlp_adam : Adam update of the FP32 masters (Kingma and Ba).
+//   k_walk_mlp : the Monte-Carlo walk with the network in place of the table
+//                (three 128-ray tiles per block; every layer, biases included,
+//                on the tensor cores).
 #include <cuda_bf16.h>
 
 #include <cmath>

@@ -2,9 +2,12 @@
 // final tally reduction.
 //   k_cell_prep : per cell, the binary32 temperature bracket (k, frac) of the
 //                 kappa table, the density scale (p x)/(p_ref x_ref) and T.
+//   k_pair_table: the walk's copy of the table, {kappa_k, kappa_k+1} per
+//                 (wavenumber, node), so a step's interpolation is one 8-byte load.
 //   k_walk      : per ray, Philox draws -> emission cell, wavenumber, position,
 //                 isotropic direction -> cell-by-cell walk with Beer-Lambert
-//                 attenuation (Eq. I, first term), binary64 atomic deposits.
+//                 attenuation (Eq. I, first term), binary64 atomic deposits;
+//                 persistent warps refilled by ballot.
 //   k_reduce / k_final : deterministic two-pass binary64 sum of the absorbed
 //                 power and the energy balance.
 #include <cmath>
