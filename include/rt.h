@@ -372,6 +372,24 @@ rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
                             float *loss, uint32_t *status, void *stream);
 
 /*
+ * n_steps consecutive training steps without a host round trip per step.  Step
+ * s = step_first - 1 + i (i = 0 .. n_steps - 1; step_first >= 1) is
+ * rt_mlp_train_step on the batch of `batch` samples starting at row
+ * (s mod (n / batch)) * batch of inputs / targets (device [n][4], [n]; the
+ * n mod batch trailing rows are not used), with Adam step number s + 1 and the
+ * cosine learning rate
+ *   lr(s) = lr1 + (lr0 - lr1) (1 + cos(pi s / max(1, total_steps - 1))) / 2
+ * evaluated in binary64 and rounded to binary32.  losses (optional device
+ * [n_steps]) receives each step's loss.  Requires 1 <= batch <= n and
+ * step_first - 1 + n_steps <= total_steps.  Asynchronous.
+ */
+rt_status rt_mlp_train_steps(float *params, float *adam_m, float *adam_v, float *grad,
+                             const float *inputs, const float *targets, int64_t n, int64_t batch,
+                             const rt_mlp_norm *norm, double lr0, double lr1, int32_t step_first,
+                             int32_t n_steps, int32_t total_steps, float *losses, uint32_t *status,
+                             void *stream);
+
+/*
  * rt_trace_mlp -- rt_trace (RT_SRC_EMIT) with the absorption coefficient of every
  * visited cell taken from the surrogate network at the cell's state:
  *   kappa = exp(MLP(log nu_j, T_cell, p_cell, x_cell)) [cm^-1]

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "rt_mlp_forward": ([_P, _P, _P, ct.c_int64, _P, _P, _P], ct.c_int),
     "rt_mlp_train_step": ([_P, _P, _P, _P, _P, _P, ct.c_int64, _P, ct.c_float, ct.c_int32, ct.c_int32,
                            _P, _P, _P], ct.c_int),
+    "rt_mlp_train_steps": ([_P, _P, _P, _P, _P, _P, ct.c_int64, ct.c_int64, _P, ct.c_double, ct.c_double,
+                            ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_tc_selftest": ([_P, _P, _P, _P, _P], ct.c_int),
     "rt_alu_probe": ([_P, _P], ct.c_int),
     "rt_trace_mlp": ([_P, _P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
@@ -321,6 +323,19 @@ class MlpTrainer:
                                      _ptr(self.status), _stream_ptr(stream))
         _check(st, "rt_mlp_train_step")
         return self.loss
+
+    def steps(self, inputs, targets, batch, lr0, lr1, step_first, n_steps, total_steps, losses=None,
+              stream=None):
+        """rt_mlp_train_steps: n_steps Adam steps over consecutive batches with the cosine
+        learning rate from lr0 to lr1 over total_steps; losses (optional float32 CUDA
+        tensor [n_steps]) receives each step's loss."""
+        st = lib().rt_mlp_train_steps(_ptr(self.params), _ptr(self.m), _ptr(self.v), _ptr(self.grad),
+                                      _ptr(inputs), _ptr(targets), int(inputs.shape[0]), int(batch),
+                                      ct.byref(self.norm), float(lr0), float(lr1), int(step_first),
+                                      int(n_steps), int(total_steps), _ptr(losses), _ptr(self.status),
+                                      _stream_ptr(stream))
+        _check(st, "rt_mlp_train_steps")
+        self.step_no = int(step_first) - 1 + int(n_steps)
 
 
 def trace_mlp(grid_struct, params, norm, spec, tally: Tally, n_rays: int, ray_begin: int = 0,

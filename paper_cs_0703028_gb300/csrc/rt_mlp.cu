@@ -17,6 +17,7 @@
 //                on the tensor cores).
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -28,6 +29,7 @@ namespace rt {
 namespace {
 
 constexpr int kH = 128;
+constexpr double kPiD = 3.14159265358979323846;
 constexpr int kNParam = 50305;
 constexpr int oW1 = 0, oB1 = 512, oW2 = 640, oB2 = 17024, oW3 = 17152, oB3 = 33536, oW4 = 33664,
               oB4 = 50048, oW5 = 50176, oB5 = 50304;
@@ -858,6 +860,38 @@ rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const f
   return RT_OK;
 }
 
+rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, const float *inputs,
+                              const float *targets, int64_t n, int64_t batch, const rt_mlp_norm *nm,
+                              double lr0, double lr1, int32_t step_first, int32_t n_steps,
+                              int32_t total_steps, float *losses, uint32_t *status, cudaStream_t st) {
+  if (!inputs || !targets) return fail(RT_E_INVAL, "rt_mlp_train_steps: NULL buffer");
+  if (batch < 1 || batch > n) return fail(RT_E_INVAL, "rt_mlp_train_steps: batch must be in [1, n]");
+  if (step_first < 1 || n_steps < 0 || total_steps < 1 ||
+      (int64_t)step_first - 1 + n_steps > (int64_t)total_steps)
+    return fail(RT_E_INVAL, "rt_mlp_train_steps: need step_first >= 1, n_steps >= 0, "
+                            "step_first - 1 + n_steps <= total_steps");
+  if (!std::isfinite(lr0) || !std::isfinite(lr1) || lr0 < 0 || lr1 < 0)
+    return fail(RT_E_INVAL, "rt_mlp_train_steps: finite learning rates >= 0 required");
+  float *loss1 = nullptr;
+  Scratch scr;
+  if (!losses) {
+    rt_status s = scr.alloc(sizeof(float), st);
+    if (s != RT_OK) return s;
+    loss1 = scr.as<float>();
+  }
+  const int64_t nb = n / batch;
+  const double span = (double)std::max(1, total_steps - 1);
+  for (int32_t i = 0; i < n_steps; ++i) {
+    const int64_t s = (int64_t)step_first - 1 + i;
+    const int64_t b = s % nb;
+    const double lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + std::cos(kPiD * (double)s / span));
+    rt_status r = mlp_train_impl(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, nm,
+                                 (float)lr, (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, st);
+    if (r != RT_OK) return r;
+  }
+  return RT_OK;
+}
+
 rt_status mlp_forward_impl(const float *params, const rt_mlp_norm *nm, const float *inputs, int64_t n,
                            float *out, uint32_t *status, cudaStream_t st) {
   if (!params || !inputs || !out) return fail(RT_E_INVAL, "rt_mlp_forward: NULL buffer");
@@ -971,6 +1005,15 @@ rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
                             float *loss, uint32_t *status, void *stream) {
   return rt::mlp_train_impl(params, adam_m, adam_v, grad, inputs, targets, n, norm, lr, step, flags,
                             loss, status, (cudaStream_t)stream);
+}
+
+rt_status rt_mlp_train_steps(float *params, float *adam_m, float *adam_v, float *grad,
+                             const float *inputs, const float *targets, int64_t n, int64_t batch,
+                             const rt_mlp_norm *norm, double lr0, double lr1, int32_t step_first,
+                             int32_t n_steps, int32_t total_steps, float *losses, uint32_t *status,
+                             void *stream) {
+  return rt::mlp_train_steps_impl(params, adam_m, adam_v, grad, inputs, targets, n, batch, norm, lr0, lr1,
+                                  step_first, n_steps, total_steps, losses, status, (cudaStream_t)stream);
 }
 
 rt_status rt_mlp_forward(const float *params, const rt_mlp_norm *norm, const float *inputs,

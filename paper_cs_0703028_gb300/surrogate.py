@@ -49,13 +49,14 @@ def train_surrogate(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, n_samples=2_000_0
     tr = MlpTrainer(params, norm)
     nb = n_samples // batch
     total = nb * epochs
+    # all steps in one library call (batch b = s mod nb, cosine learning rate), the
+    # per-step losses kept on the device and read once
+    losses = torch.zeros(max(total, 1), dtype=torch.float32, device="cuda")
+    tr.steps(inputs[:nb * batch], targets[:nb * batch], batch, lr0, lr1, 1, total, total, losses=losses)
     hist = []
-    for s in range(total):
-        b = s % nb
-        lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * s / max(1, total - 1)))
-        loss = tr.step(inputs[b * batch:(b + 1) * batch], targets[b * batch:(b + 1) * batch], lr)
-        if log_every and (s % log_every == 0 or s == total - 1):
-            hist.append((s, float(loss.item())))
+    if log_every and total:
+        lh = losses.cpu().numpy()
+        hist = [(s, float(lh[s])) for s in range(total) if s % log_every == 0 or s == total - 1]
     return params, norm, hist
 
 

@@ -120,3 +120,32 @@ def test_training_reduces_loss(rt):
         tr.step(x, t, 2e-3)
     last = float(tr.step(x, t, 2e-3).item())
     assert last < 0.05 * first, (first, last)
+
+
+def test_multi_step_training_equals_single_steps(rt):
+    # rt_mlp_train_steps is rt_mlp_train_step in a library loop: same batches, Adam
+    # step numbers and cosine learning rates, so the parameters agree bit for bit
+    # (the gradient's tile partials are summed in a fixed order)
+    import math
+    import torch
+    n, batch, total = 3 * 1024 + 100, 1024, 7
+    raw = _inputs(n, 8)
+    target = np.random.default_rng(9).normal(0, 1, n).astype(np.float32)
+    norm = rt.make_norm(LO, HI, 0.0, 1.0)
+    x, t = torch.from_numpy(raw).cuda(), torch.from_numpy(target).cuda()
+    lr0, lr1 = 1e-3, 1e-5
+    a = rt.MlpTrainer(torch.from_numpy(synth.mlp_init(4)).cuda(), norm)
+    la = []
+    for s in range(total):
+        b = s % (n // batch)
+        lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + math.cos(math.pi * s / max(1, total - 1)))
+        la.append(float(a.step(x[b * batch:(b + 1) * batch], t[b * batch:(b + 1) * batch], lr).item()))
+    bt = rt.MlpTrainer(torch.from_numpy(synth.mlp_init(4)).cuda(), norm)
+    losses = torch.zeros(total, dtype=torch.float32, device="cuda")
+    bt.steps(x, t, batch, lr0, lr1, 1, 3, total, losses=losses[:3])
+    bt.steps(x, t, batch, lr0, lr1, 4, total - 3, total, losses=losses[3:])
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, bt.params)
+    assert torch.equal(a.m, bt.m) and torch.equal(a.v, bt.v)
+    # the loss is a diagnostic summed with atomics across tiles: equal up to that order
+    assert np.allclose(np.array(la, dtype=np.float32), losses.cpu().numpy(), rtol=1e-6, atol=0)
