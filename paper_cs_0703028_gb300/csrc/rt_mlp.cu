@@ -10,8 +10,8 @@
 //   k_mlp_bwd  : per 128-row tile, for each of layers 4..2 two tcgen05 products
 //                (dW = dZ^T H, dH = dZ W), SiLU derivative epilogues, bias and
 //                first-layer gradients, written to the tile's own FP32 partial.
-//   k_grad_reduce : the gradient, the tiles' partials summed in tile order.
-//   k_mlp_adam : Adam update of the FP32 masters (Kingma and Ba).
+//   k_grad_adam : the gradient, the tiles' partials summed in tile order, and
+//                the Adam update of the FP32 masters (Kingma and Ba).
 //   k_walk_mlp : the Monte-Carlo walk with the network in place of the table
 //                (three 128-ray tiles per block; every layer, biases included,
 //                on the tensor cores).
@@ -272,7 +272,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
   // this tile's gradient partial (every parameter written exactly once; summed over
-  // the tiles in a fixed order by k_grad_reduce)
+  // the tiles in a fixed order by k_grad_adam)
   float *G = Gpart + (long long)blockIdx.x * kGradStride;
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long row = (long long)blockIdx.x * kH + tid;
@@ -427,21 +427,17 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
   }
 }
 
-// gradient = sum of the tiles' partials, in tile order (deterministic)
-__global__ void k_grad_reduce(const float *__restrict__ part, int nparts, float *__restrict__ grad) {
+// gradient = sum of the tiles' partials, in tile order (deterministic), and
+// unless `adam` is 0 the Adam update of the FP32 masters with it (Kingma and Ba)
+__global__ void k_grad_adam(const float *__restrict__ part, int nparts, float *__restrict__ grad, int adam,
+                            float *__restrict__ P, float *__restrict__ m, float *__restrict__ v, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParam) return;
-  float s = 0.0f;
-  for (int t = 0; t < nparts; ++t) s += part[(long long)t * kGradStride + i];
-  grad[i] = s;
-}
-
-__global__ void k_mlp_adam(float *__restrict__ P, float *__restrict__ m, float *__restrict__ v,
-                           const float *__restrict__ g, float lr, float b1, float b2, float eps,
-                           float c1, float c2) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kNParam) return;
-  const float gi = g[i];
+  float gi = 0.0f;
+  for (int t = 0; t < nparts; ++t) gi += part[(long long)t * kGradStride + i];
+  grad[i] = gi;
+  if (!adam) return;
   const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
   const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
   m[i] = mi;
@@ -811,15 +807,21 @@ rt_status mlp_prep_tiles(const float *params, uint16_t *tiles, cudaStream_t st) 
   return RT_OK;
 }
 
-rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const float *inputs,
-                         const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
-                         int32_t flags, float *loss, uint32_t *status, cudaStream_t st) {
+// scratch of one training step of n samples: BF16 weight tiles, pre-activations,
+// output gradient, per-tile gradient partials
+size_t train_scratch_bytes(int64_t n) {
+  const size_t grid = (size_t)((n + kH - 1) / kH);
+  return 6 * (size_t)kTileBytes + (size_t)4 * (size_t)n * kH * sizeof(float) + (size_t)n * sizeof(float) +
+         grid * kGradStride * sizeof(float) + 64;
+}
+
+rt_status validate_train(float *params, float *m, float *v, float *grad, const float *inputs,
+                         const float *targets, int64_t n, const rt_mlp_norm *nm, int32_t flags,
+                         float *loss) {
   if (!params || !grad || !inputs || !targets || !loss)
     return fail(RT_E_INVAL, "rt_mlp_train_step: NULL buffer");
   if (!(flags & RT_MLP_GRAD_ONLY) && (!m || !v)) return fail(RT_E_INVAL, "rt_mlp_train_step: NULL Adam state");
   if (n < 1 || n > (1LL << 26)) return fail(RT_E_INVAL, "rt_mlp_train_step: n out of range");
-  if (!(flags & RT_MLP_GRAD_ONLY) && (step < 1 || !std::isfinite(lr) || lr < 0))
-    return fail(RT_E_INVAL, "rt_mlp_train_step: step >= 1 and finite lr >= 0 required");
   rt_status s = validate_norm(nm);
   if (s != RT_OK) return s;
   static std::once_flag once;
@@ -828,20 +830,21 @@ rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const f
     attr = set_smem((const void *)k_mlp_fwd<true>, sizeof(FwdSmem));
     if (attr == RT_OK) attr = set_smem((const void *)k_mlp_bwd, sizeof(BwdSmem));
   });
-  if (attr != RT_OK) return attr;
-  Scratch scr;
+  return attr;
+}
+
+// one step on validated arguments, scratch of train_scratch_bytes(n) bytes
+rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const float *inputs,
+                         const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
+                         int32_t flags, float *loss, uint32_t *status, char *scr, cudaStream_t st) {
   const unsigned grid = (unsigned)((n + kH - 1) / kH);
-  const size_t zbytes = (size_t)4 * (size_t)n * kH * sizeof(float);
-  const size_t pbytes = (size_t)grid * kGradStride * sizeof(float);
-  s = scr.alloc(6 * (size_t)kTileBytes + zbytes + (size_t)n * sizeof(float) + pbytes + 64, st);
-  if (s != RT_OK) return s;
-  uint16_t *tiles = scr.as<uint16_t>();
-  float *Z = reinterpret_cast<float *>(scr.as<char>() + 6 * (size_t)kTileBytes);
+  uint16_t *tiles = reinterpret_cast<uint16_t *>(scr);
+  float *Z = reinterpret_cast<float *>(scr + 6 * (size_t)kTileBytes);
   float *dy = Z + (size_t)4 * n * kH;
   float *gpart = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(dy + n) + 63) & ~uintptr_t(63));  // 64-byte aligned rows
   RT_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
-  s = mlp_prep_tiles(params, tiles, st);
+  rt_status s = mlp_prep_tiles(params, tiles, st);
   if (s != RT_OK) return s;
   const Norm N = to_norm(nm);
   k_mlp_fwd<true><<<grid, kH, sizeof(FwdSmem), st>>>(params, tiles, N, inputs, targets, n, Z, dy, loss,
@@ -849,15 +852,27 @@ rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const f
   RT_CUDA_TRY(cudaGetLastError());
   k_mlp_bwd<<<grid, kH, sizeof(BwdSmem), st>>>(params, tiles, N, inputs, n, Z, dy, gpart, status);
   RT_CUDA_TRY(cudaGetLastError());
-  k_grad_reduce<<<(kNParam + 255) / 256, 256, 0, st>>>(gpart, (int)grid, grad);
+  const bool adam = !(flags & RT_MLP_GRAD_ONLY);
+  const float c1 = adam ? (float)(1.0 - std::pow(0.9, step)) : 1.0f;
+  const float c2 = adam ? (float)(1.0 - std::pow(0.999, step)) : 1.0f;
+  k_grad_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(gpart, (int)grid, grad, adam ? 1 : 0, params, m, v, lr,
+                                                      0.9f, 0.999f, 1e-8f, c1, c2);
   RT_CUDA_TRY(cudaGetLastError());
-  if (!(flags & RT_MLP_GRAD_ONLY)) {
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = (float)(1.0 - std::pow(0.9, step)), c2 = (float)(1.0 - std::pow(0.999, step));
-    k_mlp_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(params, m, v, grad, lr, b1, b2, 1e-8f, c1, c2);
-    RT_CUDA_TRY(cudaGetLastError());
-  }
   return RT_OK;
+}
+
+rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const float *inputs,
+                         const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
+                         int32_t flags, float *loss, uint32_t *status, cudaStream_t st) {
+  rt_status s = validate_train(params, m, v, grad, inputs, targets, n, nm, flags, loss);
+  if (s != RT_OK) return s;
+  if (!(flags & RT_MLP_GRAD_ONLY) && (step < 1 || !std::isfinite(lr) || lr < 0))
+    return fail(RT_E_INVAL, "rt_mlp_train_step: step >= 1 and finite lr >= 0 required");
+  Scratch scr;
+  s = scr.alloc(train_scratch_bytes(n), st);
+  if (s != RT_OK) return s;
+  return mlp_train_core(params, m, v, grad, inputs, targets, n, nm, lr, step, flags, loss, status,
+                        scr.as<char>(), st);
 }
 
 rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, const float *inputs,
@@ -872,21 +887,23 @@ rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, c
                             "step_first - 1 + n_steps <= total_steps");
   if (!std::isfinite(lr0) || !std::isfinite(lr1) || lr0 < 0 || lr1 < 0)
     return fail(RT_E_INVAL, "rt_mlp_train_steps: finite learning rates >= 0 required");
-  float *loss1 = nullptr;
+  if (n_steps == 0) return RT_OK;
+  // one scratch for all steps: the step's buffers, then a loss slot if none is given
+  const size_t sb = (train_scratch_bytes(batch) + 255) & ~size_t(255);
   Scratch scr;
-  if (!losses) {
-    rt_status s = scr.alloc(sizeof(float), st);
-    if (s != RT_OK) return s;
-    loss1 = scr.as<float>();
-  }
+  rt_status r = scr.alloc(sb + 256, st);
+  if (r != RT_OK) return r;
+  float *loss1 = reinterpret_cast<float *>(scr.as<char>() + sb);
+  r = validate_train(params, m, v, grad, inputs, targets, batch, nm, 0, losses ? losses : loss1);
+  if (r != RT_OK) return r;
   const int64_t nb = n / batch;
   const double span = (double)std::max(1, total_steps - 1);
   for (int32_t i = 0; i < n_steps; ++i) {
     const int64_t s = (int64_t)step_first - 1 + i;
     const int64_t b = s % nb;
     const double lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + std::cos(kPiD * (double)s / span));
-    rt_status r = mlp_train_impl(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, nm,
-                                 (float)lr, (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, st);
+    r = mlp_train_core(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, nm, (float)lr,
+                       (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, scr.as<char>(), st);
     if (r != RT_OK) return r;
   }
   return RT_OK;
