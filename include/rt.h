@@ -287,7 +287,7 @@ rt_status rt_trace_batch(int32_t n_encl, const rt_enclosure *encl, const float *
  * walk_blocks_per_sm = resident 256-thread blocks per SM the rt_trace walk is
  *   compiled for (4: 64 registers per thread, 5: 48; 0 = 5);
  * walk_refill_idle = idle lanes of a warp that trigger loading new rays in the
- *   rt_trace walk (8 or 16; 0 = 16).
+ *   rt_trace walk (12 or 16; 0 = 16).
  */
 typedef struct {
   int32_t kappa_t_per_block;

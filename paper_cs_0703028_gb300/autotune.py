@@ -7,7 +7,7 @@ choice in a JSON file keyed by a signature of the workload's sizes
 
 * ``tune_kappa``: temperature nodes per rt_build_kappa block (1, 2, 4, 8).
 * ``tune_batch``: rays per work item and threads per block of the batched walk.
-* ``tune_walk``: resident blocks per SM (4 or 5) and refill threshold (8 or 16) of the rt_trace walk.
+* ``tune_walk``: resident blocks per SM (4 or 5) and refill threshold (12 or 16) of the rt_trace walk.
 """
 from __future__ import annotations
 
@@ -103,12 +103,13 @@ def tune_walk(grid_struct, ncells, spec, kappa, n_rays, candidates=None, reps=2,
     """Pick the walk's (resident blocks per SM, refill threshold) on the caller's trace;
     returns ((blocks, refill), {"blocks,refill": ms})."""
     if candidates is None:
-        candidates = [(b, r) for b in (4, 5) for r in (8, 16)]
+        candidates = [(b, r) for b in (4, 5) for r in (12, 16)]
     key = f"walk:{ncells}:{spec.n_nu}:{spec.nT}:{int(n_rays)}"
-    if use_cache and key in _load():
-        b, r = (int(v) for v in _load()[key]["best"])
+    cached = _load().get(key) if use_cache else None
+    if cached and tuple(int(v) for v in cached["best"]) in [tuple(c) for c in candidates]:
+        b, r = (int(v) for v in cached["best"])   # a cached shape that is still a candidate
         set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
-        return (b, r), _load()[key]["ms"]
+        return (b, r), cached["ms"]
     tally = Tally(ncells)
     times = {}
     for b, r in candidates:

@@ -1015,8 +1015,8 @@ extern "C" rt_status rt_set_tuning(const rt_tuning *t) {
     return rt::fail(RT_E_INVAL, "rt_set_tuning: kappa_t_per_block must be in [0, 8]");
   if (t->walk_blocks_per_sm != 0 && t->walk_blocks_per_sm != 4 && t->walk_blocks_per_sm != 5)
     return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_blocks_per_sm must be 0, 4 or 5");
-  if (t->walk_refill_idle != 0 && t->walk_refill_idle != 8 && t->walk_refill_idle != 16)
-    return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_refill_idle must be 0, 8 or 16");
+  if (t->walk_refill_idle != 0 && t->walk_refill_idle != 12 && t->walk_refill_idle != 16)
+    return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_refill_idle must be 0, 12 or 16");
   rt::g_kappa_tpb = t->kappa_t_per_block == 0 ? 8 : t->kappa_t_per_block;
   rt::g_walk_blocks = t->walk_blocks_per_sm == 0 ? 5 : t->walk_blocks_per_sm;
   rt::g_walk_refill = t->walk_refill_idle == 0 ? 16 : t->walk_refill_idle;

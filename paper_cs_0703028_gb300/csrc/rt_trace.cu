@@ -42,7 +42,7 @@ constexpr int kWalkUnroll = 8;  // steps per pass of the walk loop
 }  // namespace
 
 int g_walk_blocks = 5;   // resident walk blocks per SM the launch is compiled for (4 or 5)
-int g_walk_refill = 16;  // idle lanes that trigger a refill (8 or 16)
+int g_walk_refill = 16;  // idle lanes that trigger a refill (12 or 16)
 
 namespace {
 
@@ -340,8 +340,8 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   auto pick = [&](auto tab) {
     constexpr int L = decltype(tab)::value;
     if (rec) return k_walk<true, L, 5, kRefillIdleDefault>;
-    if (g_walk_blocks == 4) return g_walk_refill == 8 ? k_walk<false, L, 4, 8> : k_walk<false, L, 4, 16>;
-    return g_walk_refill == 8 ? k_walk<false, L, 5, 8> : k_walk<false, L, 5, 16>;
+    if (g_walk_blocks == 4) return g_walk_refill == 12 ? k_walk<false, L, 4, 12> : k_walk<false, L, 4, 16>;
+    return g_walk_refill == 12 ? k_walk<false, L, 5, 12> : k_walk<false, L, 5, 16>;
   };
   auto kern = layout == 2 ? pick(std::integral_constant<int, 2>()) : pick(std::integral_constant<int, 1>());
   int per_sm = 0;

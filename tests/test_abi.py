@@ -109,11 +109,11 @@ def test_tuning_round_trip_and_validation():
     # launch shapes only; the calls touch no device
     before = rt.get_tuning()
     try:
-        rt.set_tuning(kappa_t_per_block=4, walk_blocks_per_sm=4, walk_refill_idle=8)
-        assert rt.get_tuning() == {"kappa_t_per_block": 4, "walk_blocks_per_sm": 4, "walk_refill_idle": 8}
+        rt.set_tuning(kappa_t_per_block=4, walk_blocks_per_sm=4, walk_refill_idle=12)
+        assert rt.get_tuning() == {"kappa_t_per_block": 4, "walk_blocks_per_sm": 4, "walk_refill_idle": 12}
         rt.set_tuning(walk_refill_idle=16)  # other fields keep their value
         assert rt.get_tuning()["walk_blocks_per_sm"] == 4
-        for bad in ({"kappa_t_per_block": 9}, {"walk_blocks_per_sm": 3}, {"walk_refill_idle": 12}):
+        for bad in ({"kappa_t_per_block": 9}, {"walk_blocks_per_sm": 3}, {"walk_refill_idle": 8}):
             with pytest.raises(rt.RtError):
                 rt.set_tuning(**bad)
         with pytest.raises(TypeError):
