@@ -276,23 +276,24 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
   if (inside) pf(cnext);
 
   const float ds = __fsub_rn(tn, R.t);
-  const float a = kap > 0.0f ? __fmul_rn(__fmul_rn(kap, 100.0f), ds) : 0.0f;
+  // the segment's optical depth; an unbounded segment (a ray that never reaches a
+  // wall, ds = inf) is held at 1e30, which leaves a transmission of exactly 0 and
+  // a deposit of w trans0, as an infinite depth would, without infinities in the sum
+  const float a = kap > 0.0f ? fminf(__fmul_rn(__fmul_rn(kap, 100.0f), ds), 1e30f) : 0.0f;
   const float trans0 = R.trans;
   // compensated optical depth
   {
     const float y = __fsub_rn(a, R.tc);
     const float sum = __fadd_rn(R.tau, y);
-    const float tcn = __fsub_rn(__fsub_rn(sum, R.tau), y);
-    const bool opaque = a == INFINITY;
-    R.tau = opaque ? INFINITY : sum;
-    R.tc = opaque ? R.tc : tcn;
+    R.tc = __fsub_rn(__fsub_rn(sum, R.tau), y);
+    R.tau = sum;
   }
   // deposit and transmission exp(-tau); once the transmission has underflowed to
   // zero it stays zero (tau only grows), so a dark ray skips both exponentials
   if (trans0 != 0.0f) {
     const float dep = R.w * trans0 * one_minus_exp_neg(a);
     if (writes && dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
-    R.trans = a == INFINITY ? 0.0f : __expf(__fsub_rn(R.tc, R.tau));
+    R.trans = __expf(__fsub_rn(R.tc, R.tau));
   }
   if (REC && writes && R.row >= 0 && R.nv < W.rec_max) {
     rec.cells[(long long)R.row * W.rec_max + R.nv] = R.cell;
