@@ -271,7 +271,7 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
     stride = a0 ? 1 : (a1 ? W.n[0] : W.n[0] * W.n[1]);
     h = a0 ? W.h[0] : (a1 ? W.h[1] : W.h[2]);
   }
-  const bool inside = tn != INFINITY && inew >= 0 && inew < nax;
+  const bool inside = tn != INFINITY && (unsigned)inew < (unsigned)nax;  // 0 <= inew < nax
   const int cnext = R.cell + st * stride;
   if (inside) pf(cnext);
 
