@@ -1,11 +1,10 @@
 """GB300 (sm_103a) Monte-Carlo line-by-line radiative transfer.
 
-Thin Python binding of the C ABI declared in ``include/rt.h``: the functions
-``rt_build_kappa``, ``rt_trace``, ``rt_tally``, ``rt_tally_zero``,
-``rt_status_read``, ``rt_last_error``, ``rt_version`` and
-``rt_kappa_table_elems`` are the library's own entry points (ctypes), and the
-helpers below only marshal arguments: every step of the computation runs in
-the library's CUDA kernels.  PyTorch supplies device memory and streams.
+Thin Python binding of the C ABI declared in ``include/rt.h`` (ctypes, the
+same names: the kappa build, the walks, tallies, the surrogate network, the
+batched walk, the spectral marching, launch shapes); the helpers below only
+marshal arguments: every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.
 
 The method follows Section 3 of Collange, Daumas and Defour, "Graphic
 processors to speed-up simulations for the design of high performance solar

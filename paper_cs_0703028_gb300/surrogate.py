@@ -1,9 +1,9 @@
 """Surrogate-network pipeline: line-by-line training tables, samples, training.
 
 Every numeric step runs in the library's kernels (rt_build_kappa for the
-tables, rt_mlp_make_samples for the samples, rt_mlp_train_step for forward,
-backward and Adam); this module only orders the calls and picks the learning
-rate of each step (cosine decay).
+tables, rt_mlp_make_samples for the samples, rt_mlp_train_steps for the
+forward and backward passes and Adam over all steps with a cosine learning
+rate); this module only orders the calls.
 """
 from __future__ import annotations
 
