@@ -196,3 +196,25 @@ def test_odd_line_count(rt, profile, memory):
     nz = ref > 0
     assert np.array_equal(got > 0, nz)
     assert _rel(got[nz], ref[nz]).max() <= TOL
+
+
+def test_fixed_points_per_line_accumulates(rt):
+    # two gases with 16 points per line, the second accumulated into the first's table
+    import torch
+    from dataclasses import replace
+    rng = synth.rng_for(9, 84)
+    co2 = synth.make_lines(800, 1995.0, 2105.0, rng)
+    h2o = replace(synth.make_lines(500, 1995.0, 2105.0, rng, S_lo=1e-23, S_hi=1e-20), mass_amu=18.0,
+                  n_T=0.6, q_exp=1.5)
+    s1 = synth.Spectral(nu_min=2000.0, dnu=0.01, n_nu=10000, cutoff=25.0, profile="voigt", nT=3,
+                        T_min=800.0, T_max=1600.0, points_per_line=16)
+    s2 = replace(s1, x_ref=0.05, accumulate=1)
+    out = torch.empty((s1.nT, s1.n_nu), dtype=torch.float32, device="cuda")
+    rt.build_kappa(co2, s1, out=out)
+    rt.build_kappa(h2o, s2, out=out)
+    torch.cuda.synchronize()
+    ref = okappa.kappa_table(co2, s1) + okappa.kappa_table(h2o, replace(s2, accumulate=0))
+    got = out.cpu().numpy().astype(np.float64)
+    nz = ref > 0
+    assert np.array_equal(got > 0, nz)
+    assert _rel(got[nz], ref[nz]).max() <= TOL

@@ -67,6 +67,18 @@ def test_static_scratch_matches_allocating_build_twice(rt):
         _close(got, ref)
 
 
+@pytest.mark.parametrize("profile", ["lorentz", "voigt"])
+def test_static_scratch_fixed_points_per_line(rt, profile):
+    # the fixed-points gather kernel through the allocation-free entry point (odd line count)
+    rng = synth.rng_for(9, 33)
+    lines = synth.make_lines(901, 1995.0, 2105.0, rng)
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.01, n_nu=10001, cutoff=25.0, profile=profile, nT=3,
+                          T_min=800.0, T_max=1600.0, points_per_line=16)
+    ref, got, ev_ref, ev_got = _both(rt, lines, spec)
+    assert ev_got == ev_ref
+    _close(got, ref)
+
+
 def test_static_scratch_rejects_oversized_input(rt):
     L = rt.lib()
     rng = synth.rng_for(9, 32)
