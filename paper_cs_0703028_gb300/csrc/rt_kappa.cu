@@ -122,25 +122,41 @@ __global__ void k_line_geometry(const double *__restrict__ nu0, const double *__
 // t <= 1/x^2), so a degree-2 series is within one binary32 rounding of the full
 // one; beyond far[1] (>= far[0]) also (3.75 + 2 y^2) t^2 <= 2^-25, so the degree-1
 // series drops at most 1.25 * 2^-24 of the value.
-__device__ __forceinline__ void prefactor_one(const double *__restrict__ nu0, const double *__restrict__ S,
-                                                  const double *__restrict__ g, const double *__restrict__ E,
-                                                  const PrefParams &Q, float4 *__restrict__ Pout,
-                                                  float4 *__restrict__ P2out, long long l, int k,
-                                                  unsigned (&far)[2]) {
+// The quantities of T node k that every line shares.
+struct PrefNode {
+  df Tk, iT, iTref;
+  float tr, qratio, wratio, sqrtT;
+};
+
+__device__ __forceinline__ PrefNode pref_node(const PrefParams &Q, int k) {
   // T_k = T_min + k (T_max - T_min) / (nT - 1) and 1/T_k in double-float
+  PrefNode N;
   df Tk = df_from_double(Q.T_min);
   if (Q.nT > 1) {
     const df span = df_add(df_from_double(Q.T_max), df_neg(Tk));
     const df step = df_mul(span, df_recip(df{(float)(Q.nT - 1), 0.0f}));
     Tk = df_add(Tk, df_mul(step, df{(float)k, 0.0f}));
   }
-  const df iT = df_recip(Tk);
+  N.Tk = Tk;
+  N.iT = df_recip(Tk);
   const df Tref = df_from_double(Q.T_ref);
-  const df iTref = df_recip(Tref);
+  N.iTref = df_recip(Tref);
+  N.tr = Tref.hi * N.iT.hi;  // T_ref / T
+  N.qratio = powf(N.tr, Q.q_exp);
+  N.wratio = powf(N.tr, Q.n_T);
+  N.sqrtT = sqrtf(Tk.hi);
+  return N;
+}
+
+__device__ __forceinline__ void prefactor_one(const double *__restrict__ nu0, const double *__restrict__ S,
+                                                  const double *__restrict__ g, const double *__restrict__ E,
+                                                  const PrefParams &Q, const PrefNode &N,
+                                                  float4 *__restrict__ Pout, float4 *__restrict__ P2out,
+                                                  long long l, int k, unsigned (&far)[2]) {
+  const df iT = N.iT, iTref = N.iTref;
   const float iTf = iT.hi;
-  const float tr = Tref.hi * iTf;  // T_ref / T
   // Eq. (S): Q ratio, Boltzmann ratio (exponent in double-float), stimulated emission
-  const float qratio = powf(tr, Q.q_exp);
+  const float qratio = N.qratio;
   const df arg = df_mul(df_mul(Q.c2, df_from_double(E[l])), df_add(iTref, df_neg(iT)));
   const float boltz = expf(arg.hi) * (1.0f + arg.lo);
   const float nu0f = __double2float_rn(nu0[l]);
@@ -148,14 +164,14 @@ __device__ __forceinline__ void prefactor_one(const double *__restrict__ nu0, co
   const float stim = expm1f(-c2nu * iTf) / expm1f(-c2nu * iTref.hi);
   const float S_T = __double2float_rn(S[l]) * qratio * boltz * stim;
   const float A = (Q.u_coef * iTf) * S_T;  // u(T) S(T), cm^-1 per unit profile
-  const float gam = __double2float_rn(g[l]) * Q.p_ref * powf(tr, Q.n_T);
+  const float gam = __double2float_rn(g[l]) * Q.p_ref * N.wratio;
   float4 out;
   far[0] = far[1] = 0;
   if (Q.profile == RT_PROFILE_LORENTZ) {
     const float gg = gam * Q.inv_dnu;  // half-width in grid units
     out = make_float4(A * gg * (float)(1.0 / kPi) * Q.inv_dnu, gg * gg, 0.0f, 0.0f);
   } else {
-    const float alpha = nu0f * sqrtf(Tk.hi) * Q.doppler;  // Doppler HWHM, cm^-1
+    const float alpha = nu0f * N.sqrtT * Q.doppler;  // Doppler HWHM, cm^-1
     const float s = 0.83255461f / alpha;                  // sqrt(ln 2) / alpha
     const float y = s * gam;
     const float sd = s * Q.dnu;
@@ -184,8 +200,12 @@ __global__ void k_prefactor(const double *__restrict__ nu0, const double *__rest
                             unsigned *__restrict__ far_bits) {
   const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
+  __shared__ PrefNode s_node;  // T node k's shared quantities, formed once per block
+  if (threadIdx.x == 0) s_node = pref_node(Q, k);
+  __syncthreads();
+  const PrefNode N = s_node;
   unsigned fb[2] = {0, 0};  // this line's far-zone distances (grid units, float bits)
-  if (l < Q.n_lines) prefactor_one(nu0, S, g, E, Q, Pout, P2out, l, k, fb);
+  if (l < Q.n_lines) prefactor_one(nu0, S, g, E, Q, N, Pout, P2out, l, k, fb);
   // block maxima, one atomic each per block (non-negative floats order like their bits)
   __shared__ unsigned s_max[2][32];
   for (int d = 0; d < 2; ++d) {
@@ -243,15 +263,6 @@ __device__ __forceinline__ long long lower_bound_lo(const int4 *R, long long n, 
   return a;
 }
 
-__device__ __forceinline__ long long lower_bound_c(const int4 *R, long long n, long long j) {
-  long long a = 0, b = n;  // first l with R[l].z >= j
-  while (a < b) {
-    long long m = (a + b) >> 1;
-    if (R[m].z < j) a = m + 1; else b = m;
-  }
-  return a;
-}
-
 // Kinds of line ranges within a tile (see k_tile_lines).
 enum SegKind : int {
   kSegGeneral = 0,   // window masking and near-centre test per line
@@ -277,23 +288,43 @@ constexpr int kTileInts = 5;  // int4 per tile: {lb, ub, nseg, 0}, 12 ends, 16 k
 __global__ void k_tile_lines(const int4 *__restrict__ R, long long n, long long n_nu, int W,
                              const unsigned *__restrict__ far_bits, long long n_tiles,
                              int4 *__restrict__ out) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_tiles) return;
+  // one warp per tile: lanes 0..9 run the tile's ten binary searches side by side
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n_tiles) return;  // warp-uniform
   const long long D2 = max((long long)W + 4, (long long)ceilf(fminf(__uint_as_float(far_bits[0]), 1e9f)) + 2);
   const long long D1 = max(D2, (long long)ceilf(fminf(__uint_as_float(far_bits[1]), 1e9f)) + 2);
   const long long jw0 = t * kTilePts, jw1 = jw0 + kTilePts - 1;
   const long long jend = min(jw0 + (long long)kTilePts, n_nu);
-  const long long lb = lower_bound_hi(R, n, (int)jw0);
-  const long long ub = max(lb, lower_bound_lo(R, n, (int)jend));
+  // search i: the first line whose field (0: window start, 1: window end, 2: centre) >= key
+  const int fld = (lane == 1 || lane == 3) ? 0 : ((lane == 0 || lane == 2) ? 1 : 2);
+  const long long key = lane == 0 ? jw0 : lane == 1 ? jend : lane == 2 ? jw1 : lane == 3 ? jw0 + 1
+                        : lane == 4 ? jw0 - D1 : lane == 5 ? jw0 - D2 : lane == 6 ? jw0 - W - 4
+                        : lane == 7 ? jw1 + W + 5 : lane == 8 ? jw1 + D2 + 1 : jw1 + D1 + 1;
+  long long a = 0, e = n;
+  if (lane < 10) {
+    while (a < e) {
+      const long long m = (a + e) >> 1;
+      const int4 r = __ldg(R + m);
+      const long long v = fld == 0 ? r.x : (fld == 1 ? r.y : r.z);
+      if (v < key) a = m + 1; else e = m;
+    }
+  }
+  long long sr[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) sr[i] = __shfl_sync(0xffffffffu, a, i);
+  if (lane != 0) return;
+  const long long lb = sr[0];
+  const long long ub = max(lb, sr[1]);
   auto cl = [&](long long v) { return min(max(v, lb), ub); };
-  const long long ca = cl(lower_bound_hi(R, n, (int)jw1));       // cover = [ca, cb)
-  const long long cb = cl(lower_bound_lo(R, n, (int)(jw0 + 1)));
-  const long long f1a = cl(lower_bound_c(R, n, jw0 - D1));        // far1: l < f1a or l >= f1b
-  const long long f2a = cl(lower_bound_c(R, n, jw0 - D2));        // far2: l < f2a or l >= f2b
-  const long long na = cl(lower_bound_c(R, n, jw0 - W - 4));      // near: [na, nb)
-  const long long nb = cl(lower_bound_c(R, n, jw1 + W + 5));
-  const long long f2b = cl(lower_bound_c(R, n, jw1 + D2 + 1));
-  const long long f1b = cl(lower_bound_c(R, n, jw1 + D1 + 1));
+  const long long ca = cl(sr[2]);   // cover = [ca, cb)
+  const long long cb = cl(sr[3]);
+  const long long f1a = cl(sr[4]);  // far1: l < f1a or l >= f1b
+  const long long f2a = cl(sr[5]);  // far2: l < f2a or l >= f2b
+  const long long na = cl(sr[6]);   // near: [na, nb)
+  const long long nb = cl(sr[7]);
+  const long long f2b = cl(sr[8]);
+  const long long f1b = cl(sr[9]);
   auto kind = [&](long long l) -> int {
     const bool far1 = l < f1a || l >= f1b, far2 = l < f2a || l >= f2b;
     if (l < ca || l >= cb) return far1 ? kSegFar1Masked : (far2 ? kSegFar2Masked : kSegGeneral);
@@ -751,8 +782,8 @@ rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *t
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
   }
-  k_tile_lines<<<(unsigned)((n_tiles + 127) / 128), 128, 0, st>>>(R, n, spec->n_nu, W, far_bits,
-                                                                    n_tiles, tiles);
+  k_tile_lines<<<(unsigned)((n_tiles + 3) / 4), 128, 0, st>>>(R, n, spec->n_nu, W, far_bits, n_tiles,
+                                                                tiles);  // a warp per tile
   RT_CUDA_TRY(cudaGetLastError());
   const int vec_ok = ((reinterpret_cast<uintptr_t>(kappa) & 15u) == 0 && spec->n_nu % 4 == 0) ? 1 : 0;
   int want = g_kappa_tpb;
