@@ -428,10 +428,12 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
 }
 
 // gradient = sum of the tiles' partials, in tile order (deterministic), and
-// unless `adam` is 0 the Adam update of the FP32 masters with it (Kingma and Ba)
+// unless `adam` is 0 the Adam update of the FP32 masters with it (Kingma and Ba);
+// with `tiles` given, an updated weight of W2..W4 is also written to its two BF16
+// tile positions (the layout k_mlp_prep writes), ready for the next step
 __global__ void k_grad_adam(const float *__restrict__ part, int nparts, float *__restrict__ grad, int adam,
                             float *__restrict__ P, float *__restrict__ m, float *__restrict__ v, float lr,
-                            float b1, float b2, float eps, float c1, float c2) {
+                            float b1, float b2, float eps, float c1, float c2, uint16_t *__restrict__ tiles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParam) return;
   float gi = 0.0f;
@@ -442,7 +444,20 @@ __global__ void k_grad_adam(const float *__restrict__ part, int nparts, float *_
   const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
   m[i] = mi;
   v[i] = vi;
-  P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  const float pi = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  P[i] = pi;
+  if (tiles) {
+    const int mat = (i >= oW2 && i < oW2 + kTileElems) ? 0
+                    : (i >= oW3 && i < oW3 + kTileElems) ? 1
+                    : (i >= oW4 && i < oW4 + kTileElems) ? 2 : -1;
+    if (mat >= 0) {
+      const int e = i - (mat == 0 ? oW2 : (mat == 1 ? oW3 : oW4));
+      const int r = e / kH, k = e % kH;  // row (output unit), column (input unit)
+      const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(pi));
+      tiles[mat * kTileElems + tile_index(r, k)] = h;
+      tiles[(mat + 3) * kTileElems + tile_index(k, r)] = h;
+    }
+  }
 }
 
 // Self-test of the tensor-core path: D = A B^T for 128 x 128 x 128, A and B
@@ -833,19 +848,24 @@ rt_status validate_train(float *params, float *m, float *v, float *grad, const f
   return attr;
 }
 
-// one step on validated arguments, scratch of train_scratch_bytes(n) bytes
+// one step on validated arguments, scratch of train_scratch_bytes(n) bytes; `chained`:
+// the scratch's BF16 tiles already hold the parameters and the loss slot is zero (a
+// run of steps), and the Adam kernel refreshes the tiles for the next step
 rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const float *inputs,
                          const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
-                         int32_t flags, float *loss, uint32_t *status, char *scr, cudaStream_t st) {
+                         int32_t flags, float *loss, uint32_t *status, char *scr, bool chained,
+                         cudaStream_t st) {
   const unsigned grid = (unsigned)((n + kH - 1) / kH);
   uint16_t *tiles = reinterpret_cast<uint16_t *>(scr);
   float *Z = reinterpret_cast<float *>(scr + 6 * (size_t)kTileBytes);
   float *dy = Z + (size_t)4 * n * kH;
   float *gpart = reinterpret_cast<float *>(
       (reinterpret_cast<uintptr_t>(dy + n) + 63) & ~uintptr_t(63));  // 64-byte aligned rows
-  RT_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
-  rt_status s = mlp_prep_tiles(params, tiles, st);
-  if (s != RT_OK) return s;
+  if (!chained) {
+    RT_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    rt_status s = mlp_prep_tiles(params, tiles, st);
+    if (s != RT_OK) return s;
+  }
   const Norm N = to_norm(nm);
   k_mlp_fwd<true><<<grid, kH, sizeof(FwdSmem), st>>>(params, tiles, N, inputs, targets, n, Z, dy, loss,
                                                      nullptr, status);
@@ -856,7 +876,7 @@ rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const f
   const float c1 = adam ? (float)(1.0 - std::pow(0.9, step)) : 1.0f;
   const float c2 = adam ? (float)(1.0 - std::pow(0.999, step)) : 1.0f;
   k_grad_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(gpart, (int)grid, grad, adam ? 1 : 0, params, m, v, lr,
-                                                      0.9f, 0.999f, 1e-8f, c1, c2);
+                                                      0.9f, 0.999f, 1e-8f, c1, c2, chained ? tiles : nullptr);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -872,7 +892,7 @@ rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const f
   s = scr.alloc(train_scratch_bytes(n), st);
   if (s != RT_OK) return s;
   return mlp_train_core(params, m, v, grad, inputs, targets, n, nm, lr, step, flags, loss, status,
-                        scr.as<char>(), st);
+                        scr.as<char>(), false, st);
 }
 
 rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, const float *inputs,
@@ -896,14 +916,20 @@ rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, c
   float *loss1 = reinterpret_cast<float *>(scr.as<char>() + sb);
   r = validate_train(params, m, v, grad, inputs, targets, batch, nm, 0, losses ? losses : loss1);
   if (r != RT_OK) return r;
+  // the steps after the first take their BF16 tiles from the previous step's Adam
+  // kernel, and a given loss buffer is zeroed once for all steps
+  if (losses) RT_CUDA_TRY(cudaMemsetAsync(losses, 0, (size_t)n_steps * sizeof(float), st));
+  r = mlp_prep_tiles(params, scr.as<uint16_t>(), st);
+  if (r != RT_OK) return r;
   const int64_t nb = n / batch;
   const double span = (double)std::max(1, total_steps - 1);
   for (int32_t i = 0; i < n_steps; ++i) {
     const int64_t s = (int64_t)step_first - 1 + i;
     const int64_t b = s % nb;
     const double lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + std::cos(kPiD * (double)s / span));
+    if (!losses) RT_CUDA_TRY(cudaMemsetAsync(loss1, 0, sizeof(float), st));
     r = mlp_train_core(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, nm, (float)lr,
-                       (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, scr.as<char>(), st);
+                       (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, scr.as<char>(), true, st);
     if (r != RT_OK) return r;
   }
   return RT_OK;

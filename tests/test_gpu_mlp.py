@@ -149,3 +149,8 @@ def test_multi_step_training_equals_single_steps(rt):
     assert torch.equal(a.m, bt.m) and torch.equal(a.v, bt.v)
     # the loss is a diagnostic summed with atomics across tiles: equal up to that order
     assert np.allclose(np.array(la, dtype=np.float32), losses.cpu().numpy(), rtol=1e-6, atol=0)
+    # all steps in one call, without a loss buffer (the library's own loss slot)
+    c = rt.MlpTrainer(torch.from_numpy(synth.mlp_init(4)).cuda(), norm)
+    c.steps(x, t, batch, lr0, lr1, 1, total, total)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, c.params)
