@@ -11,7 +11,8 @@
 //                (dW = dZ^T H, dH = dZ W), SiLU derivative epilogues, bias and
 //                first-layer gradients, written to the tile's own FP32 partial.
 //   k_grad_adam : the gradient, the tiles' partials summed in tile order, and
-//                the Adam update of the FP32 masters (Kingma and Ba).
+//                the Adam update of the FP32 masters (Kingma and Ba); within a
+//                run of steps also the next step's BF16 tiles.
 //   k_walk_mlp : the Monte-Carlo walk with the network in place of the table
 //                (three 128-ray tiles per block; every layer, biases included,
 //                on the tensor cores).
