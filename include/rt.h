@@ -313,7 +313,8 @@ rt_status rt_get_tuning(rt_tuning *t);
  *   nvis    optional device [n_paths] (overwritten): the number of cells each path
  *           crosses (each crossing is n_nu updates of Eq. I).
  *   status  optional device status word (RT_DEV_NONFINITE, RT_DEV_STEPCAP).
- * n_paths <= 65535 per call.  Asynchronous.
+ * 0 <= n_paths <= 65535 per call; with n_paths = 0 nothing is read or written and the
+ * buffers may be NULL.  Asynchronous.
  */
 rt_status rt_march(const rt_grid *grid, const float *kappa, const rt_spectral *spec,
                    int64_t n_paths, const float *pos, const float *dir, const float *I_in,
@@ -353,7 +354,8 @@ typedef struct {
   float out_mean, out_scale; /* log kappa = out_mean + out_scale * y */
 } rt_mlp_norm;
 
-/* log kappa for n raw inputs (device [n][4]) into out (device [n]).  Asynchronous. */
+/* log kappa for n raw inputs (device [n][4]) into out (device [n]); n = 0 reads and
+ * writes nothing (the buffers may then be NULL).  Asynchronous. */
 rt_status rt_mlp_forward(const float *params, const rt_mlp_norm *norm, const float *inputs,
                          int64_t n, float *out, uint32_t *status, void *stream);
 

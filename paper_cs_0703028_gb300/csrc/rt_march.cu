@@ -226,9 +226,9 @@ rt_status march_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   if (v != RT_OK) return v;
   if (!grid || !grid->T || grid->nx < 1 || grid->ny < 1 || grid->nz < 1)
     return fail(RT_E_INVAL, "rt_march: bad grid");
-  if (!kappa || !pos || !dir || !power) return fail(RT_E_INVAL, "rt_march: NULL buffer");
   if (n_paths < 0 || n_paths > 65535) return fail(RT_E_INVAL, "rt_march: n_paths must be in [0, 65535]");
-  if (n_paths == 0) return RT_OK;
+  if (n_paths == 0) return RT_OK;  // no path: the buffers are not read and may be NULL
+  if (!kappa || !pos || !dir || !power) return fail(RT_E_INVAL, "rt_march: NULL buffer");
   MarchParams M;
   const double h[3] = {grid->hx, grid->hy, grid->hz};
   const int n[3] = {grid->nx, grid->ny, grid->nz};

@@ -938,9 +938,9 @@ rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, c
 
 rt_status mlp_forward_impl(const float *params, const rt_mlp_norm *nm, const float *inputs, int64_t n,
                            float *out, uint32_t *status, cudaStream_t st) {
-  if (!params || !inputs || !out) return fail(RT_E_INVAL, "rt_mlp_forward: NULL buffer");
   if (n < 0) return fail(RT_E_INVAL, "rt_mlp_forward: n < 0");
-  if (n == 0) return RT_OK;
+  if (n == 0) return RT_OK;  // no sample: the buffers are not read and may be NULL
+  if (!params || !inputs || !out) return fail(RT_E_INVAL, "rt_mlp_forward: NULL buffer");
   rt_status s = validate_norm(nm);
   if (s != RT_OK) return s;
   static std::once_flag once;
