@@ -121,7 +121,7 @@ __device__ __forceinline__ float2 expm1_pos2(float2 x) {
 constexpr int kMarchPts = 4;
 
 template <int VEC>
-__global__ void __launch_bounds__(kMarchThreads)
+__global__ void __launch_bounds__(kMarchThreads, 6)
 k_march(const float4 *__restrict__ cells, const float *__restrict__ tab, MarchParams M,
         const int *__restrict__ vis_cell, const float *__restrict__ vis_len, const int *__restrict__ nvis,
         const float *__restrict__ I_in, float *__restrict__ I_out, double *__restrict__ power) {
@@ -183,13 +183,32 @@ k_march(const float4 *__restrict__ cells, const float *__restrict__ tab, MarchPa
             }
           }
         }
+        float2 a[2], xe[2], att[2], em1[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float2 a = __ffma2_rn(dup2(c.y), t1[h], __fmul2_rn(dup2(c.x), t0[h]));  // optical depth
-          const float2 att = one_minus_exp_neg2(a);                                      // 1 - exp(-kappa l)
-          const float2 em1 = expm1_pos2(__fmul2_rn(c2nu[h], dup2(c.z)));
-          const float2 ib = make_float2(__fdividef(pre[h].x, em1.x), __fdividef(pre[h].y, em1.y));  // Eq. (planck)
-          I[h] = __ffma2_rn(att, __fadd2_rn(ib, neg2(I[h])), I[h]);
+          a[h] = __ffma2_rn(dup2(c.y), t1[h], __fmul2_rn(dup2(c.x), t0[h]));  // optical depth
+          xe[h] = __fmul2_rn(c2nu[h], dup2(c.z));                            // c2 nu / T
+        }
+        // 1 - exp(-a) and exp(x) - 1: the series runs only when one of the thread's
+        // arguments is below 1/4 (each point takes the same form as in the helpers)
+        if (fminf(fminf(a[0].x, a[0].y), fminf(a[1].x, a[1].y)) >= 0.25f) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) att[h] = make_float2(1.0f - __expf(-a[h].x), 1.0f - __expf(-a[h].y));
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) att[h] = one_minus_exp_neg2(a[h]);
+        }
+        if (xe[0].x >= 0.25f) {  // the thread's lowest wavenumber has the lowest argument
+#pragma unroll
+          for (int h = 0; h < 2; ++h) em1[h] = make_float2(__expf(xe[h].x) - 1.0f, __expf(xe[h].y) - 1.0f);
+        } else {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) em1[h] = expm1_pos2(xe[h]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 ib = make_float2(__fdividef(pre[h].x, em1[h].x), __fdividef(pre[h].y, em1[h].y));  // Eq. (planck)
+          I[h] = __ffma2_rn(att[h], __fadd2_rn(ib, neg2(I[h])), I[h]);
         }
       }
     }
