@@ -19,7 +19,7 @@
 //                     lane owns 8 consecutive points (two float4 stores) and
 //                     Kahan-sums over lines in ascending nu0.
 //   k_kappa_ppl     : with a fixed number of points per line, one thread per
-//                     (point, T node) over the few lines whose windows hold it.
+//                     point and eight T nodes over the few lines whose windows hold it.
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -697,59 +697,63 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
 }
 
 // Fixed points per line (each line on the few grid points around its centre):
-// one thread per (point j, T node); the lines whose windows hold j are a
-// contiguous index range (windows are monotone in the sorted line index), found
-// by binary search within the block's range, and summed in ascending nu0 with
-// compensation.  Every point is near its lines' centres, so each value is the
-// near-centre form (faddeeva_re_near) rather than a far-wing series.
+// one thread per point j, looping over kPplNodes T nodes; the lines whose windows
+// hold j are a contiguous index range (windows are monotone in the sorted line
+// index), found once per thread by binary search within the block's range, and
+// summed in ascending nu0 with compensation at each node.  Every point is near its
+// lines' centres, so each value is the near-centre form (faddeeva_re_near) rather
+// than a far-wing series.
+constexpr int kPplNodes = 8;
+
 template <int PROFILE>
 __global__ void __launch_bounds__(kTilePts)
 k_kappa_ppl(const float4 *__restrict__ P, const int4 *__restrict__ R, long long n_lines, long long n_nu,
-            WeidCoef wc, int accumulate, float *__restrict__ kappa) {
+            int nT, WeidCoef wc, int accumulate, float *__restrict__ kappa) {
   __shared__ long long s_range[2];
   const long long jw0 = (long long)blockIdx.x * kTilePts;
   const long long jend = min(jw0 + (long long)kTilePts, n_nu);
-  const int k = blockIdx.y;
-  if (threadIdx.x == 0) {
-    s_range[0] = lower_bound_hi(R, n_lines, (int)jw0);
-    s_range[1] = max(s_range[0], lower_bound_lo(R, n_lines, (int)jend));
-  }
+  const int k0 = blockIdx.y * kPplNodes, k1 = min(k0 + kPplNodes, nT);
+  if (threadIdx.x == 0) s_range[0] = lower_bound_hi(R, n_lines, (int)jw0);
+  if (threadIdx.x == 1) s_range[1] = lower_bound_lo(R, n_lines, (int)jend);
   __syncthreads();
   const long long j = jw0 + threadIdx.x;
   if (j >= n_nu) return;
   // lines [a, b) of the block's range with hi >= j and lo <= j
-  long long a = s_range[0], hi_end = s_range[1];
+  long long a = s_range[0], hi_end = max(s_range[0], s_range[1]);
   while (a < hi_end) {
     const long long m = (a + hi_end) >> 1;
     if (__ldg(&R[m].y) < (int)j) a = m + 1; else hi_end = m;
   }
-  long long b = a, b_end = s_range[1];
+  long long b = a, b_end = max(s_range[0], s_range[1]);
   while (b < b_end) {
     const long long m = (b + b_end) >> 1;
     if (__ldg(&R[m].x) <= (int)j) b = m + 1; else b_end = m;
   }
-  const float4 *Pk = P + (long long)k * n_lines;
-  float acc = 0.0f, cmp = 0.0f;
-  for (long long l = a; l < b; ++l) {
-    const int4 r = __ldg(R + l);
-    const float4 p = __ldg(Pk + l);
-    const float u = __fadd_rn((float)((int)j - r.z), __int_as_float(r.w));
-    float v;
-    if (PROFILE == RT_PROFILE_LORENTZ) {
-      v = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
-    } else {
-      const float x = p.y * u;
-      const float y = sqrtf(p.z);
-      v = __fdividef(p.x, y) * faddeeva_re_near(x, y, __fmaf_rn(x, x, p.z), wc);
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const float4 *Pk = P + (long long)k * n_lines;
+    float acc = 0.0f, cmp = 0.0f;
+    for (long long l = a; l < b; ++l) {
+      const int4 r = __ldg(R + l);
+      const float4 p = __ldg(Pk + l);
+      const float u = __fadd_rn((float)((int)j - r.z), __int_as_float(r.w));
+      float v;
+      if (PROFILE == RT_PROFILE_LORENTZ) {
+        v = p.x * rcp_approx(__fmaf_rn(u, u, p.y));
+      } else {
+        const float x = p.y * u;
+        const float y = sqrtf(p.z);
+        v = __fdividef(p.x, y) * faddeeva_re_near(x, y, __fmaf_rn(x, x, p.z), wc);
+      }
+      const float yk = __fsub_rn(v, cmp);
+      const float t = __fadd_rn(acc, yk);
+      cmp = __fsub_rn(__fsub_rn(t, acc), yk);
+      acc = t;
     }
-    const float yk = __fsub_rn(v, cmp);
-    const float t = __fadd_rn(acc, yk);
-    cmp = __fsub_rn(__fsub_rn(t, acc), yk);
-    acc = t;
+    float *dst = kappa + (long long)k * n_nu + j;
+    const float out = __fsub_rn(acc, cmp);
+    *dst = accumulate ? *dst + out : out;
   }
-  float *dst = kappa + (long long)k * n_nu + j;
-  const float out = __fsub_rn(acc, cmp);
-  *dst = accumulate ? *dst + out : out;
 }
 
 int g_kappa_tpb = kMaxTPerBlock;
@@ -772,12 +776,12 @@ rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *t
   }
   const long long n_tiles = (spec->n_nu + kTilePts - 1) / kTilePts;
   if (spec->points_per_line > 0) {  // fixed points per line: the gather kernel
-    dim3 g((unsigned)n_tiles, (unsigned)spec->nT);
+    dim3 g((unsigned)n_tiles, (unsigned)((spec->nT + kPplNodes - 1) / kPplNodes));
     if (spec->profile == RT_PROFILE_LORENTZ)
-      k_kappa_ppl<RT_PROFILE_LORENTZ><<<g, kTilePts, 0, st>>>(P, R, n, spec->n_nu, wc,
+      k_kappa_ppl<RT_PROFILE_LORENTZ><<<g, kTilePts, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc,
                                                               spec->accumulate ? 1 : 0, kappa);
     else
-      k_kappa_ppl<RT_PROFILE_VOIGT><<<g, kTilePts, 0, st>>>(P, R, n, spec->n_nu, wc,
+      k_kappa_ppl<RT_PROFILE_VOIGT><<<g, kTilePts, 0, st>>>(P, R, n, spec->n_nu, spec->nT, wc,
                                                             spec->accumulate ? 1 : 0, kappa);
     RT_CUDA_TRY(cudaGetLastError());
     return RT_OK;
