@@ -84,6 +84,24 @@ constexpr int kMarchMaxVis = 1024;  // cells per path staged in shared memory at
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
+// e^x for both halves as 2^(x log2 e): one paired multiply, then the MUFU base-2
+// exponential (ex2.approx.ftz, about 2 ulp; a subnormal result is flushed to zero)
+constexpr float kLog2e = 1.44269504088896341f;
+__device__ __forceinline__ float2 exp2_ftz2(float2 x) {
+  const float2 y = __fmul2_rn(x, dup2(kLog2e));
+  float2 r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(y.x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(y.y));
+  return r;
+}
+// a / b for both halves as a times the MUFU reciprocal of b (rcp.approx.ftz)
+__device__ __forceinline__ float2 div_ftz2(float2 a, float2 b) {
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(b.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(b.y));
+  return __fmul2_rn(a, r);
+}
+
 // 1 - e^(-a) for a >= 0, both halves: below 1/4 the Taylor series to a^6
 // (truncation < a^7/5040, relative 5e-8), above it one minus the hardware
 // exponential (relative error below 1.2e-6 at a = 1/4, falling with a).
@@ -94,7 +112,8 @@ __device__ __forceinline__ float2 one_minus_exp_neg2(float2 a) {
   p = __ffma2_rn(a, p, dup2(-0.5f));
   p = __ffma2_rn(a, p, dup2(1.0f));
   const float2 s = __fmul2_rn(a, p);
-  return make_float2(a.x < 0.25f ? s.x : 1.0f - __expf(-a.x), a.y < 0.25f ? s.y : 1.0f - __expf(-a.y));
+  const float2 e = exp2_ftz2(neg2(a));
+  return make_float2(a.x < 0.25f ? s.x : 1.0f - e.x, a.y < 0.25f ? s.y : 1.0f - e.y);
 }
 
 // e^x - 1 for x >= 0, both halves: the Taylor series below 1/4, else the hardware
@@ -106,7 +125,8 @@ __device__ __forceinline__ float2 expm1_pos2(float2 x) {
   p = __ffma2_rn(x, p, dup2(0.5f));
   p = __ffma2_rn(x, p, dup2(1.0f));
   const float2 s = __fmul2_rn(x, p);
-  return make_float2(x.x < 0.25f ? s.x : __expf(x.x) - 1.0f, x.y < 0.25f ? s.y : __expf(x.y) - 1.0f);
+  const float2 e = exp2_ftz2(x);
+  return make_float2(x.x < 0.25f ? s.x : e.x - 1.0f, x.y < 0.25f ? s.y : e.y - 1.0f);
 }
 
 // Block = 1024 wavenumbers (four per thread, as two pairs) of one path.  The
@@ -193,21 +213,21 @@ k_march(const float4 *__restrict__ cells, const float *__restrict__ tab, MarchPa
         // arguments is below 1/4 (each point takes the same form as in the helpers)
         if (fminf(fminf(a[0].x, a[0].y), fminf(a[1].x, a[1].y)) >= 0.25f) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) att[h] = make_float2(1.0f - __expf(-a[h].x), 1.0f - __expf(-a[h].y));
+          for (int h = 0; h < 2; ++h) att[h] = __fadd2_rn(dup2(1.0f), neg2(exp2_ftz2(neg2(a[h]))));
         } else {
 #pragma unroll
           for (int h = 0; h < 2; ++h) att[h] = one_minus_exp_neg2(a[h]);
         }
         if (xe[0].x >= 0.25f) {  // the thread's lowest wavenumber has the lowest argument
 #pragma unroll
-          for (int h = 0; h < 2; ++h) em1[h] = make_float2(__expf(xe[h].x) - 1.0f, __expf(xe[h].y) - 1.0f);
+          for (int h = 0; h < 2; ++h) em1[h] = __fadd2_rn(exp2_ftz2(xe[h]), dup2(-1.0f));
         } else {
 #pragma unroll
           for (int h = 0; h < 2; ++h) em1[h] = expm1_pos2(xe[h]);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float2 ib = make_float2(__fdividef(pre[h].x, em1[h].x), __fdividef(pre[h].y, em1[h].y));  // Eq. (planck)
+          const float2 ib = div_ftz2(pre[h], em1[h]);  // Eq. (planck)
           I[h] = __ffma2_rn(att[h], __fadd2_rn(ib, neg2(I[h])), I[h]);
         }
       }
