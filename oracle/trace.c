@@ -72,9 +72,11 @@ typedef struct {
 } og_spec;
 
 typedef struct {
-  const double *kappa;     /* [nT][ncol], cm^-1 */
+  const double *kappa;     /* [nT][ncol] (or [ncells][ncol] when per_cell), cm^-1 */
   int64_t ncol;
   const int64_t *col_of_j; /* [n_nu] column of each j (-1 absent), NULL = identity */
+  int32_t per_cell;        /* 1: kappa holds each cell's own value at its state */
+  int32_t pad;
 } og_table;
 
 enum { OG_OK = 0, OG_E_COLUMN = 1, OG_E_ARGS = 2, OG_E_NOMEM = 3 };
@@ -130,10 +132,13 @@ static void cell_prep(og_ctx *C) {
   }
 }
 
-/* kappa of cell c at table column col [cm^-1], linear in T between nodes. */
+/* kappa of cell c at table column col [cm^-1]: linear in T between nodes times
+ * the density scale; or, for a per-cell table (kappa evaluated by the caller at
+ * each cell's own T, p, x), the cell's own row as given. */
 static double cell_kappa(const og_ctx *C, int64_t c, int64_t col) {
   const double *K = C->t->kappa;
   int64_t nc = C->t->ncol;
+  if (C->t->per_cell) return K[c * nc + col];
   int k = C->cell_k[c];
   double fr = (double)C->cell_frac[c];
   double v;
@@ -456,7 +461,7 @@ int oracle_walk_rays(const og_grid *g, const og_spec *s, const og_table *t, int6
 
 /* Cell T bracket and density scale (for tests). */
 int oracle_cell_prep(const og_grid *g, const og_spec *s, int32_t *k, float *frac, float *sc) {
-  og_table t = {NULL, 0, NULL};
+  og_table t = {NULL, 0, NULL, 0, 0};
   og_ctx C;
   int e = ctx_init(&C, g, s, &t);
   if (!e) {

@@ -53,7 +53,8 @@ class OgSpec(ct.Structure):
 
 
 class OgTable(ct.Structure):
-    _fields_ = [("kappa", ct.c_void_p), ("ncol", ct.c_int64), ("col_of_j", ct.c_void_p)]
+    _fields_ = [("kappa", ct.c_void_p), ("ncol", ct.c_int64), ("col_of_j", ct.c_void_p),
+                ("per_cell", ct.c_int32), ("pad", ct.c_int32)]
 
 
 def lib():
@@ -85,7 +86,7 @@ def _p(a):
 class _Inputs:
     """Keeps the numpy buffers behind the ctypes structs alive."""
 
-    def __init__(self, grid, spec, kappa=None, columns=None):
+    def __init__(self, grid, spec, kappa=None, columns=None, per_cell=False):
         self.T = np.ascontiguousarray(grid.T, dtype=np.float32)
         self.p = None if grid.p_atm is None else np.ascontiguousarray(grid.p_atm, dtype=np.float32)
         self.x = None if grid.x is None else np.ascontiguousarray(grid.x, dtype=np.float32)
@@ -97,14 +98,17 @@ class _Inputs:
         if kappa is not None:
             self.K = np.ascontiguousarray(kappa, dtype=np.float64)
             ncol = self.K.shape[1]
+            rows = grid.nx * grid.ny * grid.nz if per_cell else max(1, int(spec.nT))
+            if self.K.ndim != 2 or self.K.shape[0] != rows:
+                raise ValueError(f"kappa must be ({rows}, ncol), got {self.K.shape}")
             if columns is None:
                 self.map = None
             else:
                 self.map = np.full(spec.n_nu, -1, dtype=np.int64)
                 self.map[np.asarray(columns, dtype=np.int64)] = np.arange(ncol)
-            self.t = OgTable(_p(self.K), ncol, _p(self.map))
+            self.t = OgTable(_p(self.K), ncol, _p(self.map), int(bool(per_cell)), 0)
         else:
-            self.t = OgTable(None, 0, None)
+            self.t = OgTable(None, 0, None, 0, 0)
 
 
 def philox4x32_10(counter, key):
@@ -144,15 +148,18 @@ class TraceResult:
 
 
 def trace(grid, spec, kappa, seed=0, ray_begin=0, n_rays=1000, n_total=None, mode=MODE_EMIT,
-          columns=None, tau_cut=False, enclosure=0, n_record=0, max_visits=None, threads=None):
+          columns=None, tau_cut=False, enclosure=0, n_record=0, max_visits=None, threads=None,
+          per_cell=False):
     """Run the estimator on rays [ray_begin, ray_begin + n_rays) of an N = n_total run.
 
-    kappa: (nT, ncol) float64 table; columns: the j of each table column (None =
-    all n_nu columns).  Returns a TraceResult; with n_record > 0 the first
-    n_record rays' visit sequences are returned in ``rec``.
+    kappa: (nT, ncol) float64 table, or with per_cell=True (ncells, ncol): each
+    cell's own absorption coefficient at its state (no T interpolation, no
+    density scale); columns: the j of each table column (None = all n_nu
+    columns).  Returns a TraceResult; with n_record > 0 the first n_record
+    rays' visit sequences are returned in ``rec``.
     """
     n_total = n_rays if n_total is None else n_total
-    I = _Inputs(grid, spec, kappa, columns)
+    I = _Inputs(grid, spec, kappa, columns, per_cell)
     ncells = grid.nx * grid.ny * grid.nz
     absorbed = np.zeros(ncells, dtype=np.float64)
     scalars = np.zeros(3, dtype=np.float64)
@@ -178,9 +185,9 @@ def trace(grid, spec, kappa, seed=0, ray_begin=0, n_rays=1000, n_total=None, mod
 
 
 def sample_rays(grid, spec, kappa, seed=0, ray_begin=0, n=16, n_total=None, mode=MODE_EMIT,
-                columns=None, enclosure=0):
+                columns=None, enclosure=0, per_cell=False):
     n_total = n if n_total is None else n_total
-    I = _Inputs(grid, spec, kappa, columns)
+    I = _Inputs(grid, spec, kappa, columns, per_cell)
     cell = np.zeros(n, dtype=np.int64)
     j = np.zeros(n, dtype=np.int64)
     pos = np.zeros((n, 3), dtype=np.float32)
@@ -194,9 +201,9 @@ def sample_rays(grid, spec, kappa, seed=0, ray_begin=0, n=16, n_total=None, mode
     return cell, j, pos, dirs, w
 
 
-def walk_rays(grid, spec, kappa, ix3, pos, dirs, j, w, columns=None):
+def walk_rays(grid, spec, kappa, ix3, pos, dirs, j, w, columns=None, per_cell=False):
     """Walk explicitly given rays; returns (absorbed per cell, escaped per ray)."""
-    I = _Inputs(grid, spec, kappa, columns)
+    I = _Inputs(grid, spec, kappa, columns, per_cell)
     n = int(len(j))
     ix3 = np.ascontiguousarray(ix3, dtype=np.int32)
     pos = np.ascontiguousarray(pos, dtype=np.float32)

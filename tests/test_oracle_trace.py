@@ -292,5 +292,69 @@ def test_cell_prep_brackets():
     k, fr, sc = OT.cell_prep(grid, spec)
     assert list(k) == [0, 1, 1, 3, 0, 3, 3]
     assert np.allclose(fr, [0, 0, 0.5, 1, 0, 1, 199 / 200], atol=1e-6)
-    # density scale (p x) / (p_ref x_ref) with the table at 1 atm, x = 0.1
+    # density scale (p x) / (p_ref x_ref) with the table at 1 atm, x = 0.1: here p x = p_ref x_ref
     assert np.allclose(sc, 1.0, atol=1e-7)
+
+
+def test_cell_density_scale_is_the_number_density_ratio():
+    # u_g of Eq. tau is x p / (k_B T); the table holds it at (p_ref, x_ref) and the cell's own
+    # T through the node bracket, so a cell's kappa is scaled by (p x) / (p_ref x_ref).  Cells
+    # with p x != p_ref x_ref: an inverted ratio, a dropped factor or a p- or x-only scale fails.
+    T = np.full(7, 1000.0, dtype=np.float32)
+    p = np.array([2.0, 1.0, 3.0, 0.5, 1.5, 2.5, 1.2], dtype=np.float32)
+    x = np.array([0.1, 0.05, 0.2, 0.3, 0.05, 0.01, 0.15], dtype=np.float32)
+    for p_ref, x_ref in ((1.0, 0.1), (1.5, 0.05)):
+        spec = synth.Spectral(nu_min=2000.0, dnu=0.1, n_nu=4, nT=5, T_min=800.0, T_max=1600.0,
+                              p_ref_atm=p_ref, x_ref=x_ref)
+        grid = synth.Grid(7, 1, 1, 0.1, 0.1, 0.1, T, p, x)
+        _, _, sc = OT.cell_prep(grid, spec)
+        expect = p.astype(np.float64) * x.astype(np.float64) / (p_ref * x_ref)
+        assert np.allclose(sc, expect, rtol=3e-7, atol=0), (p_ref, x_ref, sc, expect)
+        if p_ref == 1.0:
+            assert sc[0] == pytest.approx(2.0, rel=1e-7) and sc[1] == pytest.approx(0.5, rel=1e-7)
+        # a missing field stands for the table's reference value
+        _, _, sp = OT.cell_prep(synth.Grid(7, 1, 1, 0.1, 0.1, 0.1, T, p, None), spec)
+        _, _, sx = OT.cell_prep(synth.Grid(7, 1, 1, 0.1, 0.1, 0.1, T, None, x), spec)
+        assert np.allclose(sp, p.astype(np.float64) / p_ref, rtol=3e-7, atol=0)
+        assert np.allclose(sx, x.astype(np.float64) / x_ref, rtol=3e-7, atol=0)
+
+
+def test_per_cell_kappa_beam_through_a_layered_slab():
+    # Per-cell kappa (each cell's own value, no T interpolation): a collimated beam
+    # through a slab of 16 layers with kappa varying by layer and wavenumber is
+    # attenuated by exp(-100 h sum_c kappa_c) (Beer-Lambert, Eq. I first term), and
+    # layer c absorbs exp(-tau_<c) - exp(-tau_<=c) of it.
+    nc, n_nu, h = 16, 64, 1.0 / 16
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.5, n_nu=n_nu, nT=2, T_min=800.0, T_max=1600.0)
+    grid = synth.Grid(nc, 1, 1, h, math.inf, math.inf, np.linspace(800, 1600, nc).astype(np.float32))
+    c = np.arange(nc)[:, None]
+    j = np.arange(n_nu)[None, :]
+    Kc = 0.02 * (1.0 + c) * (0.25 + np.sin(0.3 * j + 0.7 * c) ** 2)
+    r = OT.trace(grid, spec, Kc, n_rays=n_nu, mode=OT.MODE_BEAM, n_record=n_nu, per_cell=True)
+    tau_cum = np.concatenate([np.zeros((1, n_nu)), np.cumsum(100.0 * h * Kc, axis=0)])
+    assert np.allclose(r.rec["escaped"], np.exp(-tau_cum[-1]), rtol=1e-12, atol=0)
+    layer = (np.exp(-tau_cum[:-1]) - np.exp(-tau_cum[1:])).sum(axis=1)
+    assert np.allclose(r.absorbed, layer, rtol=1e-12, atol=0)
+    assert r.energy_residual < 1e-12
+
+
+def test_per_cell_kappa_emission_is_each_cells_own_gray_emission():
+    # Gray cells at their own temperature and kappa: the per-(cell, nu) emitted powers
+    # summed over a wide grid give 4 kappa_c sigma T_c^4 V per cell, with kappa_c the
+    # cell's own value (the table's T bracket and density scale are not applied).
+    Ts = np.array([900.0, 1200.0, 1500.0], dtype=np.float32)
+    spec = synth.Spectral(nu_min=1.0, dnu=2.0, n_nu=12000, nT=2, T_min=500.0, T_max=2500.0,
+                          p_ref_atm=1.0, x_ref=0.1)
+    grid = synth.Grid(3, 1, 1, 0.1, 0.2, 0.3, Ts, np.full(3, 2.0, np.float32), np.full(3, 0.2, np.float32))
+    kc = np.array([0.01, 0.003, 0.02])
+    Kc = np.repeat(kc[:, None], spec.n_nu, axis=1)
+    n = 2_000_000
+    cell, j, pos, dirs, w = OT.sample_rays(grid, spec, Kc, seed=2, n=n, n_total=n, per_cell=True)
+    P = w * n / (3 * spec.n_nu)
+    key = cell * spec.n_nu + j
+    uk, first = np.unique(key, return_index=True)
+    assert uk.size == 3 * spec.n_nu
+    per_cell = np.bincount(cell[first], weights=P[first], minlength=3)
+    V = 0.1 * 0.2 * 0.3
+    expect = 4 * (100 * kc) * SIGMA_SB * Ts.astype(np.float64) ** 4 * V
+    assert np.allclose(per_cell, expect, rtol=1e-6, atol=0)
