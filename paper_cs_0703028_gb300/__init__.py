@@ -204,13 +204,19 @@ def make_grid(grid, device="cuda"):
 
 
 class Tally:
-    """Device tally buffers (caller-owned torch tensors) of a grid of ncells cells."""
+    """Device tally buffers (caller-owned torch tensors) of a grid of ncells cells.
+
+    ``absorbed`` and ``scalars`` are views of one binary64 buffer ``flat`` =
+    [absorbed[ncells] | emitted, absorbed total, escaped, residual], so that ranks
+    that traced disjoint ray ranges combine their tallies with one all-reduce
+    (``shard.combine_tally``)."""
 
     def __init__(self, ncells: int, device="cuda"):
         import torch
         self.ncells = int(ncells)
-        self.absorbed = torch.zeros(self.ncells, dtype=torch.float64, device=device)
-        self.scalars = torch.zeros(4, dtype=torch.float64, device=device)
+        self.flat = torch.zeros(self.ncells + 4, dtype=torch.float64, device=device)
+        self.absorbed = self.flat[:self.ncells]
+        self.scalars = self.flat[self.ncells:]
         self.steps = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.buf = rt_tally_buf(self.absorbed.data_ptr(), self.scalars.data_ptr(),
