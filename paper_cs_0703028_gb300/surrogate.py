@@ -31,11 +31,14 @@ def input_ranges(spec, p_nodes, x_lo, x_hi):
 
 
 def train_surrogate(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, n_samples=2_000_000, batch=8192,
-                    epochs=1, lr0=1e-3, lr1=1e-5, seed=0, params=None, log_every=0):
+                    epochs=1, lr0=1e-3, lr1=1e-5, seed=0, params=None, log_every=0, objective="mse"):
     """Train the network on samples drawn from line-by-line tables; returns
-    (params, norm, history) with history = [(step, loss)]."""
+    (params, norm, history) with history = [(step, loss)].  objective "mse": the
+    mean-squared error of the standardised log kappa over uniformly drawn samples."""
     import torch
     import synth
+    if objective != "mse":
+        raise ValueError(f"unknown training objective {objective!r}")
     p_nodes = np.asarray(p_nodes, dtype=np.float32)
     tables = training_tables(lines, spec, p_nodes)
     pn = torch.from_numpy(p_nodes).cuda()
