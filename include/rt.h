@@ -211,7 +211,8 @@ rt_status rt_build_kappa(const rt_lines *lines, const rt_spectral *spec, float *
  *   inputs return RT_E_INVAL with the required size before any work is queued.
  * Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before
- *   any stream capture.
+ *   any stream capture.  The address is kept for the life of the process, so a
+ *   device reset (cudaDeviceReset) between calls is not supported.
  * Sharing: all calls use the same array and it keeps the last call's contents;
  *   every call writes the scratch it reads before reading it.  Calls whose work
  *   can overlap on the GPU (other streams, other host threads) race on the array:

@@ -487,7 +487,17 @@ k_kappa(const float4 *__restrict__ P, const float4 *__restrict__ P2, const int4 
       }
     }
     if (__syncthreads_or(timed_out)) {  // the block leaves together
-      if (threadIdx.x == 0) status_or(status, RT_DEV_TIMEOUT);
+      if (threadIdx.x == 0) {
+        status_or(status, RT_DEV_TIMEOUT);
+        // The copies of this chunk and of the next one (issued one chunk ahead) may
+        // still be writing into this block's shared memory: wait for them, again with
+        // a bound, so that no copy lands after the block has released it.
+        for (int d = c; d < min(c + 2, nchunks); ++d) {
+          unsigned n = 0;
+          while (!mbar_try_wait(&bars[d & 1], (uint32_t)((d >> 1) & 1)) && ++n <= kWaitLimit) {
+          }
+        }
+      }
       aborted = true;
       break;
     }

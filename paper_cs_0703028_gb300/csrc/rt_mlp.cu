@@ -179,6 +179,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     *reinterpret_cast<uint4 *>(&S.A[tile_index(tid, c0)]) = pk;
   }
   int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
+  int mma_pending = -1;  // parity of a product whose completion wait gave up
 
   float y = 0.0f;
 #pragma unroll 1
@@ -192,7 +193,10 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
       tc::mma_commit(&S.bar_mma);
     }
     timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)(l & 1), kWaitLimit) ? 0 : 1;
-    if (__syncthreads_or(timeout)) break;
+    if (__syncthreads_or(timeout)) {
+      mma_pending = l & 1;
+      break;
+    }
     tc::fence_after_sync();
     const float *bias = S.sp.b[l];
 #pragma unroll 1
@@ -219,7 +223,13 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     }
   }
   if (timeout) {
-    if (tid == 0) status_or(status, RT_DEV_TIMEOUT);
+    if (tid == 0) {
+      status_or(status, RT_DEV_TIMEOUT);
+      // the weight copy or a product may still be in flight: let it land (bounded)
+      // before the block releases its shared and tensor memory
+      tc::mbar_wait(&S.bar_w, 0, kWaitLimit);
+      if (mma_pending >= 0) tc::mbar_wait(&S.bar_mma, (uint32_t)mma_pending, kWaitLimit);
+    }
   } else {
     y += S.sp.b5;
     if (TRAIN) {
@@ -343,6 +353,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
   int timeout = 0;
   bool aborted = false;
   uint32_t wphase = 0;
+  int w_pending = -1, mma_pending = -1;  // parities of a copy / products whose wait gave up
 #pragma unroll 1
   for (int l = 4; l >= 2; --l) {
     // W_l (rows = out) maps h_{l-1} -> z_l
@@ -351,6 +362,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     if (__syncthreads_or(timeout)) {
+      w_pending = (int)(wphase ^ 1u);
       aborted = true;
       break;
     }
@@ -362,6 +374,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     }
     timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)((4 - l) & 1), kWaitLimit) ? 0 : 1;
     if (__syncthreads_or(timeout)) {
+      mma_pending = (4 - l) & 1;
       aborted = true;
       break;
     }
@@ -418,6 +431,10 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
     __syncthreads();  // buf is rewritten by the next layer
   }
   if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
+  if (aborted && tid == 0) {  // let what is still in flight land (bounded) before leaving
+    if (w_pending >= 0) tc::mbar_wait(&S.bar_w, (uint32_t)w_pending, kWaitLimit);
+    if (mma_pending >= 0) tc::mbar_wait(&S.bar_mma, (uint32_t)mma_pending, kWaitLimit);
+  }
   if (aborted)  // block-uniform: the partial holds no gradient of this tile
     for (int i = tid; i < kNParam; i += kH) G[i] = 0.0f;
   tc::fence_before_sync();
@@ -491,6 +508,7 @@ k_tc_selftest(const float *__restrict__ A, const float *__restrict__ B, float *_
     tc::mma_commit(bar);
   }
   const int ok = tc::mbar_wait(bar, 0, kWaitLimit) ? 1 : 0;
+  if (!ok && tid == 0) tc::mbar_wait(bar, 0, kWaitLimit);  // bounded: let the product land
   if (__syncthreads_and(ok)) {
     tc::fence_after_sync();
     for (int c0 = 0; c0 < kH; c0 += 32) {
@@ -637,7 +655,11 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
     }
     const int timeout = tc::mbar_wait(&S.bar_mma[tile], phase, kWaitLimit) ? 0 : 1;
     phase ^= 1u;
-    if (tile_or(tile, timeout)) return false;
+    if (tile_or(tile, timeout)) {
+      // the product may still be in flight: let it land (bounded) before the tile stops
+      if (r == 0) tc::mbar_wait(&S.bar_mma[tile], phase ^ 1u, kWaitLimit);
+      return false;
+    }
     tc::fence_after_sync();
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 32) {
@@ -690,6 +712,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
     tc::bulk_g2s(&S.W[0][0], tiles, 3 * kTileBytes, &S.bar_w);
   }
   int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
+  const bool weights_late = __syncthreads_or(timeout) != 0;
   const bool record = rec.cells != nullptr;
   double em = 0.0, esc = 0.0;
   unsigned long long nsteps = 0;
@@ -697,7 +720,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   Ray R;
   bool active = false;
   const int tile = tid >> 7;
-  if (!__syncthreads_or(timeout)) {
+  if (!weights_late) {
     for (;;) {
       if (!active) {
         const unsigned long long claim = atomicAdd(&S.next, 1ull);
@@ -740,6 +763,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
     }
   }
   if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
+  if (weights_late && tid == 0) tc::mbar_wait(&S.bar_w, 0, kWaitLimit);  // bounded: let the copy land
   for (int o = 16; o > 0; o >>= 1) {
     em += __shfl_down_sync(0xffffffffu, em, o);
     esc += __shfl_down_sync(0xffffffffu, esc, o);
