@@ -534,7 +534,7 @@ def surrogate_summary(args):
     r = json.loads(buf.getvalue().strip().splitlines()[-1])
     w = r["walks"]
     keep = ("workload", "objective", "error_curve", "best", "speedup_vs_lbl", "meets_1pct_target",
-            "fit_by_band", "tensor_roofline", "training", "clocks")
+            "fit_by_band", "ensemble", "tensor_roofline", "training", "clocks")
     return {"steps_per_s": {k: w[k]["ray_cell_steps_per_s"] for k in w},
             **{k: r[k] for k in keep if k in r}, "workload": r["config"]["workload"]}
 
@@ -547,22 +547,47 @@ def _planck_torch(nu_cm, T):
     return 2.0 * h * c * c * nu ** 3 / torch.expm1(h * c * nu / (kb * T))
 
 
-def fit_by_band(rt, params, norm, spec, kap, T_lo=800.0, T_hi=2000.0, n_bands=10):
+def predict_table_single(rt, params, norm, spec, T_nodes):
+    """log kappa of one network at (log nu_j, T_k, p_ref, x_ref) for all j: [len(T_nodes), n_nu]."""
+    import torch
+    nu = spec.nu_min + torch.arange(spec.n_nu, device="cuda", dtype=torch.float64) * spec.dnu
+    pred = torch.empty((len(T_nodes), spec.n_nu), dtype=torch.float32, device="cuda")
+    for i, T in enumerate(T_nodes):
+        raw = torch.stack([torch.log(nu).float(), torch.full_like(nu, float(T)).float(),
+                           torch.full_like(nu, spec.p_ref_atm).float(),
+                           torch.full_like(nu, spec.x_ref).float()], 1).contiguous()
+        pred[i] = rt.mlp_forward(params, norm, raw)
+    return pred
+
+
+def predict_table_bands(rt, params, norms, band_pts, spec, T_nodes):
+    """The same for a spectral-band ensemble: each band's network on its own wavenumbers."""
+    import torch
+    nb = int(norms.shape[0])
+    j = torch.arange(nb * band_pts, device="cuda").clamp_max(spec.n_nu - 1).reshape(nb, band_pts)
+    nu = (spec.nu_min + j.double() * spec.dnu)
+    pred = torch.empty((len(T_nodes), spec.n_nu), dtype=torch.float32, device="cuda")
+    for i, T in enumerate(T_nodes):
+        raw = torch.stack([torch.log(nu).float(), torch.full_like(nu, float(T)).float(),
+                           torch.full_like(nu, spec.p_ref_atm).float(),
+                           torch.full_like(nu, spec.x_ref).float()], 2).contiguous()
+        out = rt.mlp_forward_nets(params, norms, raw).reshape(-1)[:spec.n_nu]
+        pred[i] = out
+    return pred
+
+
+def fit_by_band(predict, spec, kap, T_lo=800.0, T_hi=2000.0, n_bands=10):
     """Where the network's error comes from: per wavenumber band, at the table's T nodes
     within [T_lo, T_hi] (p_ref, x_ref), the rms error of log kappa and the ratio of the
-    Planck-weighted kappa sums (emission, the quantity the tallies follow) minus 1."""
+    Planck-weighted kappa sums (emission, the quantity the tallies follow) minus 1.
+    predict(T_nodes) -> log kappa [len(T_nodes), n_nu]."""
     import torch
     nodes = torch.from_numpy(spec.T_nodes()).cuda()
     ks = torch.nonzero((nodes >= T_lo) & (nodes <= T_hi)).flatten()
     nu = spec.nu_min + torch.arange(spec.n_nu, device="cuda", dtype=torch.float64) * spec.dnu
     out = []
     edges = np.linspace(0, spec.n_nu, n_bands + 1).astype(int)
-    pred = torch.empty((ks.numel(), spec.n_nu), dtype=torch.float32, device="cuda")
-    for i, k in enumerate(ks.tolist()):
-        raw = torch.stack([torch.log(nu).float(), torch.full_like(nu, float(nodes[k])).float(),
-                           torch.full_like(nu, spec.p_ref_atm).float(),
-                           torch.full_like(nu, spec.x_ref).float()], 1).contiguous()
-        pred[i] = rt.mlp_forward(params, norm, raw)
+    pred = predict([float(nodes[k]) for k in ks.tolist()])
     ref = kap[ks].double().clamp_min(1e-30)
     Ib = _planck_torch(nu[None, :], nodes[ks][:, None])
     for b in range(n_bands):
@@ -642,7 +667,45 @@ def run_surrogate(args):
         if best is None or row["median"] < best[0]["median"]:
             best = (row, params, norm, name)
     row, params, norm, best_name = best
-    bands = fit_by_band(rt, params, norm, spec, kap)
+    bands = fit_by_band(lambda Ts: predict_table_single(rt, params, norm, spec, Ts), spec, kap)
+    # the spectral-band ensemble: one network per args.bands wavenumbers, trained
+    # together, walked on the same rays
+    ens = None
+    if args.bands > 0:
+        nbands = surrogate.band_count(spec, args.bands)
+        n_per = max(args.band_batch, args.samples // nbands)
+        ens_curve = []
+        ens_best = None
+        for st_n in [int(v) for v in str(args.band_steps).split(",")]:
+            torch.cuda.synchronize()
+            t0 = time.time()
+            P_e, norms_e, hist_e = surrogate.train_bands(case.lines, spec, p_nodes, ex["train_x"][0],
+                                                         ex["train_x"][1], band_pts=args.bands, n_per_band=n_per,
+                                                         batch=args.band_batch, steps=st_n, log_every=250)
+            torch.cuda.synchronize()
+            tr_s = time.time() - t0
+            name = f"bands{args.bands}_s{st_n}"
+            with ClockWindow(0) as clk_b:
+                ab = timed_walk(name, lambda t: rt.trace_mlp_bands(gs, args.bands, P_e, norms_e, spec, t, n_rays=n,
+                                                                   n_rays_total=n), n)
+            walks[name]["clocks"] = clk_b.result
+            err = np.abs(ab[big] - ref[big]) / ref[big]
+            r_e = {"steps": st_n, "train_s": tr_s, "loss_first": hist_e[0][1] if hist_e else None,
+                   "loss_last": hist_e[-1][1] if hist_e else None, "median": float(np.median(err)),
+                   "p90": float(np.percentile(err, 90)), "p99": float(np.percentile(err, 99)),
+                   "max": float(err.max()), "frac_cells_within_1pct": float(np.mean(err <= 0.01)),
+                   "total": float(ab.sum() / ref.sum() - 1.0)}
+            ens_curve.append(r_e)
+            if ens_best is None or r_e["median"] < ens_best[0]["median"]:
+                ens_best = (r_e, P_e, norms_e, name)
+        r_e, P_e, norms_e, ens_name = ens_best
+        ens = {"band_pts": args.bands, "n_bands": nbands, "networks_params": nbands * rt.RT_MLP_NPARAM,
+               "samples_per_band": n_per, "batch_per_band": args.band_batch, "error_curve": ens_curve,
+               "best": {"walk": ens_name, "median": r_e["median"], "max": r_e["max"]},
+               "speedup_vs_lbl": walks[ens_name]["ray_cell_steps_per_s"] / walks["lbl"]["ray_cell_steps_per_s"],
+               "meets_1pct_median": r_e["median"] <= 0.01, "meets_1pct_max": r_e["max"] <= 0.01,
+               "fit_by_band": fit_by_band(lambda Ts: predict_table_bands(rt, P_e, norms_e, args.bands, spec, Ts),
+                                          spec, kap)}
     # device time of the training steps alone (one rt_mlp_train_steps call over K
     # 8192-sample batches of synthetic inputs within the training ranges; no table
     # build, no sampling)
@@ -679,6 +742,7 @@ def run_surrogate(args):
            "meets_1pct_target": row["max"] <= 0.01,
            "error_note": "per-cell |mlp - table| / table over cells with a table tally >= 1e-3 of the largest",
            "fit_by_band": bands,
+           "ensemble": ens,
            "training": {"samples": args.samples, "device_ms_per_step": step_ms,
                         "samples_per_s": B / (step_ms * 1e-3), "clocks": clk_t.result,
                         "step_note": f"{K} steps of {B} samples in one rt_mlp_train_steps call, CUDA events"},
@@ -928,6 +992,9 @@ def main():
     ap.add_argument("--epochs", default="1,8,32", help="comma-separated epoch counts (one network each)")
     ap.add_argument("--objective", default="mse", choices=["mse"])
     ap.add_argument("--rays", type=int, default=50_000_000)
+    ap.add_argument("--bands", type=int, default=64, help="wavenumbers per network of the ensemble (0: none)")
+    ap.add_argument("--band-steps", default="4000", help="comma-separated training steps (one ensemble each)")
+    ap.add_argument("--band-batch", type=int, default=1024)
     ap.add_argument("--rays-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.workload == "surrogate":

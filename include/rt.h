@@ -421,6 +421,60 @@ rt_status rt_mlp_make_samples(const float *tables, int32_t n_p, const float *p_n
                               int64_t n, float *inputs, float *targets, void *stream);
 
 /*
+ * Spectral-band ensembles of surrogate networks (the learned part; no paper
+ * passage).  One network of the layout above per band of band_pts consecutive
+ * wavenumber indices: network b serves j in [b band_pts, min((b + 1) band_pts,
+ * n_nu)), n_bands = ceil(n_nu / band_pts) <= 65535.  A network for a narrow band
+ * only has to resolve that band's lines, which one network for the whole window
+ * cannot.  Parameters: device [n_nets][RT_MLP_NPARAM] (network b at b *
+ * RT_MLP_NPARAM); norms: DEVICE array of n_nets rt_mlp_norm (each band's log nu
+ * range and output scale).
+ */
+
+/* Training samples for an ensemble: n_per_band samples per band b (rows b n_per_band
+ * .. of inputs device [n_bands][n_per_band][4], targets [n_bands][n_per_band]),
+ * drawn as in rt_mlp_make_samples but with j uniform in the band's own wavenumbers:
+ * Philox4x32-10 counter (i, i >> 32, b + 1, 0x6d6c70), key = seed.  Asynchronous. */
+rt_status rt_mlp_make_samples_bands(const float *tables, int32_t n_p, const float *p_nodes,
+                                    const rt_spectral *spec, int32_t band_pts, float x_lo, float x_hi,
+                                    uint64_t seed, int64_t n_per_band, float *inputs, float *targets,
+                                    void *stream);
+
+/* rt_mlp_train_steps for n_nets independent networks at once (one launch per kernel
+ * and step for all of them): network b trains on its own n samples (rows b n .. of
+ * inputs [n_nets][n][4], targets [n_nets][n]) with its own norm (norms: device
+ * [n_nets]), parameters and Adam moments (params, adam_m, adam_v, grad: device
+ * [n_nets][RT_MLP_NPARAM]).  Step s uses batch s mod (n / batch) of every network,
+ * the learning-rate schedule of rt_mlp_train_steps; losses[i] (optional) is the
+ * mean over the networks of their step-i losses.  Requires 1 <= n_nets <= 65535
+ * and batch * n_nets <= 2^30.  Asynchronous. */
+rt_status rt_mlp_train_steps_nets(int32_t n_nets, float *params, float *adam_m, float *adam_v, float *grad,
+                                  const float *inputs, const float *targets, int64_t n, int64_t batch,
+                                  const rt_mlp_norm *norms, double lr0, double lr1, int32_t step_first,
+                                  int32_t n_steps, int32_t total_steps, float *losses, uint32_t *status,
+                                  void *stream);
+
+/* rt_mlp_forward for n_nets networks: network b maps rows b n .. of inputs (device
+ * [n_nets][n][4]) to out[b n ..] (device [n_nets][n]) with norms[b] (device).
+ * Asynchronous. */
+rt_status rt_mlp_forward_nets(int32_t n_nets, const float *params, const rt_mlp_norm *norms, const float *inputs,
+                              int64_t n, float *out, uint32_t *status, void *stream);
+
+/*
+ * rt_trace_mlp_bands -- rt_trace_mlp with a spectral-band ensemble: the kappa of a
+ * ray at wavenumber index j comes from network floor(j / band_pts).  The rays,
+ * walk, deposits and tallies are those of rt_trace (the same Philox rays); the
+ * rays are grouped by band (a counting pass over their Philox draws) and each block
+ * takes work items of one band's rays with that band's network resident.  Tallies
+ * are sums, so the grouping changes only the binary64 summation order.  At most
+ * 2^32 - 1 rays per call when there is more than one band.  Asynchronous.
+ */
+rt_status rt_trace_mlp_bands(const rt_grid *grid, int32_t band_pts, const float *params,
+                             const rt_mlp_norm *norms, const rt_spectral *spec, uint64_t ray_begin,
+                             uint64_t n_rays, uint64_t n_rays_total, uint64_t seed, uint32_t enclosure,
+                             int32_t flags, const rt_tally_buf *tally, const rt_record *record, void *stream);
+
+/*
  * rt_trace_lbl -- rt_trace with the absorption coefficient of every visited cell
  * summed line by line at the cell's own (T, p, x): Eqs. (S) and (tau) evaluated
  * per step over the lines within the cutoff of nu_j, in binary32 with a Kahan

@@ -95,6 +95,13 @@ _SIGNATURES = {
                       ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_mlp_make_samples": ([_P, ct.c_int32, _P, _P, ct.c_float, ct.c_float, ct.c_uint64, ct.c_int64,
                              _P, _P, _P], ct.c_int),
+    "rt_mlp_make_samples_bands": ([_P, ct.c_int32, _P, _P, ct.c_int32, ct.c_float, ct.c_float, ct.c_uint64,
+                                   ct.c_int64, _P, _P, _P], ct.c_int),
+    "rt_mlp_train_steps_nets": ([ct.c_int32, _P, _P, _P, _P, _P, _P, ct.c_int64, ct.c_int64, _P, ct.c_double,
+                                 ct.c_double, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P], ct.c_int),
+    "rt_mlp_forward_nets": ([ct.c_int32, _P, _P, _P, ct.c_int64, _P, _P, _P], ct.c_int),
+    "rt_trace_mlp_bands": ([_P, ct.c_int32, _P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64,
+                            ct.c_uint32, ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_trace_lbl": ([_P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
                       ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_batch_create": ([ct.c_int32, _P, _P, ct.c_uint64, ct.c_int32, _P, _P], ct.c_int),
@@ -354,6 +361,82 @@ def trace_mlp(grid_struct, params, norm, spec, tally: Tally, n_rays: int, ray_be
                             int(enclosure), int(flags), ct.byref(tally.buf),
                             None if record is None else ct.byref(record.buf), _stream_ptr(stream))
     _check(st, "rt_trace_mlp")
+
+
+def norms_tensor(in_lo, in_hi, out_mean, out_scale, device="cuda"):
+    """Device array of rt_mlp_norm for an ensemble: in_lo, in_hi (n, 4), out_mean,
+    out_scale (n,), any array-likes (torch or numpy); returns float32 [n, 10]."""
+    import torch
+
+    def t(a):
+        return torch.as_tensor(a, dtype=torch.float32).to(device)
+    lo, hi = t(in_lo).reshape(-1, 4), t(in_hi).reshape(-1, 4)
+    return torch.cat([lo, hi, t(out_mean).reshape(-1, 1), t(out_scale).reshape(-1, 1)], 1).contiguous()
+
+
+def mlp_forward_nets(params, norms, inputs, out=None, stream=None):
+    """rt_mlp_forward_nets: params [n_nets * RT_MLP_NPARAM], norms [n_nets, 10] (device),
+    inputs [n_nets, n, 4] -> log kappa [n_nets, n]."""
+    import torch
+    nn_, n = int(inputs.shape[0]), int(inputs.shape[1])
+    if out is None:
+        out = torch.empty((nn_, n), dtype=torch.float32, device=inputs.device)
+    _check(lib().rt_mlp_forward_nets(nn_, _ptr(params), _ptr(norms), _ptr(inputs), n, _ptr(out), None,
+                                     _stream_ptr(stream)), "rt_mlp_forward_nets")
+    return out
+
+
+class MlpEnsembleTrainer:
+    """Parameters, Adam moments and gradients of n_nets networks (CUDA tensors
+    [n_nets * RT_MLP_NPARAM]) with their device norms [n_nets, 10]."""
+
+    def __init__(self, params, norms):
+        import torch
+        self.params = params
+        self.norms = norms
+        self.n_nets = int(norms.shape[0])
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.grad = torch.zeros_like(params)
+        self.status = torch.zeros(1, dtype=torch.int32, device=params.device)
+
+    def steps(self, inputs, targets, batch, lr0, lr1, step_first, n_steps, total_steps, losses=None,
+              stream=None):
+        """rt_mlp_train_steps_nets over inputs [n_nets, n, 4], targets [n_nets, n]."""
+        n = int(targets.shape[1])
+        st = lib().rt_mlp_train_steps_nets(self.n_nets, _ptr(self.params), _ptr(self.m), _ptr(self.v),
+                                           _ptr(self.grad), _ptr(inputs), _ptr(targets), n, int(batch),
+                                           _ptr(self.norms), float(lr0), float(lr1), int(step_first),
+                                           int(n_steps), int(total_steps), _ptr(losses), _ptr(self.status),
+                                           _stream_ptr(stream))
+        _check(st, "rt_mlp_train_steps_nets")
+
+
+def mlp_make_samples_bands(tables, p_nodes, spec, band_pts, x_lo, x_hi, seed, n_per_band, stream=None):
+    """rt_mlp_make_samples_bands: (inputs [n_bands, n, 4], targets [n_bands, n]) CUDA tensors."""
+    import torch
+    nb = -(-int(spec.n_nu) // int(band_pts))
+    inputs = torch.empty((nb, n_per_band, 4), dtype=torch.float32, device=tables.device)
+    targets = torch.empty((nb, n_per_band), dtype=torch.float32, device=tables.device)
+    S = make_spectral(spec)
+    st = lib().rt_mlp_make_samples_bands(_ptr(tables), int(p_nodes.shape[0]), _ptr(p_nodes), ct.byref(S),
+                                         int(band_pts), float(x_lo), float(x_hi), int(seed), int(n_per_band),
+                                         _ptr(inputs), _ptr(targets), _stream_ptr(stream))
+    _check(st, "rt_mlp_make_samples_bands")
+    return inputs, targets
+
+
+def trace_mlp_bands(grid_struct, band_pts, params, norms, spec, tally: Tally, n_rays: int, ray_begin: int = 0,
+                    n_rays_total: int | None = None, seed: int = 0, enclosure: int = 0, flags: int = 0,
+                    record: Record | None = None, stream=None):
+    """Run rt_trace_mlp_bands (asynchronous); accumulates into ``tally``."""
+    S = make_spectral(spec)
+    st = lib().rt_trace_mlp_bands(ct.byref(grid_struct), int(band_pts), _ptr(params), _ptr(norms), ct.byref(S),
+                                  int(ray_begin), int(n_rays),
+                                  int(n_rays_total if n_rays_total is not None else n_rays), int(seed),
+                                  int(enclosure), int(flags), ct.byref(tally.buf),
+                                  None if record is None else ct.byref(record.buf), _stream_ptr(stream))
+    _check(st, "rt_trace_mlp_bands")
 
 
 def trace_lbl(grid_struct, lines, spec, tally: Tally, n_rays: int, ray_begin: int = 0,

@@ -42,6 +42,13 @@ constexpr uint32_t kWaitLimit = 1u << 24;
 struct Norm {
   float lo[4], hi[4], mean, scale;
 };
+static_assert(sizeof(Norm) == sizeof(rt_mlp_norm), "Norm must have the layout of rt_mlp_norm");
+
+// Network `net` of an ensemble with per-network norms in device memory (norms),
+// or the one network of a call that passed its norm by value (norms == nullptr).
+__device__ __forceinline__ Norm net_norm(const Norm *__restrict__ norms, const Norm &single, int net) {
+  return norms ? norms[net] : single;
+}
 
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;
@@ -78,8 +85,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // bf16 element (r, k) of a K-major 128x128 tile (in units of 2-byte elements)
 __device__ __forceinline__ int tile_index(int r, int k) { return (int)(tc::kmajor_offset(r, k, kH) >> 1); }
 
-__global__ void k_mlp_prep(const float *__restrict__ P, uint16_t *__restrict__ tiles) {
+__global__ void k_mlp_prep(const float *__restrict__ P, uint16_t *__restrict__ tiles, int n_mats) {
   const int m = blockIdx.y;  // 0..2: W2..W4 (rows = out), 3..5: transposes (rows = in)
+  const long long net = blockIdx.z;
+  P += net * kNParam;
+  tiles += net * n_mats * kTileElems;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kTileElems) return;
   const int r = idx / kH, k = idx % kH;
@@ -133,15 +143,30 @@ struct FwdSmem {
   float red[4];
 };
 
+// Networks of an ensemble along grid.y: network `net` reads its parameters, tiles,
+// samples (n rows at net * in_stride) and activations at net times the per-network
+// strides.
 template <bool TRAIN>
 __global__ void __launch_bounds__(128)
-k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
-          const float *__restrict__ inputs, const float *__restrict__ targets, long long n,
-          float *__restrict__ Z, float *__restrict__ dy, float *__restrict__ loss,
-          float *__restrict__ out, uint32_t *status) {
+k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long long tile_stride, Norm N1,
+          const Norm *__restrict__ norms, const float *__restrict__ inputs, const float *__restrict__ targets,
+          long long n, long long in_stride, float *__restrict__ Z, float *__restrict__ dy,
+          float *__restrict__ loss, float loss_scale, float *__restrict__ out, uint32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   FwdSmem &S = *reinterpret_cast<FwdSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long net = blockIdx.y;
+  const Norm N = net_norm(norms, N1, (int)net);
+  P += net * kNParam;
+  tiles += net * tile_stride;
+  inputs += net * in_stride * 4;  // the network's n rows of samples (in_stride rows apart)
+  if (TRAIN) {
+    targets += net * in_stride;
+    Z += net * 4 * kH * n;
+    dy += net * n;
+  } else {
+    out += net * in_stride;
+  }
   const long long row = (long long)blockIdx.x * kH + tid;
   const bool valid = row < n;
 
@@ -236,7 +261,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm 
       const float ts = valid ? (targets[row] - N.mean) / N.scale : 0.0f;
       const float r = valid ? (y - ts) : 0.0f;
       if (valid) dy[row] = r / (float)n;
-      float l2 = 0.5f * r * r / (float)n;
+      float l2 = 0.5f * r * r / (float)n * loss_scale;
       for (int o = 16; o > 0; o >>= 1) l2 += __shfl_down_sync(0xffffffffu, l2, o);
       if (lane == 0) S.red[warp] = l2;
     } else if (valid) {
@@ -277,14 +302,22 @@ __device__ __forceinline__ float column_sum(const BwdSmem &S, int c) {
 }
 
 __global__ void __launch_bounds__(128)
-k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
-          const float *__restrict__ inputs, long long n, const float *__restrict__ Z,
-          const float *__restrict__ dy, float *__restrict__ Gpart, uint32_t *status) {
+k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long long tile_stride, Norm N1,
+          const Norm *__restrict__ norms, const float *__restrict__ inputs, long long n, long long in_stride,
+          const float *__restrict__ Z, const float *__restrict__ dy, float *__restrict__ Gpart,
+          uint32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   BwdSmem &S = *reinterpret_cast<BwdSmem *>(smem_raw);
+  const long long net = blockIdx.y;  // network of an ensemble (strides as in k_mlp_fwd)
+  const Norm N = net_norm(norms, N1, (int)net);
+  P += net * kNParam;
+  tiles += net * tile_stride;
+  inputs += net * in_stride * 4;
+  Z += net * 4 * kH * n;
+  dy += net * n;
   // this tile's gradient partial (every parameter written exactly once; summed over
   // the tiles in a fixed order by k_grad_adam)
-  float *G = Gpart + (long long)blockIdx.x * kGradStride;
+  float *G = Gpart + (net * gridDim.x + blockIdx.x) * kGradStride;
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long row = (long long)blockIdx.x * kH + tid;
   const bool valid = row < n;
@@ -454,6 +487,15 @@ __global__ void k_grad_adam(const float *__restrict__ part, int nparts, float *_
                             float b1, float b2, float eps, float c1, float c2, uint16_t *__restrict__ tiles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kNParam) return;
+  const long long net = blockIdx.y;  // network of an ensemble: its partials, parameters, moments, tiles
+  part += net * nparts * kGradStride;
+  grad += net * kNParam;
+  P += net * kNParam;
+  if (adam) {
+    m += net * kNParam;
+    v += net * kNParam;
+  }
+  if (tiles) tiles += net * 6 * kTileElems;
   float gi = 0.0f;
   for (int t = 0; t < nparts; ++t) gi += part[(long long)t * kGradStride + i];
   grad[i] = gi;
@@ -556,8 +598,21 @@ struct WalkMlpSmem {
   uint16_t Bb[3][kL1Elems];            // biases of layers 2..4 against A1's constant-one columns
   WalkSmall sp;
   uint64_t bar_w, bar_mma[kWalkTiles];
-  unsigned long long next;
+  unsigned long long next, end;        // the current work item's claim cursor and end
+  int band;                            // the current work item's band (-1: no item left)
   uint32_t tmem;
+};
+
+// Work of a surrogate walk over a spectral-band ensemble: the rays grouped by the
+// band of their wavenumber index (order[band_start[b] ..] are band b's ray offsets;
+// nullptr: one band, rays in order), cut into work items of at most `chunk` rays
+// that never straddle a band (band b's items are item_start[b] .. item_start[b+1]).
+struct BandPlan {
+  const uint32_t *order;
+  const long long *band_start, *item_start;
+  unsigned long long *item_next;  // work-item counter, zero at launch
+  long long chunk;
+  int n_bands;
 };
 static_assert(sizeof(WalkMlpSmem) <= 227 * 1024, "surrogate walk shared memory exceeds 227 KB per block");
 
@@ -684,52 +739,87 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
 }
 
 __global__ void __launch_bounds__(kWalkMlpThreads, 1)
-k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N,
-           const float *__restrict__ T, const float *__restrict__ Pf, const float *__restrict__ Xf,
-           float p_ref, float x_ref, WalkParams W, double *__restrict__ absorbed,
-           double *__restrict__ scalars, unsigned long long *__restrict__ steps_out,
-           uint32_t *status, RecordPtrs rec) {
+k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm N1,
+           const Norm *__restrict__ norms, BandPlan B, const float *__restrict__ T,
+           const float *__restrict__ Pf, const float *__restrict__ Xf, float p_ref, float x_ref, WalkParams W,
+           double *__restrict__ absorbed, double *__restrict__ scalars,
+           unsigned long long *__restrict__ steps_out, uint32_t *status, RecordPtrs rec) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   WalkMlpSmem &S = *reinterpret_cast<WalkMlpSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const unsigned long long begin = W.n_rays * blockIdx.x / gridDim.x;
-  const unsigned long long end = W.n_rays * (blockIdx.x + 1) / gridDim.x;
   if (tid == 0) {
     tc::mbar_init(&S.bar_w, 1);
     for (int t = 0; t < kWalkTiles; ++t) tc::mbar_init(&S.bar_mma[t], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    S.next = begin;
   }
   if (warp == 0) tc::tmem_alloc(&S.tmem, kWalkTmemCols);
-  stage_walk(S, P);
-  tc::fence_smem_to_async();  // B1 is read by the tensor cores of every tile
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = S.tmem;
-  if (tid == 0) {
-    tc::mbar_arrive_expect_tx(&S.bar_w, 3 * kTileBytes);
-    tc::bulk_g2s(&S.W[0][0], tiles, 3 * kTileBytes, &S.bar_w);
-  }
-  int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
-  const bool weights_late = __syncthreads_or(timeout) != 0;
   const bool record = rec.cells != nullptr;
   double em = 0.0, esc = 0.0;
   unsigned long long nsteps = 0;
-  uint32_t phase = 0;
-  Ray R;
-  bool active = false;
+  uint32_t phase = 0;   // this tile's product barrier phase
+  uint32_t wphase = 0;  // the weight copies' barrier phase
+  int cur_band = -1, timeout = 0;
+  bool weights_late = false;
   const int tile = tid >> 7;
-  if (!weights_late) {
-    for (;;) {
+  Norm N = N1;
+#pragma unroll 1
+  for (;;) {  // work items: one band's network, at most B.chunk of its rays
+    if (tid == 0) {
+      const long long it = (long long)atomicAdd(B.item_next, 1ull);
+      int band = -1;
+      long long b0 = 0, b1 = 0;
+      if (it < B.item_start[B.n_bands]) {
+        int lo = 0, hi = B.n_bands - 1;  // the last band whose first item is <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (B.item_start[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        band = lo;
+        b0 = B.band_start[band] + (it - B.item_start[band]) * B.chunk;
+        b1 = min(b0 + B.chunk, B.band_start[band + 1]);
+      }
+      S.band = band;
+      S.next = (unsigned long long)b0;
+      S.end = (unsigned long long)b1;
+    }
+    __syncthreads();
+    const int band = S.band;
+    if (band < 0) break;
+    if (band != cur_band) {  // this band's network: small parameters staged, hidden layers copied
+      stage_walk(S, P + (long long)band * kNParam);
+      tc::fence_smem_to_async();  // B1, Bb are read by the tensor cores of every tile
+      if (tid == 0) {
+        tc::mbar_arrive_expect_tx(&S.bar_w, 3 * kTileBytes);
+        tc::bulk_g2s(&S.W[0][0], tiles + (long long)band * 3 * kTileElems, 3 * kTileBytes, &S.bar_w);
+      }
+      const int late = tc::mbar_wait(&S.bar_w, wphase, kWaitLimit) ? 0 : 1;
+      wphase ^= 1u;
+      tc::fence_before_sync();
+      if (__syncthreads_or(late)) {
+        weights_late = true;
+        timeout = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      N = net_norm(norms, N1, band);
+      cur_band = band;
+    }
+    Ray R;
+    bool active = false;
+#pragma unroll 1
+    for (;;) {  // the item's rays: a lane whose ray is done claims the next one
       if (!active) {
         const unsigned long long claim = atomicAdd(&S.next, 1ull);
-        if (claim < end) {
-          ray_init(W, nullptr, nullptr, claim, record, R);
+        if (claim < S.end) {
+          ray_init(W, nullptr, nullptr, B.order ? (unsigned long long)B.order[claim] : claim, record, R);
           active = true;
         }
       }
-      if (!tile_or(tile, active)) break;  // this tile has no ray left
+      if (!tile_or(tile, active)) break;  // this tile has no ray of the item left
       float raw[4] = {N.lo[0], N.lo[1], N.lo[2], N.lo[3]};
       float Tc = 1.0f;
       if (active) {
@@ -761,9 +851,11 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
         }
       }
     }
+    // every tile is done with this item (and with the band's weights) before the next
+    if (__syncthreads_or(timeout)) break;
   }
   if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
-  if (weights_late && tid == 0) tc::mbar_wait(&S.bar_w, 0, kWaitLimit);  // bounded: let the copy land
+  if (weights_late && tid == 0) tc::mbar_wait(&S.bar_w, wphase ^ 1u, kWaitLimit);  // bounded: let the copy land
   for (int o = 16; o > 0; o >>= 1) {
     em += __shfl_down_sync(0xffffffffu, em, o);
     esc += __shfl_down_sync(0xffffffffu, esc, o);
@@ -779,6 +871,86 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   if (warp == 0) {
     tc::fence_after_sync();
     tc::tmem_dealloc(tmem, kWalkTmemCols);
+  }
+}
+
+// ---------------------------------------------------------------- band plan of a walk
+// The wavenumber index of ray rr (the draw ray_init makes: Philox call 0, word 1).
+__device__ __forceinline__ int ray_nu_index(const WalkParams &W, unsigned long long rr) {
+  const unsigned long long r = W.ray_begin + rr;
+  const u32x4 v = philox4x32_10(u32x4{(uint32_t)r, (uint32_t)(r >> 32), 0u, W.enclosure}, W.seed_lo, W.seed_hi);
+  return (int)(((unsigned long long)v.y * (unsigned long long)W.n_nu) >> 32);
+}
+
+constexpr int kBandHist = 8192;  // bands counted in a shared-memory histogram (else global atomics)
+
+// rays per band (counts zeroed before the launch)
+__global__ void k_band_count(WalkParams W, int band_pts, int n_bands, unsigned long long *__restrict__ counts) {
+  __shared__ unsigned int hist[kBandHist];
+  const bool local = n_bands <= kBandHist;
+  if (local)
+    for (int b = threadIdx.x; b < n_bands; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; rr < W.n_rays;
+       rr += (unsigned long long)gridDim.x * blockDim.x) {
+    const int b = ray_nu_index(W, rr) / band_pts;
+    if (local) atomicAdd(&hist[b], 1u);
+    else atomicAdd(&counts[b], 1ull);
+  }
+  __syncthreads();
+  if (local)
+    for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
+      if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
+}
+
+// band_start and item_start (exclusive prefix sums over the bands; one block), the
+// scatter cursors; counts == nullptr: one band holding all n_rays rays
+__global__ void k_band_plan(const unsigned long long *__restrict__ counts, int n_bands, unsigned long long n_rays,
+                            long long chunk, long long *__restrict__ band_start, long long *__restrict__ item_start,
+                            unsigned long long *__restrict__ cursor) {
+  __shared__ long long sc[1024], si[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  // each thread sums a contiguous run of bands, then the runs are scanned
+  const int per = (n_bands + nt - 1) / nt;
+  const int b0 = min(n_bands, t * per), b1 = min(n_bands, b0 + per);
+  long long c = 0, it = 0;
+  for (int b = b0; b < b1; ++b) {
+    const long long k = counts ? (long long)counts[b] : (long long)n_rays;
+    c += k;
+    it += (k + chunk - 1) / chunk;
+  }
+  sc[t] = c;
+  si[t] = it;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {  // inclusive scan of the runs (Hillis-Steele)
+    const long long a = t >= o ? sc[t - o] : 0, bi = t >= o ? si[t - o] : 0;
+    __syncthreads();
+    sc[t] += a;
+    si[t] += bi;
+    __syncthreads();
+  }
+  long long pc = sc[t] - c, pi = si[t] - it;
+  for (int b = b0; b < b1; ++b) {
+    const long long k = counts ? (long long)counts[b] : (long long)n_rays;
+    band_start[b] = pc;
+    item_start[b] = pi;
+    if (cursor) cursor[b] = (unsigned long long)pc;
+    pc += k;
+    pi += (k + chunk - 1) / chunk;
+  }
+  if (t == nt - 1) {
+    band_start[n_bands] = sc[t];
+    item_start[n_bands] = si[t];
+  }
+}
+
+// ray offsets into their band's run of order (order within a band: arrival order)
+__global__ void k_band_scatter(WalkParams W, int band_pts, unsigned long long *__restrict__ cursor,
+                               uint32_t *__restrict__ order) {
+  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; rr < W.n_rays;
+       rr += (unsigned long long)gridDim.x * blockDim.x) {
+    const int b = ray_nu_index(W, rr) / band_pts;
+    order[atomicAdd(&cursor[b], 1ull)] = (uint32_t)rr;
   }
 }
 
@@ -805,6 +977,35 @@ __global__ void k_mlp_samples(const float *__restrict__ tables, int np, int nT, 
   inputs[i * 4 + 2] = p_nodes[kp];
   inputs[i * 4 + 3] = x;
   targets[i] = logf(fmaxf(kap * (x / x_ref), 1e-30f));
+}
+
+// Training samples of a spectral-band ensemble: band b (grid.y) draws its n samples
+// from its own wavenumbers j in [b band_pts, min((b + 1) band_pts, n_nu)): Philox
+// counter (i, i >> 32, b + 1, 0x6d6c70) under the seed picks j in the band, the T
+// node, the pressure node and x as k_mlp_samples does; rows b n + i.
+__global__ void k_mlp_samples_bands(const float *__restrict__ tables, int np, int nT, long long n_nu,
+                                    const float *__restrict__ p_nodes, float T_min, float dT, float nu_min,
+                                    float dnu, float x_lo, float x_hi, float x_ref, uint32_t seed_lo,
+                                    uint32_t seed_hi, int band_pts, long long n, float *__restrict__ inputs,
+                                    float *__restrict__ targets) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long b = blockIdx.y;
+  if (i >= n) return;
+  const u32x4 v = philox4x32_10(u32x4{(uint32_t)i, (uint32_t)((unsigned long long)i >> 32), (uint32_t)(b + 1),
+                                      0x6d6c70u}, seed_lo, seed_hi);
+  const long long j0 = b * band_pts;
+  const long long width = min((long long)band_pts, n_nu - j0);
+  const long long j = j0 + (long long)(((unsigned long long)v.x * (unsigned long long)width) >> 32);
+  const int kT = (int)(((unsigned long long)v.y * (unsigned long long)nT) >> 32);
+  const int kp = (int)(((unsigned long long)v.z * (unsigned long long)np) >> 32);
+  const float x = x_lo + (x_hi - x_lo) * ((float)(v.w >> 8) * 0x1p-24f);
+  const float kap = tables[((long long)kp * nT + kT) * n_nu + j];
+  const long long o = b * n + i;
+  inputs[o * 4 + 0] = __logf(fmaf((float)j, dnu, nu_min));
+  inputs[o * 4 + 1] = fmaf((float)kT, dT, T_min);
+  inputs[o * 4 + 2] = p_nodes[kp];
+  inputs[o * 4 + 3] = x;
+  targets[o] = logf(fmaxf(kap * (x / x_ref), 1e-30f));
 }
 
 }  // namespace
@@ -841,29 +1042,37 @@ Norm to_norm(const rt_mlp_norm *nm) {
 
 }  // namespace
 
-rt_status mlp_prep_tiles(const float *params, uint16_t *tiles, cudaStream_t st) {
-  k_mlp_prep<<<dim3(kTileElems / 256, 6), 256, 0, st>>>(params, tiles);
+// BF16 tiles of n_nets networks: the first n_mats of W2..W4, W2^T..W4^T per network
+rt_status mlp_prep_tiles(const float *params, uint16_t *tiles, int n_nets, int n_mats, cudaStream_t st) {
+  k_mlp_prep<<<dim3(kTileElems / 256, n_mats, n_nets), 256, 0, st>>>(params, tiles, n_mats);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
 
-// scratch of one training step of n samples: BF16 weight tiles, pre-activations,
-// output gradient, per-tile gradient partials
-size_t train_scratch_bytes(int64_t n) {
+// scratch of one training step of n samples for each of n_nets networks: BF16 weight
+// tiles, pre-activations, output gradients, per-tile gradient partials
+size_t train_scratch_bytes(int64_t n, int n_nets) {
   const size_t grid = (size_t)((n + kH - 1) / kH);
-  return 6 * (size_t)kTileBytes + (size_t)4 * (size_t)n * kH * sizeof(float) + (size_t)n * sizeof(float) +
-         grid * kGradStride * sizeof(float) + 64;
+  const size_t nn = (size_t)n_nets;
+  return nn * (6 * (size_t)kTileBytes + (size_t)4 * (size_t)n * kH * sizeof(float) + (size_t)n * sizeof(float) +
+               grid * kGradStride * sizeof(float)) + 64;
 }
 
 rt_status validate_train(float *params, float *m, float *v, float *grad, const float *inputs,
-                         const float *targets, int64_t n, const rt_mlp_norm *nm, int32_t flags,
-                         float *loss) {
+                         const float *targets, int64_t n, int n_nets, const rt_mlp_norm *nm, bool norm_on_device,
+                         int32_t flags, float *loss) {
   if (!params || !grad || !inputs || !targets || !loss)
     return fail(RT_E_INVAL, "rt_mlp_train_step: NULL buffer");
   if (!(flags & RT_MLP_GRAD_ONLY) && (!m || !v)) return fail(RT_E_INVAL, "rt_mlp_train_step: NULL Adam state");
   if (n < 1 || n > (1LL << 26)) return fail(RT_E_INVAL, "rt_mlp_train_step: n out of range");
-  rt_status s = validate_norm(nm);
-  if (s != RT_OK) return s;
+  if (n_nets < 1 || n_nets > 65535) return fail(RT_E_INVAL, "rt_mlp_train_steps_nets: n_nets must be in [1, 65535]");
+  if ((double)n * (double)n_nets > (double)(1LL << 30))
+    return fail(RT_E_INVAL, "rt_mlp_train_steps_nets: n * n_nets must not exceed 2^30 samples per step");
+  if (!nm) return fail(RT_E_INVAL, "norm is NULL");
+  if (!norm_on_device) {
+    rt_status s = validate_norm(nm);
+    if (s != RT_OK) return s;
+  }
   static std::once_flag once;
   static rt_status attr = RT_OK;
   std::call_once(once, [] {
@@ -873,35 +1082,41 @@ rt_status validate_train(float *params, float *m, float *v, float *grad, const f
   return attr;
 }
 
-// one step on validated arguments, scratch of train_scratch_bytes(n) bytes; `chained`:
-// the scratch's BF16 tiles already hold the parameters and the loss slot is zero (a
-// run of steps), and the Adam kernel refreshes the tiles for the next step
+// one step on validated arguments, scratch of train_scratch_bytes(n, n_nets) bytes;
+// `chained`: the scratch's BF16 tiles already hold the parameters and the loss slot
+// is zero (a run of steps), and the Adam kernel refreshes the tiles for the next
+// step.  n_nets networks (norms: device [n_nets], or N1 by value for one network)
+// each take n samples of inputs / targets at row net * in_stride.
 rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const float *inputs,
-                         const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
-                         int32_t flags, float *loss, uint32_t *status, char *scr, bool chained,
-                         cudaStream_t st) {
+                         const float *targets, int64_t n, int64_t in_stride, int n_nets, const Norm &N1,
+                         const Norm *norms, float lr, int32_t step, int32_t flags, float *loss, uint32_t *status,
+                         char *scr, bool chained, cudaStream_t st) {
   const unsigned grid = (unsigned)((n + kH - 1) / kH);
+  const size_t nn = (size_t)n_nets;
   uint16_t *tiles = reinterpret_cast<uint16_t *>(scr);
-  float *Z = reinterpret_cast<float *>(scr + 6 * (size_t)kTileBytes);
-  float *dy = Z + (size_t)4 * n * kH;
+  float *Z = reinterpret_cast<float *>(scr + nn * 6 * (size_t)kTileBytes);
+  float *dy = Z + nn * 4 * (size_t)n * kH;
   float *gpart = reinterpret_cast<float *>(
-      (reinterpret_cast<uintptr_t>(dy + n) + 63) & ~uintptr_t(63));  // 64-byte aligned rows
+      (reinterpret_cast<uintptr_t>(dy + nn * (size_t)n) + 63) & ~uintptr_t(63));  // 64-byte aligned rows
   if (!chained) {
     RT_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
-    rt_status s = mlp_prep_tiles(params, tiles, st);
+    rt_status s = mlp_prep_tiles(params, tiles, n_nets, 6, st);
     if (s != RT_OK) return s;
   }
-  const Norm N = to_norm(nm);
-  k_mlp_fwd<true><<<grid, kH, sizeof(FwdSmem), st>>>(params, tiles, N, inputs, targets, n, Z, dy, loss,
-                                                     nullptr, status);
+  const long long ts = 6LL * kTileElems;
+  k_mlp_fwd<true><<<dim3(grid, n_nets), kH, sizeof(FwdSmem), st>>>(
+      params, tiles, ts, N1, norms, inputs, targets, n, in_stride, Z, dy, loss, 1.0f / (float)n_nets, nullptr,
+      status);
   RT_CUDA_TRY(cudaGetLastError());
-  k_mlp_bwd<<<grid, kH, sizeof(BwdSmem), st>>>(params, tiles, N, inputs, n, Z, dy, gpart, status);
+  k_mlp_bwd<<<dim3(grid, n_nets), kH, sizeof(BwdSmem), st>>>(params, tiles, ts, N1, norms, inputs, n, in_stride,
+                                                             Z, dy, gpart, status);
   RT_CUDA_TRY(cudaGetLastError());
   const bool adam = !(flags & RT_MLP_GRAD_ONLY);
   const float c1 = adam ? (float)(1.0 - std::pow(0.9, step)) : 1.0f;
   const float c2 = adam ? (float)(1.0 - std::pow(0.999, step)) : 1.0f;
-  k_grad_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(gpart, (int)grid, grad, adam ? 1 : 0, params, m, v, lr,
-                                                      0.9f, 0.999f, 1e-8f, c1, c2, chained ? tiles : nullptr);
+  k_grad_adam<<<dim3((kNParam + 255) / 256, n_nets), 256, 0, st>>>(gpart, (int)grid, grad, adam ? 1 : 0, params,
+                                                                    m, v, lr, 0.9f, 0.999f, 1e-8f, c1, c2,
+                                                                    chained ? tiles : nullptr);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -909,20 +1124,22 @@ rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const f
 rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const float *inputs,
                          const float *targets, int64_t n, const rt_mlp_norm *nm, float lr, int32_t step,
                          int32_t flags, float *loss, uint32_t *status, cudaStream_t st) {
-  rt_status s = validate_train(params, m, v, grad, inputs, targets, n, nm, flags, loss);
+  rt_status s = validate_train(params, m, v, grad, inputs, targets, n, 1, nm, false, flags, loss);
   if (s != RT_OK) return s;
   if (!(flags & RT_MLP_GRAD_ONLY) && (step < 1 || !std::isfinite(lr) || lr < 0))
     return fail(RT_E_INVAL, "rt_mlp_train_step: step >= 1 and finite lr >= 0 required");
   Scratch scr;
-  s = scr.alloc(train_scratch_bytes(n), st);
+  s = scr.alloc(train_scratch_bytes(n, 1), st);
   if (s != RT_OK) return s;
-  return mlp_train_core(params, m, v, grad, inputs, targets, n, nm, lr, step, flags, loss, status,
-                        scr.as<char>(), false, st);
+  return mlp_train_core(params, m, v, grad, inputs, targets, n, n, 1, to_norm(nm), nullptr, lr, step, flags,
+                        loss, status, scr.as<char>(), false, st);
 }
 
+// n_steps steps of n_nets networks (one network: nm is a host norm; an ensemble: nm
+// is a device array of n_nets norms), inputs / targets [n_nets][n] rows
 rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, const float *inputs,
-                              const float *targets, int64_t n, int64_t batch, const rt_mlp_norm *nm,
-                              double lr0, double lr1, int32_t step_first, int32_t n_steps,
+                              const float *targets, int64_t n, int64_t batch, int n_nets, const rt_mlp_norm *nm,
+                              bool norm_on_device, double lr0, double lr1, int32_t step_first, int32_t n_steps,
                               int32_t total_steps, float *losses, uint32_t *status, cudaStream_t st) {
   if (!inputs || !targets) return fail(RT_E_INVAL, "rt_mlp_train_steps: NULL buffer");
   if (batch < 1 || batch > n) return fail(RT_E_INVAL, "rt_mlp_train_steps: batch must be in [1, n]");
@@ -932,19 +1149,23 @@ rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, c
                             "step_first - 1 + n_steps <= total_steps");
   if (!std::isfinite(lr0) || !std::isfinite(lr1) || lr0 < 0 || lr1 < 0)
     return fail(RT_E_INVAL, "rt_mlp_train_steps: finite learning rates >= 0 required");
+  if (n_nets < 1) return fail(RT_E_INVAL, "rt_mlp_train_steps_nets: n_nets must be >= 1");
   if (n_steps == 0) return RT_OK;
   // one scratch for all steps: the step's buffers, then a loss slot if none is given
-  const size_t sb = (train_scratch_bytes(batch) + 255) & ~size_t(255);
+  const size_t sb = (train_scratch_bytes(batch, n_nets) + 255) & ~size_t(255);
   Scratch scr;
   rt_status r = scr.alloc(sb + 256, st);
   if (r != RT_OK) return r;
   float *loss1 = reinterpret_cast<float *>(scr.as<char>() + sb);
-  r = validate_train(params, m, v, grad, inputs, targets, batch, nm, 0, losses ? losses : loss1);
+  r = validate_train(params, m, v, grad, inputs, targets, batch, n_nets, nm, norm_on_device, 0,
+                     losses ? losses : loss1);
   if (r != RT_OK) return r;
+  const Norm N1 = norm_on_device ? Norm{} : to_norm(nm);
+  const Norm *norms = norm_on_device ? reinterpret_cast<const Norm *>(nm) : nullptr;
   // the steps after the first take their BF16 tiles from the previous step's Adam
   // kernel, and a given loss buffer is zeroed once for all steps
   if (losses) RT_CUDA_TRY(cudaMemsetAsync(losses, 0, (size_t)n_steps * sizeof(float), st));
-  r = mlp_prep_tiles(params, scr.as<uint16_t>(), st);
+  r = mlp_prep_tiles(params, scr.as<uint16_t>(), n_nets, 6, st);
   if (r != RT_OK) return r;
   const int64_t nb = n / batch;
   const double span = (double)std::max(1, total_steps - 1);
@@ -953,32 +1174,40 @@ rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, c
     const int64_t b = s % nb;
     const double lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + std::cos(kPiD * (double)s / span));
     if (!losses) RT_CUDA_TRY(cudaMemsetAsync(loss1, 0, sizeof(float), st));
-    r = mlp_train_core(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, nm, (float)lr,
-                       (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, scr.as<char>(), true, st);
+    // every network's batch b: rows b * batch .. of its own n rows
+    r = mlp_train_core(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, n, n_nets, N1,
+                       norms, (float)lr, (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, scr.as<char>(),
+                       true, st);
     if (r != RT_OK) return r;
   }
   return RT_OK;
 }
 
-rt_status mlp_forward_impl(const float *params, const rt_mlp_norm *nm, const float *inputs, int64_t n,
-                           float *out, uint32_t *status, cudaStream_t st) {
+rt_status mlp_forward_impl(int n_nets, const float *params, const rt_mlp_norm *nm, bool norm_on_device,
+                           const float *inputs, int64_t n, float *out, uint32_t *status, cudaStream_t st) {
   if (n < 0) return fail(RT_E_INVAL, "rt_mlp_forward: n < 0");
+  if (n_nets < 1 || n_nets > 65535) return fail(RT_E_INVAL, "rt_mlp_forward_nets: n_nets must be in [1, 65535]");
   if (n == 0) return RT_OK;  // no sample: the buffers are not read and may be NULL
-  if (!params || !inputs || !out) return fail(RT_E_INVAL, "rt_mlp_forward: NULL buffer");
-  rt_status s = validate_norm(nm);
-  if (s != RT_OK) return s;
+  if (!params || !inputs || !out || !nm) return fail(RT_E_INVAL, "rt_mlp_forward: NULL buffer");
+  if (!norm_on_device) {
+    rt_status s = validate_norm(nm);
+    if (s != RT_OK) return s;
+  }
   static std::once_flag once;
   static rt_status attr = RT_OK;
   std::call_once(once, [] { attr = set_smem((const void *)k_mlp_fwd<false>, sizeof(FwdSmem)); });
   if (attr != RT_OK) return attr;
   Scratch scr;
-  s = scr.alloc(6 * (size_t)kTileBytes, st);
+  rt_status s = scr.alloc((size_t)n_nets * 3 * (size_t)kTileBytes, st);
   if (s != RT_OK) return s;
-  s = mlp_prep_tiles(params, scr.as<uint16_t>(), st);
+  s = mlp_prep_tiles(params, scr.as<uint16_t>(), n_nets, 3, st);
   if (s != RT_OK) return s;
   const unsigned grid = (unsigned)((n + kH - 1) / kH);
-  k_mlp_fwd<false><<<grid, kH, sizeof(FwdSmem), st>>>(params, scr.as<uint16_t>(), to_norm(nm), inputs,
-                                                      nullptr, n, nullptr, nullptr, nullptr, out, status);
+  const Norm N1 = norm_on_device ? Norm{} : to_norm(nm);
+  const Norm *norms = norm_on_device ? reinterpret_cast<const Norm *>(nm) : nullptr;
+  k_mlp_fwd<false><<<dim3(grid, n_nets), kH, sizeof(FwdSmem), st>>>(
+      params, scr.as<uint16_t>(), 3LL * kTileElems, N1, norms, inputs, nullptr, n, n, nullptr, nullptr, nullptr,
+      1.0f, out, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -995,6 +1224,76 @@ rt_status tc_selftest_impl(const float *A, const float *B, float *D, uint32_t *s
   return RT_OK;
 }
 
+// The surrogate walk over n_bands networks (band b serves j in [b band_pts, ..)):
+// params device [n_bands][RT_MLP_NPARAM], norms device [n_bands] (or N1 by value
+// for a single network with band_pts >= n_nu).
+rt_status trace_mlp_core(const rt_grid *grid, int band_pts, const float *params, const Norm &N1,
+                         const Norm *norms, const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays,
+                         uint64_t n_total, uint64_t seed, uint32_t enclosure, int32_t flags,
+                         const rt_tally_buf *tally, const rt_record *record, cudaStream_t st) {
+  WalkParams W;
+  RecordPtrs rp;
+  rt_status v = walk_setup(grid, spec, ray_begin, n_rays, n_total, seed, enclosure, flags, tally, record, &W, &rp);
+  if (v != RT_OK) return v;
+  if ((flags & 0xF) != RT_SRC_EMIT) return fail(RT_E_INVAL, "rt_trace_mlp: only RT_SRC_EMIT");
+  if (band_pts < 1) return fail(RT_E_INVAL, "rt_trace_mlp_bands: band_pts must be >= 1");
+  const long long nb_ll = (spec->n_nu + band_pts - 1) / band_pts;
+  if (nb_ll > 65535) return fail(RT_E_INVAL, "rt_trace_mlp_bands: at most 65535 bands (n_nu / band_pts)");
+  const int n_bands = (int)nb_ll;
+  if (n_bands > 1 && n_rays > 0xFFFFFFFFull)
+    return fail(RT_E_INVAL, "rt_trace_mlp_bands: at most 2^32 - 1 rays per call with several bands");
+  if (n_rays == 0) return RT_OK;
+  static std::once_flag once;
+  static rt_status attr = RT_OK;
+  std::call_once(once, [] { attr = set_smem((const void *)k_walk_mlp, sizeof(WalkMlpSmem)); });
+  if (attr != RT_OK) return attr;
+  int dev = 0, sms = 0;
+  RT_CUDA_TRY(cudaGetDevice(&dev));
+  RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned long long want = (n_rays + 8ull * kWalkMlpThreads - 1) / (8ull * kWalkMlpThreads);
+  const unsigned blocks = (unsigned)(want < (unsigned long long)sms ? (want > 0 ? want : 1) : sms);
+  // work items of about 1/8 of a block's share of the rays (at least 1024), so that
+  // the blocks finish together
+  const long long chunk = std::max(1024LL, (long long)(n_rays / (8ull * blocks)));
+  // scratch: the bands' BF16 hidden-layer tiles, the plan, the band-grouped ray order
+  const size_t tiles_b = (size_t)n_bands * 3 * kTileBytes;
+  const size_t plan_b = (((size_t)n_bands * 8 * 3 + 16 * 3 + 255) / 256) * 256;
+  const size_t order_b = n_bands > 1 ? (size_t)n_rays * sizeof(uint32_t) : 0;
+  Scratch scr;
+  v = scr.alloc(tiles_b + plan_b + order_b, st);
+  if (v != RT_OK) return v;
+  char *base = scr.as<char>();
+  uint16_t *tiles = reinterpret_cast<uint16_t *>(base);
+  unsigned long long *counts = reinterpret_cast<unsigned long long *>(base + tiles_b);  // then cursors
+  long long *band_start = reinterpret_cast<long long *>(counts + n_bands);
+  long long *item_start = band_start + (n_bands + 1);
+  unsigned long long *item_next = reinterpret_cast<unsigned long long *>(item_start + (n_bands + 1));
+  uint32_t *order = n_bands > 1 ? reinterpret_cast<uint32_t *>(base + tiles_b + plan_b) : nullptr;
+  v = mlp_prep_tiles(params, tiles, n_bands, 3, st);
+  if (v != RT_OK) return v;
+  RT_CUDA_TRY(cudaMemsetAsync(item_next, 0, sizeof(unsigned long long), st));
+  if (n_bands > 1) {
+    RT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)n_bands * sizeof(unsigned long long), st));
+    const unsigned gb = (unsigned)std::min<unsigned long long>((n_rays + 255) / 256, 8ull * (unsigned)sms);
+    k_band_count<<<gb, 256, 0, st>>>(W, band_pts, n_bands, counts);
+    RT_CUDA_TRY(cudaGetLastError());
+    // the counts are read by the plan, then the same words serve as the scatter cursors
+    k_band_plan<<<1, 1024, 0, st>>>(counts, n_bands, n_rays, chunk, band_start, item_start, counts);
+    RT_CUDA_TRY(cudaGetLastError());
+    k_band_scatter<<<gb, 256, 0, st>>>(W, band_pts, counts, order);
+    RT_CUDA_TRY(cudaGetLastError());
+  } else {
+    k_band_plan<<<1, 1024, 0, st>>>(nullptr, 1, n_rays, chunk, band_start, item_start, nullptr);
+    RT_CUDA_TRY(cudaGetLastError());
+  }
+  BandPlan B{order, band_start, item_start, item_next, chunk, n_bands};
+  k_walk_mlp<<<blocks, kWalkMlpThreads, sizeof(WalkMlpSmem), st>>>(
+      params, tiles, N1, norms, B, grid->T, grid->p_atm, grid->x, (float)spec->p_ref_atm, (float)spec->x_ref, W,
+      tally->absorbed, tally->scalars, tally->steps, tally->status, rp);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
 rt_status trace_mlp_impl(const rt_grid *grid, const float *params, const rt_mlp_norm *nm,
                          const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays, uint64_t n_total,
                          uint64_t seed, uint32_t enclosure, int32_t flags, const rt_tally_buf *tally,
@@ -1002,31 +1301,20 @@ rt_status trace_mlp_impl(const rt_grid *grid, const float *params, const rt_mlp_
   if (!params) return fail(RT_E_INVAL, "rt_trace_mlp: params is NULL");
   rt_status v = validate_norm(nm);
   if (v != RT_OK) return v;
-  WalkParams W;
-  RecordPtrs rp;
-  v = walk_setup(grid, spec, ray_begin, n_rays, n_total, seed, enclosure, flags, tally, record, &W, &rp);
-  if (v != RT_OK) return v;
-  if ((flags & 0xF) != RT_SRC_EMIT) return fail(RT_E_INVAL, "rt_trace_mlp: only RT_SRC_EMIT");
-  if (n_rays == 0) return RT_OK;
-  static std::once_flag once;
-  static rt_status attr = RT_OK;
-  std::call_once(once, [] { attr = set_smem((const void *)k_walk_mlp, sizeof(WalkMlpSmem)); });
-  if (attr != RT_OK) return attr;
-  Scratch scr;
-  v = scr.alloc(6 * (size_t)kTileBytes, st);
-  if (v != RT_OK) return v;
-  v = mlp_prep_tiles(params, scr.as<uint16_t>(), st);
-  if (v != RT_OK) return v;
-  int dev = 0, sms = 0;
-  RT_CUDA_TRY(cudaGetDevice(&dev));
-  RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned long long want = (n_rays + 8ull * kWalkMlpThreads - 1) / (8ull * kWalkMlpThreads);
-  const unsigned blocks = (unsigned)(want < (unsigned long long)sms ? (want > 0 ? want : 1) : sms);
-  k_walk_mlp<<<blocks, kWalkMlpThreads, sizeof(WalkMlpSmem), st>>>(
-      params, scr.as<uint16_t>(), to_norm(nm), grid->T, grid->p_atm, grid->x, (float)spec->p_ref_atm,
-      (float)spec->x_ref, W, tally->absorbed, tally->scalars, tally->steps, tally->status, rp);
-  RT_CUDA_TRY(cudaGetLastError());
-  return RT_OK;
+  if (!spec) return fail(RT_E_INVAL, "rt_trace_mlp: spec is NULL");
+  const long long pts = std::max<long long>(1, std::min<long long>(spec->n_nu, 0x7FFFFFFF));
+  return trace_mlp_core(grid, (int)pts, params, to_norm(nm), nullptr, spec, ray_begin, n_rays, n_total, seed,
+                        enclosure, flags, tally, record, st);
+}
+
+rt_status trace_mlp_bands_impl(const rt_grid *grid, int32_t band_pts, const float *params,
+                               const rt_mlp_norm *norms, const rt_spectral *spec, uint64_t ray_begin,
+                               uint64_t n_rays, uint64_t n_total, uint64_t seed, uint32_t enclosure, int32_t flags,
+                               const rt_tally_buf *tally, const rt_record *record, cudaStream_t st) {
+  if (!params || !norms) return fail(RT_E_INVAL, "rt_trace_mlp_bands: params or norms is NULL");
+  if (!spec) return fail(RT_E_INVAL, "rt_trace_mlp_bands: spec is NULL");
+  return trace_mlp_core(grid, band_pts, params, Norm{}, reinterpret_cast<const Norm *>(norms), spec, ray_begin,
+                        n_rays, n_total, seed, enclosure, flags, tally, record, st);
 }
 
 rt_status mlp_samples_impl(const float *tables, int32_t np, const float *p_nodes, const rt_spectral *spec,
@@ -1047,9 +1335,44 @@ rt_status mlp_samples_impl(const float *tables, int32_t np, const float *p_nodes
   return RT_OK;
 }
 
+rt_status mlp_samples_bands_impl(const float *tables, int32_t np, const float *p_nodes, const rt_spectral *spec,
+                                 int32_t band_pts, float x_lo, float x_hi, uint64_t seed, int64_t n, float *inputs,
+                                 float *targets, cudaStream_t st) {
+  rt_status v = validate_spec(spec);
+  if (v != RT_OK) return v;
+  if (!tables || !p_nodes || !inputs || !targets || np < 1 || n < 0 || band_pts < 1)
+    return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: bad arguments");
+  if (!(x_lo > 0) || !(x_hi >= x_lo)) return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: need 0 < x_lo <= x_hi");
+  const long long n_bands = (spec->n_nu + band_pts - 1) / band_pts;
+  if (n_bands > 65535) return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: at most 65535 bands");
+  if (n == 0) return RT_OK;
+  const float dT = spec->nT > 1 ? (float)((spec->T_max - spec->T_min) / (spec->nT - 1)) : 0.0f;
+  k_mlp_samples_bands<<<dim3((unsigned)((n + 255) / 256), (unsigned)n_bands), 256, 0, st>>>(
+      tables, np, spec->nT, spec->n_nu, p_nodes, (float)spec->T_min, dT, (float)spec->nu_min, (float)spec->dnu,
+      x_lo, x_hi, (float)spec->x_ref, (uint32_t)seed, (uint32_t)(seed >> 32), band_pts, n, inputs, targets);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
+
 }  // namespace rt
 
 extern "C" {
+
+rt_status rt_trace_mlp_bands(const rt_grid *grid, int32_t band_pts, const float *params,
+                             const rt_mlp_norm *norms, const rt_spectral *spec, uint64_t ray_begin,
+                             uint64_t n_rays, uint64_t n_rays_total, uint64_t seed, uint32_t enclosure,
+                             int32_t flags, const rt_tally_buf *tally, const rt_record *record, void *stream) {
+  return rt::trace_mlp_bands_impl(grid, band_pts, params, norms, spec, ray_begin, n_rays, n_rays_total, seed,
+                                  enclosure, flags, tally, record, (cudaStream_t)stream);
+}
+
+rt_status rt_mlp_make_samples_bands(const float *tables, int32_t n_p, const float *p_nodes,
+                                    const rt_spectral *spec, int32_t band_pts, float x_lo, float x_hi,
+                                    uint64_t seed, int64_t n_per_band, float *inputs, float *targets,
+                                    void *stream) {
+  return rt::mlp_samples_bands_impl(tables, n_p, p_nodes, spec, band_pts, x_lo, x_hi, seed, n_per_band, inputs,
+                                    targets, (cudaStream_t)stream);
+}
 
 rt_status rt_trace_mlp(const rt_grid *grid, const float *params, const rt_mlp_norm *norm,
                        const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays,
@@ -1080,13 +1403,28 @@ rt_status rt_mlp_train_steps(float *params, float *adam_m, float *adam_v, float 
                              const rt_mlp_norm *norm, double lr0, double lr1, int32_t step_first,
                              int32_t n_steps, int32_t total_steps, float *losses, uint32_t *status,
                              void *stream) {
-  return rt::mlp_train_steps_impl(params, adam_m, adam_v, grad, inputs, targets, n, batch, norm, lr0, lr1,
-                                  step_first, n_steps, total_steps, losses, status, (cudaStream_t)stream);
+  return rt::mlp_train_steps_impl(params, adam_m, adam_v, grad, inputs, targets, n, batch, 1, norm, false, lr0,
+                                  lr1, step_first, n_steps, total_steps, losses, status, (cudaStream_t)stream);
+}
+
+rt_status rt_mlp_train_steps_nets(int32_t n_nets, float *params, float *adam_m, float *adam_v, float *grad,
+                                  const float *inputs, const float *targets, int64_t n, int64_t batch,
+                                  const rt_mlp_norm *norms, double lr0, double lr1, int32_t step_first,
+                                  int32_t n_steps, int32_t total_steps, float *losses, uint32_t *status,
+                                  void *stream) {
+  return rt::mlp_train_steps_impl(params, adam_m, adam_v, grad, inputs, targets, n, batch, n_nets, norms, true,
+                                  lr0, lr1, step_first, n_steps, total_steps, losses, status,
+                                  (cudaStream_t)stream);
 }
 
 rt_status rt_mlp_forward(const float *params, const rt_mlp_norm *norm, const float *inputs,
                          int64_t n, float *out, uint32_t *status, void *stream) {
-  return rt::mlp_forward_impl(params, norm, inputs, n, out, status, (cudaStream_t)stream);
+  return rt::mlp_forward_impl(1, params, norm, false, inputs, n, out, status, (cudaStream_t)stream);
+}
+
+rt_status rt_mlp_forward_nets(int32_t n_nets, const float *params, const rt_mlp_norm *norms, const float *inputs,
+                              int64_t n, float *out, uint32_t *status, void *stream) {
+  return rt::mlp_forward_impl(n_nets, params, norms, true, inputs, n, out, status, (cudaStream_t)stream);
 }
 
 rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream) {
