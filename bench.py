@@ -237,7 +237,7 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
     step()
     torch.cuda.synchronize()
     walk_shape, walk_tune_ms = autotune.tune_walk(gs, grid.ncells, spec, kappa, min(n_rays, 10_000_000),
-                                                  use_cache=False)
+                                                  use_cache=False, n_rays_group=n_rays)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -282,7 +282,10 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
            # table copy, k_walk; k_reduce, k_final
            "gpu_launches": 9 * args.steps,
            "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
-                      "walk_candidates_ms": walk_tune_ms},
+                      "walk_group_by_wavenumber": walk_shape[2] == 2,
+                      "walk_candidates_ms": walk_tune_ms,
+                      "note": "blocks,refill timed on min(rays, 1e7) ungrouped; blocks,refill,group "
+                              "(1 off, 2 on) on the step's rays"},
            "clocks": clk.result}
 
     if e2e:
@@ -681,7 +684,8 @@ def run_surrogate(args):
             t0 = time.time()
             P_e, norms_e, hist_e = surrogate.train_bands(case.lines, spec, p_nodes, ex["train_x"][0],
                                                          ex["train_x"][1], band_pts=args.bands, n_per_band=n_per,
-                                                         batch=args.band_batch, steps=st_n, log_every=250)
+                                                         batch=args.band_batch, steps=st_n, lr0=args.band_lr,
+                                                         log_every=250)
             torch.cuda.synchronize()
             tr_s = time.time() - t0
             name = f"bands{args.bands}_s{st_n}"
@@ -700,7 +704,8 @@ def run_surrogate(args):
                 ens_best = (r_e, P_e, norms_e, name)
         r_e, P_e, norms_e, ens_name = ens_best
         ens = {"band_pts": args.bands, "n_bands": nbands, "networks_params": nbands * rt.RT_MLP_NPARAM,
-               "samples_per_band": n_per, "batch_per_band": args.band_batch, "error_curve": ens_curve,
+               "samples_per_band": n_per, "batch_per_band": args.band_batch, "lr0": args.band_lr,
+               "error_curve": ens_curve,
                "best": {"walk": ens_name, "median": r_e["median"], "max": r_e["max"]},
                "speedup_vs_lbl": walks[ens_name]["ray_cell_steps_per_s"] / walks["lbl"]["ray_cell_steps_per_s"],
                "meets_1pct_median": r_e["median"] <= 0.01, "meets_1pct_max": r_e["max"] <= 0.01,
@@ -951,7 +956,7 @@ def run_box128(args):
         ms_build = _ev_time(lambda: build(spec, kap), reps=args.steps)
     from paper_cs_0703028_gb300 import autotune
     walk_shape, walk_ms = autotune.tune_walk(gs, case.grid.ncells, spec, kap, min(n, 10_000_000),
-                                             use_cache=False)
+                                             use_cache=False, n_rays_group=n)
     t = rt.Tally(case.grid.ncells)
     t.zero()
     rt.trace(gs, kap, spec, t, n_rays=min(n, 10_000_000), n_rays_total=n)
@@ -971,7 +976,7 @@ def run_box128(args):
                                           torch.cuda.get_device_properties(0).multi_processor_count,
                                           _peaks().get("sm_max_mhz", 2070.0)),
            "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
-                      "walk_candidates_ms_1e7_rays": walk_ms},
+                      "walk_group_by_wavenumber": walk_shape[2] == 2, "walk_candidates_ms": walk_ms},
            "clocks": {"build": clk_b.result, "trace": clk_t.result},
            "pressure_reading_error_vs_lbl": pressure_reading_error(rt, case, kap)}
     print(json.dumps(res), flush=True)
@@ -993,8 +998,9 @@ def main():
     ap.add_argument("--objective", default="mse", choices=["mse"])
     ap.add_argument("--rays", type=int, default=50_000_000)
     ap.add_argument("--bands", type=int, default=64, help="wavenumbers per network of the ensemble (0: none)")
-    ap.add_argument("--band-steps", default="4000", help="comma-separated training steps (one ensemble each)")
-    ap.add_argument("--band-batch", type=int, default=1024)
+    ap.add_argument("--band-steps", default="16000", help="comma-separated training steps (one ensemble each)")
+    ap.add_argument("--band-batch", type=int, default=256)
+    ap.add_argument("--band-lr", type=float, default=3e-3)
     ap.add_argument("--rays-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.workload == "surrogate":

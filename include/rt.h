@@ -288,13 +288,19 @@ rt_status rt_trace_batch(int32_t n_encl, const rt_enclosure *encl, const float *
  * walk_blocks_per_sm = resident 256-thread blocks per SM the rt_trace walk is
  *   compiled for (4: 64 registers per thread, 5: 48; 0 = 5);
  * walk_refill_idle = idle lanes of a warp that trigger loading new rays in the
- *   rt_trace walk (12 or 16; 0 = 16).
+ *   rt_trace walk (12 or 16; 0 = 16);
+ * walk_group = rays of an rt_trace call grouped by wavenumber before the walk, so
+ *   that the lanes of a warp read one row of the table (a counting pass over the
+ *   rays' Philox draws; scratch of 4 bytes per ray + 8 per wavenumber): 1 never,
+ *   2 always, 0 = when there are at least 32 rays per wavenumber.  Tallies are
+ *   sums, so the grouping changes only their binary64 summation order.
  */
 typedef struct {
   int32_t kappa_t_per_block;
   int32_t walk_blocks_per_sm;
   int32_t walk_refill_idle;
-  int32_t reserved[5];
+  int32_t walk_group;
+  int32_t reserved[4];
 } rt_tuning;
 rt_status rt_set_tuning(const rt_tuning *t);
 rt_status rt_get_tuning(rt_tuning *t);

@@ -476,10 +476,10 @@ class rt_batch_opts(ct.Structure):
 
 class rt_tuning(ct.Structure):
     _fields_ = [("kappa_t_per_block", ct.c_int32), ("walk_blocks_per_sm", ct.c_int32),
-                ("walk_refill_idle", ct.c_int32), ("reserved", ct.c_int32 * 5)]
+                ("walk_refill_idle", ct.c_int32), ("walk_group", ct.c_int32), ("reserved", ct.c_int32 * 4)]
 
 
-_TUNING_FIELDS = ("kappa_t_per_block", "walk_blocks_per_sm", "walk_refill_idle")
+_TUNING_FIELDS = ("kappa_t_per_block", "walk_blocks_per_sm", "walk_refill_idle", "walk_group")
 
 
 def set_tuning(**shapes):

@@ -7,7 +7,8 @@ choice in a JSON file keyed by a signature of the workload's sizes
 
 * ``tune_kappa``: temperature nodes per rt_build_kappa block (1, 2, 4, 8).
 * ``tune_batch``: rays per work item and threads per block of the batched walk.
-* ``tune_walk``: resident blocks per SM (4 or 5) and refill threshold (12 or 16) of the rt_trace walk.
+* ``tune_walk``: resident blocks per SM (4 or 5) and refill threshold (12 or 16) of the rt_trace walk,
+  then whether grouping its rays by wavenumber pays.
 """
 from __future__ import annotations
 
@@ -99,24 +100,38 @@ def tune_batch(grids, n_rays, spec, kappa, candidates=None, reps=2, use_cache=Tr
     return (rpi, th), times
 
 
-def tune_walk(grid_struct, ncells, spec, kappa, n_rays, candidates=None, reps=2, use_cache=True):
-    """Pick the walk's (resident blocks per SM, refill threshold) on the caller's trace;
-    returns ((blocks, refill), {"blocks,refill": ms})."""
+def tune_walk(grid_struct, ncells, spec, kappa, n_rays, candidates=None, reps=2, use_cache=True,
+              n_rays_group=None):
+    """Pick the walk's (resident blocks per SM, refill threshold) on the caller's trace
+    (n_rays rays, no wavenumber grouping), then, with that shape, whether grouping the
+    rays by wavenumber pays on n_rays_group rays (default n_rays): grouping costs a
+    counting pass over the rays and gains only when many rays share each wavenumber.
+    Returns ((blocks, refill, group), {"blocks,refill[,group]": ms}) with group 1 (off)
+    or 2 (on) as rt_tuning.walk_group."""
     if candidates is None:
         candidates = [(b, r) for b in (4, 5) for r in (12, 16)]
-    key = f"walk:{ncells}:{spec.n_nu}:{spec.nT}:{int(n_rays)}"
+    ng = int(n_rays if n_rays_group is None else n_rays_group)
+    key = f"walk:{ncells}:{spec.n_nu}:{spec.nT}:{int(n_rays)}:{ng}"
     cached = _load().get(key) if use_cache else None
-    if cached and tuple(int(v) for v in cached["best"]) in [tuple(c) for c in candidates]:
-        b, r = (int(v) for v in cached["best"])   # a cached shape that is still a candidate
-        set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
-        return (b, r), cached["ms"]
+    if cached and tuple(int(v) for v in cached["best"][:2]) in [tuple(c) for c in candidates]:
+        b, r, g = (int(v) for v in cached["best"])   # a cached shape that is still a candidate
+        set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r, walk_group=g)
+        return (b, r, g), cached["ms"]
     tally = Tally(ncells)
     times = {}
+    set_tuning(walk_group=1)
     for b, r in candidates:
         set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
         times[f"{b},{r}"] = _time(lambda: (tally.zero(), trace(grid_struct, kappa, spec, tally, n_rays)), reps)
     best = min(times, key=times.get)
     b, r = (int(v) for v in best.split(","))
     set_tuning(walk_blocks_per_sm=b, walk_refill_idle=r)
-    _store(key, {"best": [b, r], "ms": times})
-    return (b, r), times
+    tg = {}
+    for g in (1, 2):
+        set_tuning(walk_group=g)
+        tg[g] = _time(lambda: (tally.zero(), trace(grid_struct, kappa, spec, tally, ng)), 1)
+        times[f"{b},{r},{g}"] = tg[g]
+    g = min(tg, key=tg.get)
+    set_tuning(walk_group=g)
+    _store(key, {"best": [b, r, g], "ms": times})
+    return (b, r, g), times

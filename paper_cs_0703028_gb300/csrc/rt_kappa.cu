@@ -1051,7 +1051,7 @@ extern "C" rt_status rt_build_kappa_static(const rt_lines *lines, const rt_spect
 }
 
 namespace rt {
-extern int g_walk_blocks, g_walk_refill;  // rt_trace.cu
+extern int g_walk_blocks, g_walk_refill, g_walk_group;  // rt_trace.cu
 }
 
 extern "C" rt_status rt_set_tuning(const rt_tuning *t) {
@@ -1062,9 +1062,11 @@ extern "C" rt_status rt_set_tuning(const rt_tuning *t) {
     return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_blocks_per_sm must be 0, 4 or 5");
   if (t->walk_refill_idle != 0 && t->walk_refill_idle != 12 && t->walk_refill_idle != 16)
     return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_refill_idle must be 0, 12 or 16");
+  if (t->walk_group < 0 || t->walk_group > 2) return rt::fail(RT_E_INVAL, "rt_set_tuning: walk_group must be 0, 1 or 2");
   rt::g_kappa_tpb = t->kappa_t_per_block == 0 ? 8 : t->kappa_t_per_block;
   rt::g_walk_blocks = t->walk_blocks_per_sm == 0 ? 5 : t->walk_blocks_per_sm;
   rt::g_walk_refill = t->walk_refill_idle == 0 ? 16 : t->walk_refill_idle;
+  rt::g_walk_group = t->walk_group;
   return RT_OK;
 }
 
@@ -1074,5 +1076,6 @@ extern "C" rt_status rt_get_tuning(rt_tuning *t) {
   t->kappa_t_per_block = rt::g_kappa_tpb;
   t->walk_blocks_per_sm = rt::g_walk_blocks;
   t->walk_refill_idle = rt::g_walk_refill;
+  t->walk_group = rt::g_walk_group;
   return RT_OK;
 }

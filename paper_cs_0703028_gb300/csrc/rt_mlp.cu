@@ -874,86 +874,6 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   }
 }
 
-// ---------------------------------------------------------------- band plan of a walk
-// The wavenumber index of ray rr (the draw ray_init makes: Philox call 0, word 1).
-__device__ __forceinline__ int ray_nu_index(const WalkParams &W, unsigned long long rr) {
-  const unsigned long long r = W.ray_begin + rr;
-  const u32x4 v = philox4x32_10(u32x4{(uint32_t)r, (uint32_t)(r >> 32), 0u, W.enclosure}, W.seed_lo, W.seed_hi);
-  return (int)(((unsigned long long)v.y * (unsigned long long)W.n_nu) >> 32);
-}
-
-constexpr int kBandHist = 8192;  // bands counted in a shared-memory histogram (else global atomics)
-
-// rays per band (counts zeroed before the launch)
-__global__ void k_band_count(WalkParams W, int band_pts, int n_bands, unsigned long long *__restrict__ counts) {
-  __shared__ unsigned int hist[kBandHist];
-  const bool local = n_bands <= kBandHist;
-  if (local)
-    for (int b = threadIdx.x; b < n_bands; b += blockDim.x) hist[b] = 0u;
-  __syncthreads();
-  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; rr < W.n_rays;
-       rr += (unsigned long long)gridDim.x * blockDim.x) {
-    const int b = ray_nu_index(W, rr) / band_pts;
-    if (local) atomicAdd(&hist[b], 1u);
-    else atomicAdd(&counts[b], 1ull);
-  }
-  __syncthreads();
-  if (local)
-    for (int b = threadIdx.x; b < n_bands; b += blockDim.x)
-      if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
-}
-
-// band_start and item_start (exclusive prefix sums over the bands; one block), the
-// scatter cursors; counts == nullptr: one band holding all n_rays rays
-__global__ void k_band_plan(const unsigned long long *__restrict__ counts, int n_bands, unsigned long long n_rays,
-                            long long chunk, long long *__restrict__ band_start, long long *__restrict__ item_start,
-                            unsigned long long *__restrict__ cursor) {
-  __shared__ long long sc[1024], si[1024];
-  const int t = threadIdx.x, nt = blockDim.x;
-  // each thread sums a contiguous run of bands, then the runs are scanned
-  const int per = (n_bands + nt - 1) / nt;
-  const int b0 = min(n_bands, t * per), b1 = min(n_bands, b0 + per);
-  long long c = 0, it = 0;
-  for (int b = b0; b < b1; ++b) {
-    const long long k = counts ? (long long)counts[b] : (long long)n_rays;
-    c += k;
-    it += (k + chunk - 1) / chunk;
-  }
-  sc[t] = c;
-  si[t] = it;
-  __syncthreads();
-  for (int o = 1; o < nt; o <<= 1) {  // inclusive scan of the runs (Hillis-Steele)
-    const long long a = t >= o ? sc[t - o] : 0, bi = t >= o ? si[t - o] : 0;
-    __syncthreads();
-    sc[t] += a;
-    si[t] += bi;
-    __syncthreads();
-  }
-  long long pc = sc[t] - c, pi = si[t] - it;
-  for (int b = b0; b < b1; ++b) {
-    const long long k = counts ? (long long)counts[b] : (long long)n_rays;
-    band_start[b] = pc;
-    item_start[b] = pi;
-    if (cursor) cursor[b] = (unsigned long long)pc;
-    pc += k;
-    pi += (k + chunk - 1) / chunk;
-  }
-  if (t == nt - 1) {
-    band_start[n_bands] = sc[t];
-    item_start[n_bands] = si[t];
-  }
-}
-
-// ray offsets into their band's run of order (order within a band: arrival order)
-__global__ void k_band_scatter(WalkParams W, int band_pts, unsigned long long *__restrict__ cursor,
-                               uint32_t *__restrict__ order) {
-  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; rr < W.n_rays;
-       rr += (unsigned long long)gridDim.x * blockDim.x) {
-    const int b = ray_nu_index(W, rr) / band_pts;
-    order[atomicAdd(&cursor[b], 1ull)] = (uint32_t)rr;
-  }
-}
-
 // Training samples drawn from line-by-line tables kappa[kp][kT][j] (x_ref mole
 // fraction): Philox counter (i, 0, 0, 0x6d6c70) under the seed picks the
 // wavenumber, temperature node, pressure node and a mole fraction in
@@ -1272,20 +1192,8 @@ rt_status trace_mlp_core(const rt_grid *grid, int band_pts, const float *params,
   v = mlp_prep_tiles(params, tiles, n_bands, 3, st);
   if (v != RT_OK) return v;
   RT_CUDA_TRY(cudaMemsetAsync(item_next, 0, sizeof(unsigned long long), st));
-  if (n_bands > 1) {
-    RT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)n_bands * sizeof(unsigned long long), st));
-    const unsigned gb = (unsigned)std::min<unsigned long long>((n_rays + 255) / 256, 8ull * (unsigned)sms);
-    k_band_count<<<gb, 256, 0, st>>>(W, band_pts, n_bands, counts);
-    RT_CUDA_TRY(cudaGetLastError());
-    // the counts are read by the plan, then the same words serve as the scatter cursors
-    k_band_plan<<<1, 1024, 0, st>>>(counts, n_bands, n_rays, chunk, band_start, item_start, counts);
-    RT_CUDA_TRY(cudaGetLastError());
-    k_band_scatter<<<gb, 256, 0, st>>>(W, band_pts, counts, order);
-    RT_CUDA_TRY(cudaGetLastError());
-  } else {
-    k_band_plan<<<1, 1024, 0, st>>>(nullptr, 1, n_rays, chunk, band_start, item_start, nullptr);
-    RT_CUDA_TRY(cudaGetLastError());
-  }
+  v = band_plan(W, band_pts, n_bands, chunk, counts, band_start, item_start, order, sms, st);
+  if (v != RT_OK) return v;
   BandPlan B{order, band_start, item_start, item_next, chunk, n_bands};
   k_walk_mlp<<<blocks, kWalkMlpThreads, sizeof(WalkMlpSmem), st>>>(
       params, tiles, N1, norms, B, grid->T, grid->p_atm, grid->x, (float)spec->p_ref_atm, (float)spec->x_ref, W,

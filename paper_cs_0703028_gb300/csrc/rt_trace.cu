@@ -10,6 +10,7 @@
 //                 persistent warps refilled by ballot.
 //   k_reduce / k_final : deterministic two-pass binary64 sum of the absorbed
 //                 power and the energy balance.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -39,10 +40,84 @@ __global__ void k_cell_prep(const float *__restrict__ T, const float *__restrict
 constexpr int kRefillIdleDefault = 16;
 constexpr int kWalkUnroll = 8;  // steps per pass of the walk loop
 
+// ---------------------------------------------------------------- grouping rays by wavenumber band
+constexpr int kBandHist = 8192;  // bands counted in a shared-memory histogram (else global atomics)
+
+// rays per band (counts zeroed before the launch)
+__global__ void k_band_count(WalkParams W, int band_pts, long long n_bands, unsigned long long *__restrict__ counts) {
+  __shared__ unsigned int hist[kBandHist];
+  const bool local = n_bands <= kBandHist;
+  if (local)
+    for (int b = threadIdx.x; b < (int)n_bands; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; rr < W.n_rays;
+       rr += (unsigned long long)gridDim.x * blockDim.x) {
+    const int b = ray_nu_index(W, rr) / band_pts;
+    if (local) atomicAdd(&hist[b], 1u);
+    else atomicAdd(&counts[b], 1ull);
+  }
+  __syncthreads();
+  if (local)
+    for (int b = threadIdx.x; b < (int)n_bands; b += blockDim.x)
+      if (hist[b]) atomicAdd(&counts[b], (unsigned long long)hist[b]);
+}
+
+// band_start and item_start (exclusive prefix sums over the bands; one block), the
+// scatter cursors; counts == nullptr: one band holding all n_rays rays
+__global__ void k_band_plan(const unsigned long long *__restrict__ counts, long long n_bands,
+                            unsigned long long n_rays, long long chunk, long long *__restrict__ band_start,
+                            long long *__restrict__ item_start, unsigned long long *__restrict__ cursor) {
+  __shared__ long long sc[1024], si[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  // each thread sums a contiguous run of bands, then the runs are scanned
+  const long long per = (n_bands + nt - 1) / nt;
+  const long long b0 = min(n_bands, (long long)t * per), b1 = min(n_bands, b0 + per);
+  long long c = 0, it = 0;
+  for (long long b = b0; b < b1; ++b) {
+    const long long k = counts ? (long long)counts[b] : (long long)n_rays;
+    c += k;
+    it += (k + chunk - 1) / chunk;
+  }
+  sc[t] = c;
+  si[t] = it;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {  // inclusive scan of the runs (Hillis-Steele)
+    const long long a = t >= o ? sc[t - o] : 0, bi = t >= o ? si[t - o] : 0;
+    __syncthreads();
+    sc[t] += a;
+    si[t] += bi;
+    __syncthreads();
+  }
+  long long pc = sc[t] - c, pi = si[t] - it;
+  for (long long b = b0; b < b1; ++b) {
+    const long long k = counts ? (long long)counts[b] : (long long)n_rays;
+    band_start[b] = pc;
+    item_start[b] = pi;
+    if (cursor) cursor[b] = (unsigned long long)pc;
+    pc += k;
+    pi += (k + chunk - 1) / chunk;
+  }
+  if (t == nt - 1) {
+    band_start[n_bands] = sc[t];
+    item_start[n_bands] = si[t];
+  }
+}
+
+// ray offsets into their band's run of order (order within a band: arrival order)
+__global__ void k_band_scatter(WalkParams W, int band_pts, unsigned long long *__restrict__ cursor,
+                               uint32_t *__restrict__ order) {
+  for (unsigned long long rr = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; rr < W.n_rays;
+       rr += (unsigned long long)gridDim.x * blockDim.x) {
+    const int b = ray_nu_index(W, rr) / band_pts;
+    order[atomicAdd(&cursor[b], 1ull)] = (uint32_t)rr;
+  }
+}
+
 }  // namespace
 
 int g_walk_blocks = 5;   // resident walk blocks per SM the launch is compiled for (4 or 5)
 int g_walk_refill = 16;  // idle lanes that trigger a refill (12 or 16)
+int g_walk_group = 0;    // rays grouped by wavenumber: 0 when >= 32 rays per wavenumber, 1 never, 2 always
 
 namespace {
 
@@ -86,8 +161,8 @@ __global__ void k_pair_table(const float *__restrict__ in, int nT, long long n_n
 
 template <bool REC, int TAB, int MINB, int REFILL>
 __global__ void __launch_bounds__(kWalkThreads, MINB)
-k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkParams W,
-       double *__restrict__ absorbed, double *__restrict__ scalars,
+k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, const uint32_t *__restrict__ order,
+       WalkParams W, double *__restrict__ absorbed, double *__restrict__ scalars,
        unsigned long long *__restrict__ steps_out, uint32_t *status, RecordPtrs rec) {
   const int lane = threadIdx.x & 31;
   const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
@@ -113,7 +188,9 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, WalkPara
     if (next < last && (idle == 0xffffffffu || __popc(idle) >= REFILL)) {
       const unsigned rank = __popc(idle & ((1u << lane) - 1u));
       if (!active && next + rank < last) {
-        ray_init(W, cells, tab, next + rank, record, R, &cd);
+        // order: the rays grouped by wavenumber, so that a warp's lanes share a table row
+        ray_init(W, cells, tab, order ? (unsigned long long)__ldg(order + next + rank) : next + rank, record, R,
+                 &cd);
         if (TAB == 2) krow = reinterpret_cast<const float2 *>(tab) + (long long)R.j * (W.nT - 1);
         if (TAB == 1) krow1 = tab + (long long)R.j * W.nT;
         active = true;
@@ -309,6 +386,28 @@ rt_status cell_prep(const rt_grid *grid, const rt_spectral *spec, float4 *cells,
   return RT_OK;
 }
 
+rt_status band_plan(const WalkParams &W, int band_pts, long long n_bands, long long chunk,
+                    unsigned long long *counts, long long *band_start, long long *item_start, uint32_t *order,
+                    int sms, cudaStream_t st) {
+  if (n_bands > 1) {
+    RT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)n_bands * sizeof(unsigned long long), st));
+    const unsigned gb = (unsigned)std::min<unsigned long long>((W.n_rays + 255) / 256, 8ull * (unsigned)sms);
+    k_band_count<<<gb, 256, 0, st>>>(W, band_pts, n_bands, counts);
+    RT_CUDA_TRY(cudaGetLastError());
+    // the counts are read by the plan, then the same words serve as the scatter cursors
+    k_band_plan<<<1, 1024, 0, st>>>(counts, n_bands, W.n_rays, chunk, band_start, item_start, counts);
+    RT_CUDA_TRY(cudaGetLastError());
+    if (order) {
+      k_band_scatter<<<gb, 256, 0, st>>>(W, band_pts, counts, order);
+      RT_CUDA_TRY(cudaGetLastError());
+    }
+  } else {
+    k_band_plan<<<1, 1024, 0, st>>>(nullptr, 1, W.n_rays, chunk, band_start, item_start, nullptr);
+    RT_CUDA_TRY(cudaGetLastError());
+  }
+  return RT_OK;
+}
+
 rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral *spec,
                      uint64_t ray_begin, uint64_t n_rays, uint64_t n_total, uint64_t seed,
                      uint32_t enclosure, int32_t flags, const rt_tally_buf *tally,
@@ -323,7 +422,14 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   Scratch scr;
   const int layout = walk_table_layout(spec->nT, spec->n_nu);
   const size_t cbytes = ((size_t)W.ncells * sizeof(float4) + 255) & ~size_t(255);
-  v = scr.alloc(cbytes + walk_table_bytes(layout, spec->nT, spec->n_nu), st);
+  const size_t tbytes = (walk_table_bytes(layout, spec->nT, spec->n_nu) + 255) & ~size_t(255);
+  // rays grouped by wavenumber (one band per wavenumber): counts, band and item starts, order
+  const bool group = n_rays <= 0xFFFFFFFFull &&
+                     (g_walk_group == 2 || (g_walk_group == 0 && n_rays >= 32ull * (unsigned long long)spec->n_nu));
+  const long long nb = spec->n_nu;
+  const size_t pbytes = group ? (((size_t)nb * 8 * 3 + 64 + 255) & ~size_t(255)) : 0;
+  const size_t obytes = group ? (size_t)n_rays * sizeof(uint32_t) : 0;
+  v = scr.alloc(cbytes + tbytes + pbytes + obytes, st);
   if (v != RT_OK) return v;
   float4 *cells = scr.as<float4>();
   float *tabw = reinterpret_cast<float *>(scr.as<char>() + cbytes);
@@ -335,6 +441,16 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   int dev = 0, sms = 0;
   RT_CUDA_TRY(cudaGetDevice(&dev));
   RT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  uint32_t *order = nullptr;
+  if (group) {
+    char *pb = scr.as<char>() + cbytes + tbytes;
+    unsigned long long *counts = reinterpret_cast<unsigned long long *>(pb);
+    long long *band_start = reinterpret_cast<long long *>(counts + nb);
+    long long *item_start = band_start + (nb + 1);
+    order = reinterpret_cast<uint32_t *>(pb + pbytes);
+    v = band_plan(W, 1, nb, 1LL << 40, counts, band_start, item_start, order, sms, st);
+    if (v != RT_OK) return v;
+  }
   const bool rec = rp.cells != nullptr;
   // visit recording (a test path) uses one configuration; the tuned shape otherwise
   auto pick = [&](auto tab) {
@@ -351,7 +467,7 @@ rt_status trace_impl(const rt_grid *grid, const float *kappa, const rt_spectral 
   unsigned long long want = (n_rays + 64ull * (kWalkThreads / 32) - 1) / (64ull * (kWalkThreads / 32));
   const unsigned long long cap = (unsigned long long)sms * (unsigned long long)per_sm;
   const unsigned blocks = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
-  kern<<<blocks, kWalkThreads, 0, st>>>(cells, tabw, W, tally->absorbed, tally->scalars, tally->steps,
+  kern<<<blocks, kWalkThreads, 0, st>>>(cells, tabw, order, W, tally->absorbed, tally->scalars, tally->steps,
                                         tally->status, rp);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;

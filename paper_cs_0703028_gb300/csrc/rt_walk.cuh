@@ -220,6 +220,14 @@ __device__ __forceinline__ void ray_init(const WalkParams &W, const float4 *__re
   R.nv = 0;
 }
 
+// The wavenumber index of ray rr: the draw ray_init makes (Philox call 0, word 1),
+// for grouping rays by wavenumber before a walk.
+__device__ __forceinline__ int ray_nu_index(const WalkParams &W, unsigned long long rr) {
+  const unsigned long long r = W.ray_begin + rr;
+  const u32x4 v = philox4x32_10(u32x4{(uint32_t)r, (uint32_t)(r >> 32), 0u, W.enclosure}, W.seed_lo, W.seed_hi);
+  return (int)(((unsigned long long)v.y * (unsigned long long)W.n_nu) >> 32);
+}
+
 // 1 - exp(-a) for a >= 0: below 1/4 its Taylor series to a^6 (truncation
 // < a^7/5040, relative 5e-8 of the result), above it 1 - exp(-a) with the
 // hardware exponential (relative error < 1.2e-6 at a = 1/4, falling with a).
@@ -342,6 +350,14 @@ size_t walk_table_bytes(int layout, int nT, long long n_nu);
 rt_status launch_walk_table(int layout, const float *tab, int nT, long long n_nu, float *out, cudaStream_t st);
 // Host: the CellParams of a spectral spec (table T grid, reference state).
 CellParams cell_params(const rt_spectral *spec, long long ncells, int has_px);
+// Host: rays [0, W.n_rays) grouped by band = (wavenumber index) / band_pts: per-band
+// counts (n_bands words, reused as scatter cursors), band_start and item_start
+// ([n_bands + 1]: first position of each band in the grouped order and first work
+// item of `chunk` rays), and, if order is given, the rays' offsets grouped by band
+// (within a band in arrival order).  One band: band_start = {0, n_rays}, no order.
+rt_status band_plan(const WalkParams &W, int band_pts, long long n_bands, long long chunk,
+                    unsigned long long *counts, long long *band_start, long long *item_start, uint32_t *order,
+                    int sms, cudaStream_t st);
 // Host: per-cell T bracket, density scale and T (float4 per cell).
 rt_status cell_prep(const rt_grid *grid, const rt_spectral *spec, float4 *cells, uint32_t *status,
                     cudaStream_t st);

@@ -54,7 +54,7 @@ def train_surrogate(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, n_samples=2_000_0
     lo, hi = input_ranges(spec, p_nodes, x_lo, x_hi)
     norm = make_norm(lo, hi, float(head.mean()), float(head.std()))
     if params is None:
-        params = torch.from_numpy(synth.mlp_init(seed)).cuda()
+        params = torch.from_numpy(synth.mlp_init(seed, spread_biases=True)).cuda()
     tr = MlpTrainer(params, norm)
     nb = n_samples // batch
     total = nb * epochs
@@ -106,8 +106,8 @@ def band_norms(spec, band_pts, p_nodes, x_lo, x_hi, targets):
     return norms_tensor(lo, hi, mean, scale, device=targets.device)
 
 
-def train_bands(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, band_pts=64, n_per_band=12800, batch=1024,
-                steps=4000, lr0=1e-3, lr1=1e-5, seed=0, group=2048, log_every=0):
+def train_bands(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, band_pts=64, n_per_band=12800, batch=256,
+                steps=16000, lr0=3e-3, lr1=1e-5, seed=0, group=2048, log_every=0):
     """Train a spectral-band ensemble on samples drawn from line-by-line tables: one
     network per band_pts wavenumbers, groups of up to `group` networks per library
     call.  Returns (params [n_bands * RT_MLP_NPARAM], norms [n_bands, 10], history)
@@ -121,7 +121,7 @@ def train_bands(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, band_pts=64, n_per_ba
     del tables
     nb = band_count(spec, band_pts)
     norms = band_norms(spec, band_pts, p_nodes, x_lo, x_hi, targets)
-    params = torch.from_numpy(synth.mlp_init(seed)).cuda().repeat(nb).contiguous()
+    params = torch.from_numpy(synth.mlp_init(seed, spread_biases=True)).cuda().repeat(nb).contiguous()
     hist = []
     for g0 in range(0, nb, group):
         g1 = min(nb, g0 + group)

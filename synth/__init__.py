@@ -284,13 +284,23 @@ def mlp_offsets():
     return out
 
 
-def mlp_init(seed: int = 0) -> np.ndarray:
-    """Flat float32 initial parameters: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0."""
+def mlp_init(seed: int = 0, spread_biases: bool = False) -> np.ndarray:
+    """Flat float32 initial parameters: W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)); biases 0,
+    or with spread_biases also U(-1/sqrt(fan_in), 1/sqrt(fan_in)) (the first layer's
+    kinks then lie at different points of the input range instead of all at its
+    centre, which speeds up fitting a spectrum's lines)."""
     rng = np.random.default_rng([0, 2, 100 + int(seed)])
     flat = np.zeros(MLP_NPARAM, dtype=np.float32)
+    fan = {"b1": 4, "b2": 128, "b3": 128, "b4": 128, "b5": 128}
     for name, (off, shape) in mlp_offsets().items():
+        n = int(np.prod(shape))
         if name.startswith("W") or name == "w5":
             fan_in = shape[-1] if len(shape) == 2 else shape[0]
-            n = int(np.prod(shape))
             flat[off:off + n] = rng.uniform(-1, 1, n).astype(np.float32) / np.float32(np.sqrt(fan_in))
+    if spread_biases:
+        rb = np.random.default_rng([0, 2, 200 + int(seed)])
+        for name, (off, shape) in mlp_offsets().items():
+            if name in fan:
+                n = int(np.prod(shape))
+                flat[off:off + n] = rb.uniform(-1, 1, n).astype(np.float32) / np.float32(np.sqrt(fan[name]))
     return flat

@@ -109,16 +109,19 @@ def test_tuning_round_trip_and_validation():
     # launch shapes only; the calls touch no device
     before = rt.get_tuning()
     try:
-        rt.set_tuning(kappa_t_per_block=4, walk_blocks_per_sm=4, walk_refill_idle=12)
-        assert rt.get_tuning() == {"kappa_t_per_block": 4, "walk_blocks_per_sm": 4, "walk_refill_idle": 12}
+        rt.set_tuning(kappa_t_per_block=4, walk_blocks_per_sm=4, walk_refill_idle=12, walk_group=2)
+        assert rt.get_tuning() == {"kappa_t_per_block": 4, "walk_blocks_per_sm": 4, "walk_refill_idle": 12,
+                                   "walk_group": 2}
         rt.set_tuning(walk_refill_idle=16)  # other fields keep their value
-        assert rt.get_tuning()["walk_blocks_per_sm"] == 4
-        for bad in ({"kappa_t_per_block": 9}, {"walk_blocks_per_sm": 3}, {"walk_refill_idle": 8}):
+        assert rt.get_tuning()["walk_blocks_per_sm"] == 4 and rt.get_tuning()["walk_group"] == 2
+        for bad in ({"kappa_t_per_block": 9}, {"walk_blocks_per_sm": 3}, {"walk_refill_idle": 8},
+                    {"walk_group": 3}):
             with pytest.raises(rt.RtError):
                 rt.set_tuning(**bad)
         with pytest.raises(TypeError):
             rt.set_tuning(rays_per_block=1)
-        rt.set_tuning(kappa_t_per_block=0, walk_blocks_per_sm=0, walk_refill_idle=0)  # defaults
-        assert rt.get_tuning() == {"kappa_t_per_block": 8, "walk_blocks_per_sm": 5, "walk_refill_idle": 16}
+        rt.set_tuning(kappa_t_per_block=0, walk_blocks_per_sm=0, walk_refill_idle=0, walk_group=0)  # defaults
+        assert rt.get_tuning() == {"kappa_t_per_block": 8, "walk_blocks_per_sm": 5, "walk_refill_idle": 16,
+                                   "walk_group": 0}
     finally:
         rt.set_tuning(**before)

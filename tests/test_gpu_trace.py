@@ -212,3 +212,50 @@ def test_c1_ray_subset_tallies(rt):
     _check_tally(ab, o.absorbed, o.emitted)
     assert steps == o.steps
     assert sc[0] == pytest.approx(o.emitted, rel=1e-5)
+
+
+def _with_group(rt, mode, fn):
+    before = rt.get_tuning()
+    try:
+        rt.set_tuning(walk_group=mode)
+        return fn()
+    finally:
+        rt.set_tuning(**before)
+
+
+def test_wavenumber_grouped_walk_matches_oracle(rt):
+    # The walk over rays grouped by wavenumber (walk_group = 2: counting pass over the
+    # rays' Philox draws, warps walk runs of equal-wavenumber rays) traces the same
+    # rays: per-cell tallies against the oracle at 1e-4, against the ungrouped walk up
+    # to the binary64 summation order, the same step count.
+    case = synth.config(1)
+    kap = rt.build_kappa(case.lines, case.spec)
+    n = 1500
+    ab_g, sc_g, st_g, _ = _with_group(rt, 2, lambda: _run(rt, case.grid, case.spec, kap, n, n_total=case.n_rays))
+    ab_u, sc_u, st_u, _ = _with_group(rt, 1, lambda: _run(rt, case.grid, case.spec, kap, n, n_total=case.n_rays))
+    o = otrace.trace_case(case, n_rays=n)
+    _check_tally(ab_g, o.absorbed, o.emitted)
+    assert st_g == o.steps == st_u
+    assert np.allclose(ab_g, ab_u, rtol=1e-12, atol=1e-13 * ab_u.max())
+    assert sc_g[0] == pytest.approx(sc_u[0], rel=1e-12)
+
+
+def test_wavenumber_grouped_walk_records_bit_exact_visits(rt):
+    # record rows follow the ray's index, whatever order the grouped walk takes the rays in;
+    # many rays per wavenumber (n_nu = 64): the grouping runs through its shared histogram
+    import torch
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.5, n_nu=64, cutoff=25.0, profile="voigt", nT=13,
+                          T_min=800.0, T_max=2000.0)
+    g = synth.gaussian_hotspot_grid(12, 1.0, 800.0, 2000.0, 0.2, dims=(12, 9, 7))
+    K = np.full((spec.nT, spec.n_nu), 2e-3)
+    kd = torch.full((spec.nT, spec.n_nu), 2e-3, dtype=torch.float32, device="cuda")
+    n = 8000
+    ab, sc, steps, rec = _with_group(rt, 2, lambda: _run(rt, g, spec, kd, n, seed=3, rec_n=n))
+    o = otrace.trace(g, spec, K, seed=3, n_rays=n, n_record=n)
+    nv = rec.n_visits.cpu().numpy()
+    assert np.array_equal(nv, o.rec["n"])
+    cells = rec.cells.cpu().numpy()
+    mask = np.arange(cells.shape[1])[None, :] < nv[:, None]
+    assert np.array_equal(cells[mask], o.rec["cells"][mask])
+    assert np.array_equal(rec.ds.cpu().numpy()[mask].view(np.uint32), o.rec["ds"][mask].view(np.uint32))
+    _check_tally(ab, o.absorbed, o.emitted)
