@@ -279,8 +279,9 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
            "kernels_ms": {"rt_build_kappa": ms_build, "rt_trace": ms_trace},
            "energy_residual": energy_residual,
            # per step: k_line_geometry, k_prefactor, k_tile_lines, k_kappa; k_cell_prep, walk
-           # table copy, k_walk; k_reduce, k_final
-           "gpu_launches": 9 * args.steps,
+           # table copy, [k_band_count, k_band_plan, k_band_scatter when the rays are grouped by
+           # wavenumber], k_walk; k_reduce, k_final
+           "gpu_launches": (9 + (3 if walk_shape[2] == 2 else 0)) * args.steps,
            "tuning": {"walk_blocks_per_sm": walk_shape[0], "walk_refill_idle": walk_shape[1],
                       "walk_group_by_wavenumber": walk_shape[2] == 2,
                       "walk_candidates_ms": walk_tune_ms,
@@ -334,19 +335,25 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
         cut = rt.Tally(grid.ncells)
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
-        for rep in range(2):
-            cut.zero()
-            c0.record(stream)
-            st = L.rt_trace(ct.byref(gs), ct.c_void_p(kappa.data_ptr()), ct.byref(S), ray_begin, n_rays,
-                            n_total, case.seed, 0, rt.RT_TAU_CUT, ct.byref(cut.buf), None, sp)
-            c1.record(stream)
-            if st:
-                raise rt.RtError(st, "rt_trace (tau cut)", L.rt_last_error().decode())
-        torch.cuda.synchronize()
+        tuned = rt.get_tuning()
+        cut_by_group = {}
+        for g in (1, 2):   # the cut walk is short: time it with and without the wavenumber grouping
+            rt.set_tuning(walk_group=g)
+            for rep in range(2):
+                cut.zero()
+                c0.record(stream)
+                st = L.rt_trace(ct.byref(gs), ct.c_void_p(kappa.data_ptr()), ct.byref(S), ray_begin, n_rays,
+                                n_total, case.seed, 0, rt.RT_TAU_CUT, ct.byref(cut.buf), None, sp)
+                c1.record(stream)
+                if st:
+                    raise rt.RtError(st, "rt_trace (tau cut)", L.rt_last_error().decode())
+            torch.cuda.synchronize()
+            cut_by_group[g] = c0.elapsed_time(c1)
+        rt.set_tuning(**tuned)
         if world > 1:
             shard.combine_tally(cut)
         _, cut_sc, _ = cut.read()
-        cut_ms = c0.elapsed_time(c1)
+        cut_ms = min(cut_by_group.values())
         cut_steps = int(cut.steps.item())
         out["trace_with_tau_cut"] = {
             "trace_ms": cut_ms, "ray_cell_steps": cut_steps,
@@ -354,7 +361,9 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
             "rays_per_s": n_rays * world / (cut_ms * 1e-3),
             "rays_per_s_without_cut": n_rays * world / (ms_trace * 1e-3),
             "absorbed_total_rel_diff": abs(float(cut_sc[1]) - float(host_sc[1])) / float(host_sc[1]),
-            "note": "steps after tau > 100 skipped and not counted (transmission below 4e-44)"}
+            "trace_ms_by_grouping": {"off": cut_by_group[1], "on": cut_by_group[2]},
+            "note": "steps after tau > 100 skipped and not counted (transmission below 4e-44); "
+                    "the faster of the two groupings"}
 
     if rank != 0:
         return None
@@ -390,8 +399,9 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    main = hot_path_line(4, args, world, rank, local)
-    small = hot_path_line(1, args, world, rank, local, e2e=False)
+    order = [int(c) for c in str(args.configs).split(",")]
+    main = hot_path_line(order[0], args, world, rank, local)
+    small = hot_path_line(order[1], args, world, rank, local, e2e=False) if len(order) > 1 else None
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -411,12 +421,13 @@ def run_gpu(args):
         "data": "synthetic (seeded line list, random smooth T and p fields; no HITRAN data)",
         **main,
     }
-    out["gpu_launches"] += small["gpu_launches"]
-    out["box32"] = small
+    if small is not None:
+        out["gpu_launches"] += small["gpu_launches"]
+        out["box32" if order[1] == 1 else "box128"] = small
     if world == 1 and not args.no_surrogate:
         out["surrogate"] = surrogate_summary(args)
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(synth.config(4), out["profile_evals_per_step"],
+        out["cpu_baseline"] = cpu_baseline(synth.config(order[0]), out["profile_evals_per_step"],
                                            out["ray_cell_steps_per_step"], budget_s=args.cpu_seconds)
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -957,6 +968,9 @@ def run_box128(args):
     from paper_cs_0703028_gb300 import autotune
     walk_shape, walk_ms = autotune.tune_walk(gs, case.grid.ncells, spec, kap, min(n, 10_000_000),
                                              use_cache=False, n_rays_group=n)
+    if args.walk_group != "tune":   # the tuner's grouping choice overridden (profiling)
+        rt.set_tuning(walk_group=1 if args.walk_group == "off" else 2)
+        walk_shape = (walk_shape[0], walk_shape[1], 1 if args.walk_group == "off" else 2)
     t = rt.Tally(case.grid.ncells)
     t.zero()
     rt.trace(gs, kap, spec, t, n_rays=min(n, 10_000_000), n_rays_total=n)
@@ -982,6 +996,77 @@ def run_box128(args):
     print(json.dumps(res), flush=True)
 
 
+def run_surrogate128(args):
+    """The learned part on the 128^3 workload: a spectral-band ensemble trained on that
+    workload's line-by-line tables (16 log-spaced pressures 0.5-5 atm x 64 T nodes x
+    400k wavenumbers), walked against the table on the same rays; on a ray subset all
+    three walks (table, ensemble, on-the-fly line by line at each cell's own T, p, x)
+    against the line-by-line one, which carries the p field exactly."""
+    import torch
+    import paper_cs_0703028_gb300 as rt
+    from paper_cs_0703028_gb300 import surrogate
+    case = synth.config(4)
+    spec, lines, g = case.spec, case.lines, case.grid
+    n = int(case.n_rays * args.rays_scale)
+    n_sub = max(1, min(n, args.lbl_rays))
+    p_nodes = np.exp(np.linspace(np.log(0.5), np.log(5.0), 16))
+    gs, keep = rt.make_grid(g)
+    kap = rt.build_kappa(lines, spec)
+    nbands = surrogate.band_count(spec, args.bands)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    P, norms, hist = surrogate.train_bands(lines, spec, p_nodes, 0.01, 0.3, band_pts=args.bands,
+                                           n_per_band=args.band_samples, batch=args.band_batch,
+                                           steps=int(str(args.band_steps).split(",")[-1]), lr0=args.band_lr,
+                                           group=65535, log_every=500)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    walks, tallies = {}, {}
+
+    def timed(name, fn, rays, flags=0):
+        t = rt.Tally(g.ncells)
+        t.zero()
+        fn(t, rays, flags)
+        torch.cuda.synchronize()
+        t.zero()
+        with ClockWindow(0) as clk:
+            ms = _ev_time(lambda: fn(t, rays, flags))
+        ab, sc, _ = t.read()
+        st = int(t.steps.item())
+        walks[name] = {"rays": rays, "ms": ms, "steps": st, "ray_cell_steps_per_s": st / (ms * 1e-3),
+                       "energy_residual": float(sc[3]), "clocks": clk.result}
+        return ab
+
+    table = lambda t, m, f: rt.trace(gs, kap, spec, t, n_rays=m, n_rays_total=m, flags=f)
+    ens = lambda t, m, f: rt.trace_mlp_bands(gs, args.bands, P, norms, spec, t, n_rays=m, n_rays_total=m, flags=f)
+    lbl = lambda t, m, f: rt.trace_lbl(gs, lines, spec, t, n_rays=m, n_rays_total=m, flags=f)
+    tallies["table"] = timed("table", table, n)
+    tallies["ensemble"] = timed("ensemble", ens, n)
+    timed("table_tau_cut", table, n, rt.RT_TAU_CUT)
+    timed("ensemble_tau_cut", ens, n, rt.RT_TAU_CUT)
+    sub = {k: timed(k + "_subset", f, n_sub) for k, f in (("table", table), ("ensemble", ens), ("lbl", lbl))}
+
+    def err(got, ref):
+        big = ref >= 1e-3 * ref.max()
+        e = np.abs(got[big] - ref[big]) / ref[big]
+        return {"median": float(np.median(e)), "p90": float(np.percentile(e, 90)),
+                "p99": float(np.percentile(e, 99)), "max": float(e.max()), "cells": int(big.sum()),
+                "frac_cells_within_1pct": float(np.mean(e <= 0.01)), "total": float(got.sum() / ref.sum() - 1.0)}
+    res = {"metric": "ray-cell steps/s, spectral-band ensemble walk vs table and line-by-line walks",
+           "value": walks["ensemble"]["ray_cell_steps_per_s"], "unit": "ray-cell steps/s", "higher_is_better": True,
+           "config": {"workload": f"box128 learned part: 128^3, 100k Voigt lines, 64 T x 400k nu, {n} rays "
+                                  f"(all three walks on {n_sub}); ensemble of {nbands} networks x {args.bands} "
+                                  f"wavenumbers, {args.band_samples} samples per band (16 p x 64 T tables)"},
+           "training": {"seconds": train_s, "steps": hist[-1][0] + 1 if hist else 0,
+                        "loss_first": hist[0][1] if hist else None, "loss_last": hist[-1][1] if hist else None,
+                        "batch_per_band": args.band_batch, "lr0": args.band_lr},
+           "walks": walks,
+           "ensemble_vs_table": err(tallies["ensemble"], tallies["table"]),
+           "subset_vs_lbl": {"table": err(sub["table"], sub["lbl"]), "ensemble": err(sub["ensemble"], sub["lbl"])},
+           "speedup_vs_lbl": walks["ensemble_subset"]["ray_cell_steps_per_s"] / walks["lbl_subset"]["ray_cell_steps_per_s"]}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -991,7 +1076,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--workload", default="step", choices=["step", "surrogate", "batched", "box128", "next"],
+    ap.add_argument("--workload", default="step",
+                    choices=["step", "surrogate", "surrogate128", "batched", "box128", "next"],
                     help="step: the benchmark line (128^3 step, 32^3 step, surrogate, oracle baseline)")
     ap.add_argument("--samples", type=int, default=20_000_000)
     ap.add_argument("--epochs", default="1,8,32", help="comma-separated epoch counts (one network each)")
@@ -1001,10 +1087,17 @@ def main():
     ap.add_argument("--band-steps", default="16000", help="comma-separated training steps (one ensemble each)")
     ap.add_argument("--band-batch", type=int, default=256)
     ap.add_argument("--band-lr", type=float, default=3e-3)
+    ap.add_argument("--band-samples", type=int, default=12800, help="samples per band (128^3 learned part)")
+    ap.add_argument("--configs", default="4,1", help="step line: main workload index[,extra workload index]")
+    ap.add_argument("--walk-group", default="tune", choices=["tune", "off", "on"],
+                    help="box128 workload: wavenumber grouping of the walk's rays (tune: the tuner decides)")
+    ap.add_argument("--lbl-rays", type=int, default=10_000_000, help="rays of the three-walk subset (128^3)")
     ap.add_argument("--rays-scale", type=float, default=1.0)
     args = ap.parse_args()
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "surrogate128":
+        return run_surrogate128(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "box128":
