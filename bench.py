@@ -714,7 +714,13 @@ def run_surrogate(args):
             if ens_best is None or r_e["median"] < ens_best[0]["median"]:
                 ens_best = (r_e, P_e, norms_e, name)
         r_e, P_e, norms_e, ens_name = ens_best
+        # tensor-core work of the ensemble's training: every step trains every band's network
+        # on a batch (forward + two backward products per layer and sample)
+        ens_tf = r_e["steps"] * nbands * args.band_batch * 3 * (3 * 2 * 128 * 128) / r_e["train_s"] / 1e12
         ens = {"band_pts": args.bands, "n_bands": nbands, "networks_params": nbands * rt.RT_MLP_NPARAM,
+               "training_tflops": ens_tf,
+               "training_frac": ens_tf / _peaks().get("bf16_tflops", 1978.3),
+               "training_note": "wall clock of train_bands incl. tables and sampling; measured bf16 burst peak",
                "samples_per_band": n_per, "batch_per_band": args.band_batch, "lr0": args.band_lr,
                "error_curve": ens_curve,
                "best": {"walk": ens_name, "median": r_e["median"], "max": r_e["max"]},
