@@ -9,8 +9,20 @@ spectral grid is nu_j = nu_min + j * dnu evaluated in float64, and the cutoff
 test |nu_j - nu0| <= cutoff is applied in float64 exactly as written (edge
 inclusive, no renormalisation of the truncated profile, no pedestal).
 
+With spec.kappa_min > 0 the points per line adapt to the temperature and the
+line's intensity (the next version Section 4 announces: "dynamically adapt the
+number of points depending on the local temperature and the intensity of the
+line"; the paper gives no rule).  Reading: at T node T_k, line l is evaluated
+only where its Lorentz wing reaches kappa_min,
+    |nu_j - nu0_l| <= w_lk = min(cutoff, sqrt(A_lk gamma_lk / (pi kappa_min))),
+A_lk = u(T_k) S_l(T_k) and gamma_lk the Lorentz half-width at T_k (the distance at
+which A gamma / (pi dnu^2), the far wing of both profiles, equals kappa_min);
+w_lk and the test are float64.
+
 Parity: pinned (single-line area against closed forms, superposition over
-lines, direct evaluation at each temperature node).
+lines, direct evaluation at each temperature node; adaptive windows: the cutoff
+table as kappa_min -> 0, every dropped Lorentz term below kappa_min and every
+kept one's wing at or above it, monotone in kappa_min).
 """
 from __future__ import annotations
 
@@ -69,6 +81,12 @@ def _pairs(lines, spec, js):
     return col[keep], lid[keep], dnu[keep]
 
 
+def adaptive_halfwidth(A, gamma, spec):
+    """w = min(cutoff, sqrt(A gamma / (pi kappa_min))) per line [cm^-1] (adaptive points)."""
+    w = np.sqrt(A * gamma / (np.pi * spec.kappa_min))
+    return np.where(w <= spec.cutoff, w, spec.cutoff)
+
+
 def kappa_columns(lines, spec, js, T_nodes=None, p_atm=None, x=None, chunk=512):
     """kappa[k, i] at columns js[i] and temperatures T_nodes[k] (default: the
     spec's T grid at its p_ref, x_ref).  Returns (nT, len(js)) float64."""
@@ -78,6 +96,8 @@ def kappa_columns(lines, spec, js, T_nodes=None, p_atm=None, x=None, chunk=512):
     x = spec.x_ref if x is None else x
     out = np.zeros((len(T_nodes), len(js)), dtype=np.float64)
     terms = [line_terms(lines, float(T), p_atm, x, spec.profile) for T in T_nodes]
+    adaptive = getattr(spec, "kappa_min", 0.0) > 0
+    wins = [adaptive_halfwidth(A, g, spec) for A, g, _ in terms] if adaptive else None
     for c0 in range(0, len(js), chunk):
         sl = slice(c0, min(len(js), c0 + chunk))
         col, lid, dnu = _pairs(lines, spec, js[sl])
@@ -89,7 +109,10 @@ def kappa_columns(lines, spec, js, T_nodes=None, p_atm=None, x=None, chunk=512):
                 f = ph.lorentz_profile(dnu, g[lid])
             else:
                 f = ph.voigt_profile(dnu, g[lid], a[lid])
-            out[k, sl] = np.bincount(col, weights=A[lid] * f, minlength=n)
+            wt = A[lid] * f
+            if adaptive:   # the line's own window at this node
+                wt = np.where(np.abs(dnu) <= wins[k][lid], wt, 0.0)
+            out[k, sl] = np.bincount(col, weights=wt, minlength=n)
     return out
 
 
@@ -121,7 +144,42 @@ def line_ranges(lines, spec):
     return lo, hi
 
 
+def window_range(lines, spec, w):
+    """Inclusive grid-index range [j_lo, j_hi] of |nu_j - nu0_l| <= w_l (float64 test)."""
+    nu0 = lines.nu0
+    n = spec.n_nu
+    lo = np.floor((nu0 - w - spec.nu_min) / spec.dnu).astype(np.int64) - 1
+    hi = np.ceil((nu0 + w - spec.nu_min) / spec.dnu).astype(np.int64) + 1
+    lo = np.clip(lo, 0, n)
+    hi = np.clip(hi, -1, n - 1)
+
+    def inc(j):
+        ok = (j >= 0) & (j < n)
+        return ok & (np.abs(grid_nu(spec, np.clip(j, 0, n - 1)) - nu0) <= w)
+
+    for _ in range(6):
+        lo = np.where((lo <= hi) & ~inc(lo), lo + 1, lo)
+    for _ in range(6):
+        hi = np.where((hi >= lo) & ~inc(hi), hi - 1, hi)
+    return lo, hi
+
+
+def adaptive_ranges(lines, spec):
+    """Per T node k, the grid-index range of each line's adaptive window: (lo, hi),
+    each of shape (nT, n_lines)."""
+    los, his = [], []
+    for T in spec.T_nodes():
+        A, g, _ = line_terms(lines, float(T), spec.p_ref_atm, spec.x_ref, "lorentz")
+        lo, hi = window_range(lines, spec, adaptive_halfwidth(A, g, spec))
+        los.append(lo)
+        his.append(hi)
+    return np.stack(los), np.stack(his)
+
+
 def profile_evals(lines, spec):
     """Exact number of (T node, line, nu_j) profile evaluations of the table."""
+    if getattr(spec, "kappa_min", 0.0) > 0:
+        lo, hi = adaptive_ranges(lines, spec)
+        return int(np.maximum(hi - lo + 1, 0).sum())
     lo, hi = line_ranges(lines, spec)
     return int(np.maximum(hi - lo + 1, 0).sum()) * int(spec.nT)

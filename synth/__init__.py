@@ -72,6 +72,7 @@ class Spectral:
     x_ref: float = 0.1       # table absorber mole fraction
     points_per_line: int = 0  # > 0: fixed number of grid points per line instead of the cutoff
     accumulate: int = 0       # add into an existing table (one build per absorbing gas)
+    kappa_min: float = 0.0    # > 0: adaptive points per line, each line evaluated where its wing >= kappa_min
 
     @property
     def nu_max(self) -> float:

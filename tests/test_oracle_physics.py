@@ -212,3 +212,65 @@ def test_fixed_points_per_line_window():
     tab = K.kappa_table(case.lines, spec)[0]
     assert K.profile_evals(case.lines, spec) == int(np.sum(hi - lo + 1))
     assert np.count_nonzero(tab) <= 500 * 16
+
+
+def _adaptive_case(profile="lorentz", kappa_min=1e-3):
+    from dataclasses import replace
+    rng = synth.rng_for(9, 60)
+    lines = synth.make_lines(400, 2000.0, 2040.0, rng)
+    spec = synth.Spectral(nu_min=2005.0, dnu=0.01, n_nu=3001, cutoff=25.0, profile=profile, nT=4,
+                          T_min=700.0, T_max=1900.0, p_ref_atm=1.5, x_ref=0.08)
+    return lines, spec, replace(spec, kappa_min=kappa_min)
+
+
+def test_adaptive_points_reduce_to_the_cutoff_table():
+    # kappa_min -> 0 makes every window the cutoff window: the same table, bit for bit
+    lines, spec, _ = _adaptive_case()
+    from dataclasses import replace
+    tiny = replace(spec, kappa_min=1e-300)
+    assert np.array_equal(K.kappa_table(lines, tiny), K.kappa_table(lines, spec))
+    assert K.profile_evals(lines, tiny) == K.profile_evals(lines, spec)
+
+
+def test_adaptive_points_drop_only_terms_below_kappa_min():
+    # Every (node, line, point) of the cutoff set: kept iff its Lorentz wing A gamma / (pi dnu^2)
+    # reaches kappa_min (within the cutoff); the exact Lorentz value of a dropped term is then
+    # below kappa_min, so 0 <= full - adaptive <= (dropped terms) * kappa_min at every entry.
+    lines, spec, ad = _adaptive_case()
+    full, adap = K.kappa_table(lines, spec), K.kappa_table(lines, ad)
+    lo, hi = K.adaptive_ranges(lines, ad)
+    clo, chi = K.line_ranges(lines, spec)
+    js = np.arange(spec.n_nu)
+    nu = K.grid_nu(spec, js)
+    for k, T in enumerate(spec.T_nodes()):
+        A, g, _ = K.line_terms(lines, float(T), spec.p_ref_atm, spec.x_ref, "lorentz")
+        dropped = np.zeros(spec.n_nu)
+        kept_n = 0
+        for l in range(lines.n):
+            if chi[l] < clo[l]:
+                continue
+            jj = js[clo[l]:chi[l] + 1]
+            d = nu[jj] - lines.nu0[l]
+            keep = (jj >= lo[k, l]) & (jj <= hi[k, l])
+            wing = A[l] * g[l] / (math.pi * d * d)
+            assert np.all(wing[keep & (d != 0)] >= ad.kappa_min)
+            val = A[l] * g[l] / (math.pi * (d * d + g[l] * g[l]))
+            assert np.all(val[~keep] < ad.kappa_min)
+            dropped[jj[~keep]] += 1
+            kept_n += int(keep.sum())
+        diff = full[k] - adap[k]
+        assert np.all(diff >= -1e-12 * full[k]) and np.all(diff <= dropped * ad.kappa_min * (1 + 1e-12))
+        assert kept_n == int(np.maximum(hi[k] - lo[k] + 1, 0).sum())
+    assert K.profile_evals(lines, ad) < K.profile_evals(lines, spec)
+
+
+def test_adaptive_points_monotone_in_kappa_min():
+    from dataclasses import replace
+    lines, spec, _ = _adaptive_case("voigt")
+    prev_t, prev_n = None, None
+    for km in (1e-4, 1e-3, 1e-2, 1e-1):
+        s = replace(spec, kappa_min=km)
+        t, n = K.kappa_table(lines, s), K.profile_evals(lines, s)
+        if prev_t is not None:
+            assert n <= prev_n and np.all(t <= prev_t * (1 + 1e-12))
+        prev_t, prev_n = t, n
