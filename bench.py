@@ -878,7 +878,9 @@ def _resident_build(rt, lines):
 def run_next(args):
     """The rows after the hot path, on the 32^3 workload's line list and table: the
     paper's spectrally resolved marching (Eq. I per wavenumber along 4096 straight
-    paths), the fixed 16 points per line, and a second gas accumulated into the table."""
+    paths), the fixed 16 points per line, adaptive points per line (two thresholds,
+    with their deviation from the cutoff build in the table and in the tallies of
+    2e6 rays), and a second gas accumulated into the table."""
     import torch
     from dataclasses import replace
     import paper_cs_0703028_gb300 as rt
@@ -918,11 +920,54 @@ def run_next(args):
         co2(s16, k16)
     with ClockWindow(0) as clk16:
         ms16 = _ev_time(lambda: co2(s16, k16), reps=args.steps)
+    ev_full_t = torch.zeros(1, dtype=torch.int64, device="cuda")
+    k_full = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    co2(spec, k_full, ev_full_t)
+    torch.cuda.synchronize()
+    ev16_full = int(ev_full_t.item())   # evaluations of the cutoff build
+    ms_full = _ev_time(lambda: co2(spec, k_full), reps=args.steps)
     out["points_per_line_16"] = {"evals": ev16, "ms": ms16, "evals_per_s": ev16 / (ms16 * 1e-3),
                                  "roofline": alu_roofline(ev16 / (ms16 * 1e-3), "voigt_near", probe, n_sm,
                                                           clock),
                                  "note": "per call: line geometry, prefactors and the gather kernel",
                                  "clocks": clk16.result}
+    # adaptive points per line: each line where its Lorentz wing reaches kappa_min
+    ad_out = {}
+    full = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+    co2(spec, full)
+    gsum = rt.make_grid(case.grid)
+    n_tr = 2_000_000
+    t_full = rt.Tally(case.grid.ncells)
+    t_full.zero()
+    rt.trace(gsum[0], full, spec, t_full, n_rays=n_tr, n_rays_total=n_tr)
+    ab_full = t_full.read()[0]
+    for km in (1e-3, 1e-1):
+        sa = replace(spec, kappa_min=km)
+        ka = torch.empty((spec.nT, spec.n_nu), dtype=torch.float32, device="cuda")
+        ev_a = torch.zeros(1, dtype=torch.int64, device="cuda")
+        co2(sa, ka, ev_a)
+        torch.cuda.synchronize()
+        n_ev = int(ev_a.item())
+        for _ in range(args.warmup):
+            co2(sa, ka)
+        with ClockWindow(0) as clk_a:
+            ms_a = _ev_time(lambda: co2(sa, ka), reps=args.steps)
+        rel = ((ka.double() - full.double()).abs() / full.double()).flatten()
+        ta = rt.Tally(case.grid.ncells)
+        ta.zero()
+        rt.trace(gsum[0], ka, spec, ta, n_rays=n_tr, n_rays_total=n_tr)
+        ab = ta.read()[0]
+        big = ab_full >= 1e-3 * ab_full.max()
+        terr = np.abs(ab[big] - ab_full[big]) / ab_full[big]
+        ad_out[f"kappa_min_{km:g}"] = {
+            "evals": n_ev, "ms": ms_a, "evals_per_s": n_ev / (ms_a * 1e-3),
+            "evals_fraction_of_cutoff_build": n_ev / float(ev16_full),
+            "speedup_vs_cutoff_build": ms_full / ms_a,
+            "table_rel_dev_vs_cutoff_build": {"median": float(rel.median()), "max": float(rel.max())},
+            "tally_rel_dev_vs_cutoff_build": {"rays": n_tr, "median": float(np.median(terr)),
+                                              "max": float(terr.max())},
+            "clocks": clk_a.result}
+    out["adaptive_points"] = ad_out
     # a second gas (an H2O-like list: 10k lines, mass 18 u) accumulated into the CO2 table
     h2o = replace(synth.make_lines(10000, 2000.0, 3000.0, synth.rng_for(1, 9), S_lo=1e-23, S_hi=1e-20),
                   mass_amu=18.0, n_T=0.6, q_exp=1.5)
@@ -946,6 +991,7 @@ def run_next(args):
     out["two_gases"] = {"evals": ev2, "ms": ms2, "evals_per_s": ev2 / (ms2 * 1e-3),
                         "roofline": alu_roofline(ev2 / (ms2 * 1e-3), "voigt", probe, n_sm, clock),
                         "clocks": clk2.result}
+    out["cutoff_build"] = {"evals": ev16_full, "ms": ms_full}
     res = {"metric": "Eq. I updates/s (marching), line-profile evals/s (variants)",
            "value": out["march"]["updates_per_s"], "unit": "(cell, nu) updates/s", "higher_is_better": True,
            "config": {"workload": "next32: 32^3 box, 20k Voigt lines, 64 T x 100k nu; 4096 paths"},

@@ -111,6 +111,13 @@ typedef struct {
                               the cutoff window; 0: cutoff window */
   int32_t accumulate;      /* rt_build_kappa: 1 adds into kappa (one call per absorbing gas of
                               a mixture, Eq. tau's sum over g), 0 overwrites it */
+  double kappa_min;        /* > 0: adaptive points per line (the next version of Section 4:
+                              points from the local temperature and the line's intensity):
+                              at T node T_k line l contributes only where |nu_j - nu0| <= w =
+                              min(cutoff, sqrt(A gamma / (pi kappa_min))), A = u(T_k) S(T_k),
+                              gamma its Lorentz half-width at T_k (the distance at which its
+                              Lorentz wing A gamma / (pi dnu^2) falls to kappa_min, cm^-1),
+                              decided in binary64; requires points_per_line = 0; 0: off */
 } rt_spectral;
 
 /*

@@ -52,7 +52,8 @@ class rt_spectral(ct.Structure):
     _fields_ = [("nu_min", ct.c_double), ("dnu", ct.c_double), ("n_nu", ct.c_int64),
                 ("cutoff", ct.c_double), ("profile", ct.c_int32), ("nT", ct.c_int32),
                 ("T_min", ct.c_double), ("T_max", ct.c_double), ("p_ref_atm", ct.c_double),
-                ("x_ref", ct.c_double), ("points_per_line", ct.c_int32), ("accumulate", ct.c_int32)]
+                ("x_ref", ct.c_double), ("points_per_line", ct.c_int32), ("accumulate", ct.c_int32),
+                ("kappa_min", ct.c_double)]
 
 
 class rt_grid(ct.Structure):
@@ -190,7 +191,7 @@ def make_spectral(spec) -> rt_spectral:
                        PROFILE[spec.profile] if isinstance(spec.profile, str) else int(spec.profile),
                        int(spec.nT), float(spec.T_min), float(spec.T_max), float(spec.p_ref_atm),
                        float(spec.x_ref), int(getattr(spec, "points_per_line", 0)),
-                       int(getattr(spec, "accumulate", 0)))
+                       int(getattr(spec, "accumulate", 0)), float(getattr(spec, "kappa_min", 0.0)))
 
 
 def make_grid(grid, device="cuda"):

@@ -766,15 +766,166 @@ k_kappa_ppl(const float4 *__restrict__ P, const int4 *__restrict__ R, long long 
   }
 }
 
+// ---- adaptive points per line
+// Each line's window at each T node: |nu_j - nu0| <= w = min(cutoff, sqrt(A gamma /
+// (pi kappa_min))) with A = u(T_k) S(T_k) and gamma the Lorentz half-width at T_k, in
+// binary64 in the order the float64 reading states it (number density x p atm / (k_B T)
+// 1e-6, Eq. (S) as S_ref (T_ref/T)^q Boltzmann ratio stimulated-emission ratio).
+struct AdaptParams {
+  double nu_min, dnu, cutoff, T_min, T_max, T_ref, c2, x_ref, p_ref, n_T, q_exp, kappa_min;
+  long long n_nu, n_lines;
+  int nT;
+};
+
+__global__ void k_adaptive_windows(const double *__restrict__ nu0, const double *__restrict__ S,
+                                   const double *__restrict__ g, const double *__restrict__ E, AdaptParams P,
+                                   int2 *__restrict__ AW, unsigned long long *evals) {
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  unsigned long long cnt = 0;
+  if (l < P.n_lines) {
+    const double T = P.nT > 1 ? P.T_min + (double)k * ((P.T_max - P.T_min) / (double)(P.nT - 1)) : P.T_min;
+    const double v = nu0[l];
+    const double q = pow(P.T_ref / T, P.q_exp);
+    const double boltz = exp(-P.c2 * E[l] / T) / exp(-P.c2 * E[l] / P.T_ref);
+    const double stim = (-expm1(-P.c2 * v / T)) / (-expm1(-P.c2 * v / P.T_ref));
+    const double ST = S[l] * q * boltz * stim;
+    const double A = P.x_ref * P.p_ref * kAtm / (kKB * T) * 1e-6 * ST;
+    const double gam = g[l] * P.p_ref * pow(P.T_ref / T, P.n_T);
+    double w = sqrt(A * gam / (kPi * P.kappa_min));
+    if (!(w <= P.cutoff)) w = P.cutoff;
+    double flo = floor((v - w - P.nu_min) / P.dnu) - 1.0;
+    double fhi = ceil((v + w - P.nu_min) / P.dnu) + 1.0;
+    flo = fmin(fmax(isfinite(flo) ? flo : 0.0, -1.0), (double)P.n_nu + 1.0);
+    fhi = fmin(fmax(isfinite(fhi) ? fhi : 0.0, -2.0), (double)P.n_nu + 1.0);
+    long long lo = (long long)flo, hi = (long long)fhi;
+    if (lo < 0) lo = 0;
+    if (hi > P.n_nu - 1) hi = P.n_nu - 1;
+#pragma unroll 1
+    for (int it = 0; it < 6 && lo < P.n_nu; ++it)
+      if (__dsub_rn(grid_nu(P.nu_min, lo, P.dnu), v) < -w) ++lo;
+#pragma unroll 1
+    for (int it = 0; it < 6 && hi >= 0; ++it)
+      if (__dsub_rn(grid_nu(P.nu_min, hi, P.dnu), v) > w) --hi;
+    AW[(long long)k * P.n_lines + l] = make_int2((int)lo, (int)hi);
+    if (hi >= lo) cnt = (unsigned long long)(hi - lo + 1);
+  }
+  if (evals) {
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(evals, cnt);
+  }
+}
+
+// The line sum with adaptive windows: a block per (256-point tile, T node).  The lines
+// whose cutoff windows touch the tile are a contiguous index range; the block takes it
+// in chunks of 256 lines, keeps (ballot compaction, in ascending nu0) those whose
+// adaptive window at this node meets the tile, and each point then sums the kept
+// lines whose window holds it (Kahan, ascending nu0).  A kept line can be far from
+// the point (strong lines keep the whole cutoff window), so values take the full-range
+// form: the Lorentz reciprocal, or the Faddeeva function in all its regions.
+template <int PROFILE>
+__global__ void __launch_bounds__(kTilePts)
+k_kappa_adaptive(const float4 *__restrict__ P, const int4 *__restrict__ R, const int2 *__restrict__ AW,
+                 long long n_lines, long long n_nu, WeidCoef wc, int accumulate, float *__restrict__ kappa) {
+  __shared__ long long s_range[2];
+  __shared__ int2 s_win[kTilePts];     // kept lines' windows at this node
+  __shared__ float4 s_par[kTilePts];   // their {centre index bits, centre offset, coefficient, g^2 or y}
+  __shared__ float s_sd[kTilePts];     // Voigt: s dnu (grid units to x)
+  __shared__ int s_warp[kTilePts / 32];
+  const long long jw0 = (long long)blockIdx.x * kTilePts;
+  const long long jend = min(jw0 + (long long)kTilePts, n_nu);
+  const int k = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_range[0] = lower_bound_hi(R, n_lines, (int)jw0);
+  if (threadIdx.x == 1) s_range[1] = lower_bound_lo(R, n_lines, (int)jend);
+  __syncthreads();
+  const long long a = s_range[0], b = max(s_range[0], s_range[1]);
+  const long long j = jw0 + threadIdx.x;
+  const float4 *Pk = P + (long long)k * n_lines;
+  const int2 *Wk = AW + (long long)k * n_lines;
+  float acc = 0.0f, cmp = 0.0f;
+#pragma unroll 1
+  for (long long c0 = a; c0 < b; c0 += kTilePts) {
+    const long long l = c0 + threadIdx.x;
+    int2 w = make_int2(1, 0);
+    bool keep = false;
+    if (l < b) {
+      w = __ldg(Wk + l);
+      keep = w.y >= w.x && w.y >= (int)jw0 && (long long)w.x < jend;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    int off = 0, total = 0;
+#pragma unroll
+    for (int q = 0; q < kTilePts / 32; ++q) {
+      const int c = s_warp[q];
+      off += q < warp ? c : 0;
+      total += c;
+    }
+    if (keep) {  // the kept line's constants, formed once for all the tile's points
+      const int pos = off + __popc(m & ((1u << lane) - 1u));
+      const int4 r = __ldg(R + l);
+      const float4 p = __ldg(Pk + l);
+      s_win[pos] = w;
+      if (PROFILE == RT_PROFILE_LORENTZ) {
+        s_par[pos] = make_float4(__int_as_float(r.z), __int_as_float(r.w), p.x, p.y);
+      } else {
+        const float y = sqrtf(p.z);
+        s_par[pos] = make_float4(__int_as_float(r.z), __int_as_float(r.w), __fdividef(p.x, y), y);
+        s_sd[pos] = p.y;
+      }
+    }
+    __syncthreads();
+    if (j < jend) {
+#pragma unroll 1
+      for (int i = 0; i < total; ++i) {
+        const int2 ww = s_win[i];
+        if ((int)j < ww.x || (int)j > ww.y) continue;
+        const float4 q = s_par[i];
+        const float u = __fadd_rn((float)((int)j - __float_as_int(q.x)), q.y);
+        float v;
+        if (PROFILE == RT_PROFILE_LORENTZ) {
+          v = q.z * rcp_approx(__fmaf_rn(u, u, q.w));
+        } else {
+          v = q.z * faddeeva_re(s_sd[i] * u, q.w, wc);
+        }
+        const float yk = __fsub_rn(v, cmp);
+        const float t = __fadd_rn(acc, yk);
+        cmp = __fsub_rn(__fsub_rn(t, acc), yk);
+        acc = t;
+      }
+    }
+    __syncthreads();  // the kept list is rewritten by the next chunk
+  }
+  if (j < jend) {
+    float *dst = kappa + (long long)k * n_nu + j;
+    const float out = __fsub_rn(acc, cmp);
+    *dst = accumulate ? *dst + out : out;
+  }
+}
+
 int g_kappa_tpb = kMaxTPerBlock;
 
 rt_status launch_kappa(const float4 *P, const float4 *P2, const int4 *R, int4 *tiles,
-                       const unsigned *far_bits, long long n, const rt_spectral *spec,
+                       const unsigned *far_bits, const int2 *AW, long long n, const rt_spectral *spec,
                        double nu_abs_max, double mass_amu, float *kappa, uint32_t *status,
                        cudaStream_t st) {
   static WeidCoef wc;
   static std::once_flag wc_once;
   std::call_once(wc_once, [] { weideman_coefficients(&wc); });
+  const long long n_tiles_a = (spec->n_nu + kTilePts - 1) / kTilePts;
+  if (AW) {  // adaptive points per line: the windows' gather kernel
+    dim3 g((unsigned)n_tiles_a, (unsigned)spec->nT);
+    if (spec->profile == RT_PROFILE_LORENTZ)
+      k_kappa_adaptive<RT_PROFILE_LORENTZ><<<g, kTilePts, 0, st>>>(P, R, AW, n, spec->n_nu, wc,
+                                                                   spec->accumulate ? 1 : 0, kappa);
+    else
+      k_kappa_adaptive<RT_PROFILE_VOIGT><<<g, kTilePts, 0, st>>>(P, R, AW, n, spec->n_nu, wc,
+                                                                 spec->accumulate ? 1 : 0, kappa);
+    RT_CUDA_TRY(cudaGetLastError());
+    return RT_OK;
+  }
   // W bounds every line's near-centre half-width sqrt(400 - y^2) / (s dnu) <= 20 alpha /
   // (sqrt(ln 2) dnu), alpha the largest Doppler half-width of a line that reaches the grid
   int W = 0;
@@ -833,6 +984,10 @@ rt_status validate_spec(const rt_spectral *s) {
   if (s->points_per_line < 0 || s->points_per_line > (1 << 20))
     return fail(RT_E_INVAL, "spec.points_per_line must be in [0, 2^20]");
   if (s->accumulate != 0 && s->accumulate != 1) return fail(RT_E_INVAL, "spec.accumulate must be 0 or 1");
+  if (!std::isfinite(s->kappa_min) || s->kappa_min < 0)
+    return fail(RT_E_INVAL, "spec.kappa_min must be finite and >= 0");
+  if (s->kappa_min > 0 && s->points_per_line > 0)
+    return fail(RT_E_INVAL, "spec.kappa_min (adaptive points) and points_per_line exclude each other");
   return RT_OK;
 }
 
@@ -871,7 +1026,7 @@ namespace {
 // Scratch of one build: [line arrays if host-resident][R: n int4][P: nT n float4]
 // [P2: nT n float4, Voigt][tile segments: 3 int4 per 256-point tile][far-zone bound]
 struct KappaLayout {
-  size_t off_R, off_P, off_P2, off_tiles, off_far, total;
+  size_t off_R, off_P, off_P2, off_tiles, off_far, off_AW, total;
 };
 
 KappaLayout kappa_layout(const rt_lines *lines, const rt_spectral *spec) {
@@ -885,7 +1040,8 @@ KappaLayout kappa_layout(const rt_lines *lines, const rt_spectral *spec) {
   L.off_tiles = up(L.off_P2 + (spec->profile == RT_PROFILE_VOIGT ? pn : 0));
   const size_t n_tiles = (size_t)((spec->n_nu + kTilePts - 1) / kTilePts);
   L.off_far = up(L.off_tiles + n_tiles * kTileInts * sizeof(int4));
-  L.total = L.off_far + 256;
+  L.off_AW = L.off_far + 256;  // adaptive windows: nT n int2
+  L.total = L.off_AW + (spec->kappa_min > 0 ? up((size_t)spec->nT * n * sizeof(int2)) : 0);
   return L;
 }
 
@@ -929,9 +1085,21 @@ rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, con
   GeomParams G{spec->nu_min, spec->dnu, spec->cutoff, spec->n_nu, n, spec->nT,
                lines->memory == RT_MEM_DEVICE ? 1 : 0, spec->points_per_line};
   const int tb = 256;
+  const bool adaptive = spec->kappa_min > 0;
+  // with adaptive points the evaluations are counted per (node, line) window below
   k_line_geometry<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(d_nu0, d_S, d_g, d_E, G, R,
-                                                                evals_out, status);
+                                                                adaptive ? nullptr : evals_out, status);
   RT_CUDA_TRY(cudaGetLastError());
+  int2 *AW = nullptr;
+  if (adaptive) {
+    AW = reinterpret_cast<int2 *>(base + L.off_AW);
+    AdaptParams A{spec->nu_min, spec->dnu, spec->cutoff, spec->T_min, spec->T_max, lines->T_ref,
+                  100.0 * (kH * kC / kKB), spec->x_ref, spec->p_ref_atm, lines->n_T, lines->q_exp,
+                  spec->kappa_min, spec->n_nu, n, spec->nT};
+    dim3 ga((unsigned)((n + tb - 1) / tb), (unsigned)spec->nT);
+    k_adaptive_windows<<<ga, tb, 0, st>>>(d_nu0, d_S, d_g, d_E, A, AW, evals_out);
+    RT_CUDA_TRY(cudaGetLastError());
+  }
 
   PrefParams Q;
   Q.T_min = spec->T_min;
@@ -960,7 +1128,7 @@ rt_status run_build(char *base, const KappaLayout &L, const rt_lines *lines, con
   const double nu_abs_max =
       std::fmax(std::fabs(spec->nu_min - reach),
                 std::fabs(spec->nu_min + (double)spec->n_nu * spec->dnu + reach));
-  return launch_kappa(P, P2, R, tiles, far_bits, n, spec, nu_abs_max, lines->mass_amu, kappa, status, st);
+  return launch_kappa(P, P2, R, tiles, far_bits, AW, n, spec, nu_abs_max, lines->mass_amu, kappa, status, st);
 }
 
 }  // namespace

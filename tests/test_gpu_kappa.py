@@ -218,3 +218,56 @@ def test_fixed_points_per_line_accumulates(rt):
     nz = ref > 0
     assert np.array_equal(got > 0, nz)
     assert _rel(got[nz], ref[nz]).max() <= TOL
+
+
+@pytest.mark.parametrize("profile,kappa_min", [("lorentz", 1e-3), ("voigt", 1e-3), ("voigt", 0.3)])
+def test_adaptive_points_per_line(rt, profile, kappa_min):
+    # each line at each T node only where its Lorentz wing reaches kappa_min (windows decided
+    # in binary64 on both sides: the evaluation counts must match exactly); points no window
+    # reaches stay exactly zero
+    from dataclasses import replace
+    rng = synth.rng_for(9, 82)
+    lines = synth.make_lines(2000, 1990.0, 2110.0, rng)
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.01, n_nu=10001, cutoff=25.0, profile=profile, nT=3,
+                          T_min=800.0, T_max=1600.0, p_ref_atm=1.3, x_ref=0.07, kappa_min=kappa_min)
+    got, ev, st = _gpu_table(rt, lines, spec)
+    ref = okappa.kappa_table(lines, spec)
+    assert st == 0
+    assert ev == okappa.profile_evals(lines, spec)
+    assert ev < okappa.profile_evals(lines, replace(spec, kappa_min=0.0))
+    nz = ref > 0
+    assert np.array_equal(got > 0, nz)
+    assert _rel(got[nz], ref[nz]).max() <= TOL
+
+
+def test_adaptive_points_accumulate_and_device_lines(rt):
+    import torch
+    from dataclasses import replace
+    rng = synth.rng_for(9, 83)
+    co2 = synth.make_lines(700, 2000.0, 2200.0, rng)
+    h2o = replace(synth.make_lines(500, 2050.0, 2250.0, rng, S_lo=1e-23, S_hi=1e-20), mass_amu=18.0,
+                  n_T=0.6, q_exp=1.5)
+    s1 = synth.Spectral(nu_min=2020.0, dnu=0.02, n_nu=8000, cutoff=25.0, profile="voigt", nT=4,
+                        T_min=700.0, T_max=1900.0, x_ref=0.1, kappa_min=1e-2)
+    s2 = replace(s1, x_ref=0.05, accumulate=1)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tab = rt.build_kappa(co2, s1, memory="device", status=status)
+    rt.build_kappa(h2o, s2, out=tab, memory="device", status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = okappa.kappa_table(co2, s1) + okappa.kappa_table(h2o, s2)
+    got = tab.cpu().numpy().astype(np.float64)
+    nz = ref > 0
+    assert np.array_equal(got > 0, nz)
+    assert _rel(got[nz], ref[nz]).max() <= TOL
+
+
+def test_adaptive_points_exclude_fixed_points(rt):
+    import torch
+    from dataclasses import replace
+    c0 = synth.config(0)
+    bad = replace(c0.spec, kappa_min=1e-3, points_per_line=16)
+    with pytest.raises(rt.RtError):
+        rt.build_kappa(c0.lines, bad)
+    with pytest.raises(rt.RtError):
+        rt.build_kappa(c0.lines, replace(c0.spec, kappa_min=-1.0))

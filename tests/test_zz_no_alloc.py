@@ -73,6 +73,18 @@ def test_static_scratch_matches_allocating_build_twice(rt):
         _close(got, ref)
 
 
+def test_static_scratch_adaptive_points_per_line(rt):
+    # adaptive points per line: the per-(node, line) windows live in the static array too
+    rng = synth.rng_for(9, 35)
+    lines = synth.make_lines(1500, 1995.0, 2105.0, rng)
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.01, n_nu=10001, cutoff=25.0, profile="voigt", nT=4,
+                          T_min=800.0, T_max=1600.0, kappa_min=1e-3)
+    for _ in range(2):
+        ref, got, ev_ref, ev_got = _both(rt, lines, spec)
+        assert ev_got == ev_ref
+        _close(got, ref)
+
+
 @pytest.mark.parametrize("profile", ["lorentz", "voigt"])
 def test_static_scratch_fixed_points_per_line(rt, profile):
     # the fixed-points gather kernel through the allocation-free entry point (odd line count)
