@@ -696,7 +696,7 @@ def run_surrogate(args):
             P_e, norms_e, hist_e = surrogate.train_bands(case.lines, spec, p_nodes, ex["train_x"][0],
                                                          ex["train_x"][1], band_pts=args.bands, n_per_band=n_per,
                                                          batch=args.band_batch, steps=st_n, lr0=args.band_lr,
-                                                         log_every=250)
+                                                         log_every=250, emission_mix=args.band_mix)
             torch.cuda.synchronize()
             tr_s = time.time() - t0
             name = f"bands{args.bands}_s{st_n}"
@@ -705,7 +705,14 @@ def run_surrogate(args):
                                                                    n_rays_total=n), n)
             walks[name]["clocks"] = clk_b.result
             err = np.abs(ab[big] - ref[big]) / ref[big]
+            # the worst cells: their temperature, share of the largest tally, error
+            cells_big = np.nonzero(big)[0]
+            worst = cells_big[np.argsort(err)[-8:]]
+            T_cells = np.asarray(g.T, dtype=np.float64)
+            worst_cells = [{"cell": int(c), "T": float(T_cells[c]), "tally_share_of_max": float(ref[c] / ref.max()),
+                            "err": float(abs(ab[c] - ref[c]) / ref[c])} for c in worst]
             r_e = {"steps": st_n, "train_s": tr_s, "loss_first": hist_e[0][1] if hist_e else None,
+                   "worst_cells": worst_cells,
                    "loss_last": hist_e[-1][1] if hist_e else None, "median": float(np.median(err)),
                    "p90": float(np.percentile(err, 90)), "p99": float(np.percentile(err, 99)),
                    "max": float(err.max()), "frac_cells_within_1pct": float(np.mean(err <= 0.01)),
@@ -722,6 +729,7 @@ def run_surrogate(args):
                "training_frac": ens_tf / _peaks().get("bf16_tflops", 1978.3),
                "training_note": "wall clock of train_bands incl. tables and sampling; measured bf16 burst peak",
                "samples_per_band": n_per, "batch_per_band": args.band_batch, "lr0": args.band_lr,
+               "emission_mix": args.band_mix,
                "error_curve": ens_curve,
                "best": {"walk": ens_name, "median": r_e["median"], "max": r_e["max"]},
                "speedup_vs_lbl": walks[ens_name]["ray_cell_steps_per_s"] / walks["lbl"]["ray_cell_steps_per_s"],
@@ -1136,9 +1144,11 @@ def main():
     ap.add_argument("--objective", default="mse", choices=["mse"])
     ap.add_argument("--rays", type=int, default=50_000_000)
     ap.add_argument("--bands", type=int, default=64, help="wavenumbers per network of the ensemble (0: none)")
-    ap.add_argument("--band-steps", default="16000", help="comma-separated training steps (one ensemble each)")
+    ap.add_argument("--band-steps", default="24000", help="comma-separated training steps (one ensemble each)")
     ap.add_argument("--band-batch", type=int, default=256)
     ap.add_argument("--band-lr", type=float, default=3e-3)
+    ap.add_argument("--band-mix", type=float, default=0.0,
+                    help="fraction of the ensemble's samples drawn in proportion to kappa I_b")
     ap.add_argument("--band-samples", type=int, default=12800, help="samples per band (128^3 learned part)")
     ap.add_argument("--configs", default="4,1", help="step line: main workload index[,extra workload index]")
     ap.add_argument("--walk-group", default="tune", choices=["tune", "off", "on"],

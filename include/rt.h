@@ -446,12 +446,15 @@ rt_status rt_mlp_make_samples(const float *tables, int32_t n_p, const float *p_n
 
 /* Training samples for an ensemble: n_per_band samples per band b (rows b n_per_band
  * .. of inputs device [n_bands][n_per_band][4], targets [n_bands][n_per_band]),
- * drawn as in rt_mlp_make_samples but with j uniform in the band's own wavenumbers:
- * Philox4x32-10 counter (i, i >> 32, b + 1, 0x6d6c70), key = seed.  Asynchronous. */
+ * drawn as in rt_mlp_make_samples but with j in the band's own wavenumbers: Philox4x32-10
+ * counter (i, i >> 32, b + 1, 0x6d6c70), key = seed.  j is uniform in the band, except for
+ * a fraction emission_mix (in [0, 1], decided per sample by the low byte of word 3 against
+ * round(256 emission_mix)) drawn with probability proportional to kappa I_b(nu_j, T_k) at
+ * the sample's (p, T) node: the emission the walk samples.  Asynchronous. */
 rt_status rt_mlp_make_samples_bands(const float *tables, int32_t n_p, const float *p_nodes,
                                     const rt_spectral *spec, int32_t band_pts, float x_lo, float x_hi,
-                                    uint64_t seed, int64_t n_per_band, float *inputs, float *targets,
-                                    void *stream);
+                                    float emission_mix, uint64_t seed, int64_t n_per_band, float *inputs,
+                                    float *targets, void *stream);
 
 /* rt_mlp_train_steps for n_nets independent networks at once (one launch per kernel
  * and step for all of them): network b trains on its own n samples (rows b n .. of

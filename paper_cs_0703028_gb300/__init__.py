@@ -96,8 +96,8 @@ _SIGNATURES = {
                       ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_mlp_make_samples": ([_P, ct.c_int32, _P, _P, ct.c_float, ct.c_float, ct.c_uint64, ct.c_int64,
                              _P, _P, _P], ct.c_int),
-    "rt_mlp_make_samples_bands": ([_P, ct.c_int32, _P, _P, ct.c_int32, ct.c_float, ct.c_float, ct.c_uint64,
-                                   ct.c_int64, _P, _P, _P], ct.c_int),
+    "rt_mlp_make_samples_bands": ([_P, ct.c_int32, _P, _P, ct.c_int32, ct.c_float, ct.c_float, ct.c_float,
+                                   ct.c_uint64, ct.c_int64, _P, _P, _P], ct.c_int),
     "rt_mlp_train_steps_nets": ([ct.c_int32, _P, _P, _P, _P, _P, _P, ct.c_int64, ct.c_int64, _P, ct.c_double,
                                  ct.c_double, ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_mlp_forward_nets": ([ct.c_int32, _P, _P, _P, ct.c_int64, _P, _P, _P], ct.c_int),
@@ -413,7 +413,8 @@ class MlpEnsembleTrainer:
         _check(st, "rt_mlp_train_steps_nets")
 
 
-def mlp_make_samples_bands(tables, p_nodes, spec, band_pts, x_lo, x_hi, seed, n_per_band, stream=None):
+def mlp_make_samples_bands(tables, p_nodes, spec, band_pts, x_lo, x_hi, seed, n_per_band, stream=None,
+                           emission_mix=0.0):
     """rt_mlp_make_samples_bands: (inputs [n_bands, n, 4], targets [n_bands, n]) CUDA tensors."""
     import torch
     nb = -(-int(spec.n_nu) // int(band_pts))
@@ -421,7 +422,8 @@ def mlp_make_samples_bands(tables, p_nodes, spec, band_pts, x_lo, x_hi, seed, n_
     targets = torch.empty((nb, n_per_band), dtype=torch.float32, device=tables.device)
     S = make_spectral(spec)
     st = lib().rt_mlp_make_samples_bands(_ptr(tables), int(p_nodes.shape[0]), _ptr(p_nodes), ct.byref(S),
-                                         int(band_pts), float(x_lo), float(x_hi), int(seed), int(n_per_band),
+                                         int(band_pts), float(x_lo), float(x_hi), float(emission_mix), int(seed),
+                                         int(n_per_band),
                                          _ptr(inputs), _ptr(targets), _stream_ptr(stream))
     _check(st, "rt_mlp_make_samples_bands")
     return inputs, targets

@@ -902,12 +902,15 @@ __global__ void k_mlp_samples(const float *__restrict__ tables, int np, int nT, 
 // Training samples of a spectral-band ensemble: band b (grid.y) draws its n samples
 // from its own wavenumbers j in [b band_pts, min((b + 1) band_pts, n_nu)): Philox
 // counter (i, i >> 32, b + 1, 0x6d6c70) under the seed picks j in the band, the T
-// node, the pressure node and x as k_mlp_samples does; rows b n + i.
+// node, the pressure node and x as k_mlp_samples does; rows b n + i.  A sample whose
+// low byte of word 3 is below em_256 (of 256) instead draws j with probability
+// proportional to kappa I_b(nu_j, T_k) over the band at its (p, T) node (the
+// emission the walk samples), by a scan of the band's cumulative weights.
 __global__ void k_mlp_samples_bands(const float *__restrict__ tables, int np, int nT, long long n_nu,
                                     const float *__restrict__ p_nodes, float T_min, float dT, float nu_min,
                                     float dnu, float x_lo, float x_hi, float x_ref, uint32_t seed_lo,
-                                    uint32_t seed_hi, int band_pts, long long n, float *__restrict__ inputs,
-                                    float *__restrict__ targets) {
+                                    uint32_t seed_hi, int band_pts, int em_256, float c2_cm, long long n,
+                                    float *__restrict__ inputs, float *__restrict__ targets) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long b = blockIdx.y;
   if (i >= n) return;
@@ -915,11 +918,31 @@ __global__ void k_mlp_samples_bands(const float *__restrict__ tables, int np, in
                                       0x6d6c70u}, seed_lo, seed_hi);
   const long long j0 = b * band_pts;
   const long long width = min((long long)band_pts, n_nu - j0);
-  const long long j = j0 + (long long)(((unsigned long long)v.x * (unsigned long long)width) >> 32);
   const int kT = (int)(((unsigned long long)v.y * (unsigned long long)nT) >> 32);
   const int kp = (int)(((unsigned long long)v.z * (unsigned long long)np) >> 32);
   const float x = x_lo + (x_hi - x_lo) * ((float)(v.w >> 8) * 0x1p-24f);
-  const float kap = tables[((long long)kp * nT + kT) * n_nu + j];
+  const float *row = tables + ((long long)kp * nT + kT) * n_nu;
+  long long j = j0 + (long long)(((unsigned long long)v.x * (unsigned long long)width) >> 32);
+  if ((int)(v.w & 255u) < em_256) {
+    const float Tk = fmaf((float)kT, dT, T_min);
+    auto weight = [&](long long q) {  // kappa nu^3 / (exp(c2 nu / T) - 1), the Planck constants dropped
+      const float nu = fmaf((float)q, dnu, nu_min);
+      return row[q] * nu * nu * nu / expm1f(c2_cm * nu / Tk);
+    };
+    float tot = 0.0f;
+    for (long long q = j0; q < j0 + width; ++q) tot += weight(q);
+    const float target = tot * ((float)(v.x >> 8) * 0x1p-24f);
+    float acc = 0.0f;
+    j = j0 + width - 1;
+    for (long long q = j0; q < j0 + width; ++q) {
+      acc += weight(q);
+      if (acc > target) {
+        j = q;
+        break;
+      }
+    }
+  }
+  const float kap = row[j];
   const long long o = b * n + i;
   inputs[o * 4 + 0] = __logf(fmaf((float)j, dnu, nu_min));
   inputs[o * 4 + 1] = fmaf((float)kT, dT, T_min);
@@ -1244,20 +1267,24 @@ rt_status mlp_samples_impl(const float *tables, int32_t np, const float *p_nodes
 }
 
 rt_status mlp_samples_bands_impl(const float *tables, int32_t np, const float *p_nodes, const rt_spectral *spec,
-                                 int32_t band_pts, float x_lo, float x_hi, uint64_t seed, int64_t n, float *inputs,
-                                 float *targets, cudaStream_t st) {
+                                 int32_t band_pts, float x_lo, float x_hi, float emission_mix, uint64_t seed,
+                                 int64_t n, float *inputs, float *targets, cudaStream_t st) {
   rt_status v = validate_spec(spec);
   if (v != RT_OK) return v;
   if (!tables || !p_nodes || !inputs || !targets || np < 1 || n < 0 || band_pts < 1)
     return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: bad arguments");
   if (!(x_lo > 0) || !(x_hi >= x_lo)) return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: need 0 < x_lo <= x_hi");
+  if (!(emission_mix >= 0.0f && emission_mix <= 1.0f))
+    return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: emission_mix must be in [0, 1]");
   const long long n_bands = (spec->n_nu + band_pts - 1) / band_pts;
   if (n_bands > 65535) return fail(RT_E_INVAL, "rt_mlp_make_samples_bands: at most 65535 bands");
   if (n == 0) return RT_OK;
   const float dT = spec->nT > 1 ? (float)((spec->T_max - spec->T_min) / (spec->nT - 1)) : 0.0f;
   k_mlp_samples_bands<<<dim3((unsigned)((n + 255) / 256), (unsigned)n_bands), 256, 0, st>>>(
       tables, np, spec->nT, spec->n_nu, p_nodes, (float)spec->T_min, dT, (float)spec->nu_min, (float)spec->dnu,
-      x_lo, x_hi, (float)spec->x_ref, (uint32_t)seed, (uint32_t)(seed >> 32), band_pts, n, inputs, targets);
+      x_lo, x_hi, (float)spec->x_ref, (uint32_t)seed, (uint32_t)(seed >> 32), band_pts,
+      (int)std::lround(emission_mix * 256.0f), (float)(100.0 * 6.62607015e-34 * 299792458.0 / 1.380649e-23), n,
+      inputs, targets);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -1276,10 +1303,10 @@ rt_status rt_trace_mlp_bands(const rt_grid *grid, int32_t band_pts, const float 
 
 rt_status rt_mlp_make_samples_bands(const float *tables, int32_t n_p, const float *p_nodes,
                                     const rt_spectral *spec, int32_t band_pts, float x_lo, float x_hi,
-                                    uint64_t seed, int64_t n_per_band, float *inputs, float *targets,
-                                    void *stream) {
-  return rt::mlp_samples_bands_impl(tables, n_p, p_nodes, spec, band_pts, x_lo, x_hi, seed, n_per_band, inputs,
-                                    targets, (cudaStream_t)stream);
+                                    float emission_mix, uint64_t seed, int64_t n_per_band, float *inputs,
+                                    float *targets, void *stream) {
+  return rt::mlp_samples_bands_impl(tables, n_p, p_nodes, spec, band_pts, x_lo, x_hi, emission_mix, seed,
+                                    n_per_band, inputs, targets, (cudaStream_t)stream);
 }
 
 rt_status rt_trace_mlp(const rt_grid *grid, const float *params, const rt_mlp_norm *norm,

@@ -238,3 +238,32 @@ def test_band_samples_lie_in_their_band(rt):
         assert np.all((x >= 0.05) & (x <= 0.2))
         ref = np.log(tab[kp, kT, j].astype(np.float64) * x / 0.1)
         assert np.allclose(tg[b], ref, rtol=0, atol=2e-6 * np.abs(ref).max() + 1e-6)
+
+
+@pytest.mark.parametrize("mix", [1.0, 0.5])
+def test_band_samples_follow_the_emission_weights(rt, mix):
+    # With emission_mix m, a sample's wavenumber follows (1 - m) uniform + m kappa I_b(nu, T)
+    # over its band (at its own T and p node): the empirical frequencies match within 5 sigma.
+    import torch
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.5, n_nu=16, cutoff=25.0, profile="voigt", nT=3,
+                          T_min=800.0, T_max=1600.0, p_ref_atm=1.0, x_ref=0.1)
+    rng = np.random.default_rng(4)
+    tab = rng.uniform(0.2, 5.0, (1, spec.nT, spec.n_nu)).astype(np.float32)
+    p_nodes = torch.tensor([1.0], dtype=torch.float32, device="cuda")
+    n = 60000
+    inp, _ = rt.mlp_make_samples_bands(torch.from_numpy(tab).cuda(), p_nodes, spec, 8, 0.05, 0.2, 11, n,
+                                       emission_mix=mix)
+    inp = inp.cpu().numpy().astype(np.float64)
+    c2 = 1.438776877
+    for b in range(2):
+        j = np.rint((np.exp(inp[b, :, 0]) - spec.nu_min) / spec.dnu).astype(int) - 8 * b
+        kT = np.rint((inp[b, :, 1] - spec.T_min) / 400.0).astype(int)
+        for k in range(spec.nT):
+            sel = kT == k
+            js = np.arange(8 * b, 8 * b + 8)
+            nu = spec.nu_min + js * spec.dnu
+            w = tab[0, k, js].astype(np.float64) * nu ** 3 / np.expm1(c2 * nu / spec.T_nodes()[k])
+            p = (1 - mix) / 8 + mix * w / w.sum()
+            cnt = np.bincount(j[sel], minlength=8)
+            m = sel.sum()
+            assert np.all(np.abs(cnt - m * p) <= 5 * np.sqrt(m * p * (1 - p)) + 1), (b, k, cnt, m * p)
