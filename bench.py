@@ -1078,7 +1078,7 @@ def run_surrogate128(args):
     P, norms, hist = surrogate.train_bands(lines, spec, p_nodes, 0.01, 0.3, band_pts=args.bands,
                                            n_per_band=args.band_samples, batch=args.band_batch,
                                            steps=int(str(args.band_steps).split(",")[-1]), lr0=args.band_lr,
-                                           group=65535, log_every=500)
+                                           group=65535, log_every=500, emission_mix=args.band_mix)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     walks, tallies = {}, {}
@@ -1119,7 +1119,7 @@ def run_surrogate128(args):
                                   f"wavenumbers, {args.band_samples} samples per band (16 p x 64 T tables)"},
            "training": {"seconds": train_s, "steps": hist[-1][0] + 1 if hist else 0,
                         "loss_first": hist[0][1] if hist else None, "loss_last": hist[-1][1] if hist else None,
-                        "batch_per_band": args.band_batch, "lr0": args.band_lr},
+                        "batch_per_band": args.band_batch, "lr0": args.band_lr, "emission_mix": args.band_mix},
            "walks": walks,
            "ensemble_vs_table": err(tallies["ensemble"], tallies["table"]),
            "subset_vs_lbl": {"table": err(sub["table"], sub["lbl"]), "ensemble": err(sub["ensemble"], sub["lbl"])},
@@ -1147,7 +1147,7 @@ def main():
     ap.add_argument("--band-steps", default="24000", help="comma-separated training steps (one ensemble each)")
     ap.add_argument("--band-batch", type=int, default=256)
     ap.add_argument("--band-lr", type=float, default=3e-3)
-    ap.add_argument("--band-mix", type=float, default=0.0,
+    ap.add_argument("--band-mix", type=float, default=0.5,
                     help="fraction of the ensemble's samples drawn in proportion to kappa I_b")
     ap.add_argument("--band-samples", type=int, default=12800, help="samples per band (128^3 learned part)")
     ap.add_argument("--configs", default="4,1", help="step line: main workload index[,extra workload index]")

@@ -107,7 +107,7 @@ def band_norms(spec, band_pts, p_nodes, x_lo, x_hi, targets):
 
 
 def train_bands(lines, spec, p_nodes, x_lo=0.01, x_hi=0.3, band_pts=64, n_per_band=12800, batch=256,
-                steps=24000, lr0=3e-3, lr1=1e-5, seed=0, group=2048, log_every=0, emission_mix=0.0):
+                steps=24000, lr0=3e-3, lr1=1e-5, seed=0, group=2048, log_every=0, emission_mix=0.5):
     """Train a spectral-band ensemble on samples drawn from line-by-line tables: one
     network per band_pts wavenumbers, groups of up to `group` networks per library
     call; a fraction emission_mix of the samples drawn in proportion to kappa I_b.  Returns (params [n_bands * RT_MLP_NPARAM], norms [n_bands, 10], history)
