@@ -514,6 +514,16 @@ rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *sta
  */
 rt_status rt_alu_probe(double *out, void *stream);
 
+/*
+ * rt_wait_probe -- exercises the bounded waits that guard the library's bulk copies and
+ * tensor-core products (failure detection without a fault): one block waits on an
+ * mbarrier with the kernels' bounded try-wait loop for `limit` iterations (1 .. 2^24).
+ * arrive = 0: nothing arrives, the wait gives up and RT_DEV_TIMEOUT is OR-ed into the
+ * device status word (rt_status_read then returns RT_E_TIMEOUT); arrive = 1: the
+ * barrier completes first and the status is left as it was.  Asynchronous.
+ */
+rt_status rt_wait_probe(uint32_t limit, int32_t arrive, uint32_t *status, void *stream);
+
 /* Synchronise the stream and translate a device status word into an rt_status. */
 rt_status rt_status_read(const uint32_t *status, void *stream);
 

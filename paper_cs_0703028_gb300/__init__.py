@@ -92,6 +92,7 @@ _SIGNATURES = {
                             ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_tc_selftest": ([_P, _P, _P, _P, _P], ct.c_int),
     "rt_alu_probe": ([_P, _P], ct.c_int),
+    "rt_wait_probe": ([ct.c_uint32, ct.c_int32, _P, _P], ct.c_int),
     "rt_trace_mlp": ([_P, _P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,
                       ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_mlp_make_samples": ([_P, ct.c_int32, _P, _P, ct.c_float, ct.c_float, ct.c_uint64, ct.c_int64,

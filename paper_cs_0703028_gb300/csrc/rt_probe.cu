@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "rt_common.cuh"
+#include "rt_tc.cuh"
 
 namespace rt {
 namespace {
@@ -42,7 +43,35 @@ __global__ void __launch_bounds__(kProbeThreads) k_rcp_probe(float *out) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// The bounded-wait path the library's kernels take when a copy or a product never
+// completes: one mbarrier that expects one arrival, waited on with the bounded
+// try-wait loop of the tensor-core kernels (tc::mbar_wait) for `limit` iterations.
+// With arrive = 0 nothing arrives, the wait gives up, and the status word receives
+// RT_DEV_TIMEOUT, as a timed-out kernel reports it; with arrive = 1 thread 0 arrives
+// first and the wait succeeds.
+__global__ void k_wait_probe(uint32_t limit, int arrive, uint32_t *status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(&bar)) : "memory");
+  __syncthreads();
+  const int ok = tc::mbar_wait(&bar, 0, limit) ? 1 : 0;
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) status_or(status, RT_DEV_TIMEOUT);
+}
+
 }  // namespace
+
+rt_status wait_probe(uint32_t limit, int32_t arrive, uint32_t *status, cudaStream_t st) {
+  if (!status) return fail(RT_E_INVAL, "rt_wait_probe: status is NULL");
+  if (limit < 1 || limit > (1u << 24)) return fail(RT_E_INVAL, "rt_wait_probe: limit must be in [1, 2^24]");
+  k_wait_probe<<<1, 32, 0, st>>>(limit, arrive ? 1 : 0, status);
+  RT_CUDA_TRY(cudaGetLastError());
+  return RT_OK;
+}
 
 rt_status alu_probe(double *out, cudaStream_t st) {
   if (!out) return fail(RT_E_INVAL, "rt_alu_probe: out is NULL");
@@ -89,4 +118,8 @@ rt_status alu_probe(double *out, cudaStream_t st) {
 
 extern "C" rt_status rt_alu_probe(double *out, void *stream) {
   return rt::alu_probe(out, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_wait_probe(uint32_t limit, int32_t arrive, uint32_t *status, void *stream) {
+  return rt::wait_probe(limit, arrive, status, (cudaStream_t)stream);
 }
