@@ -1072,11 +1072,11 @@ def run_surrogate128(args):
     p_nodes = np.exp(np.linspace(np.log(0.5), np.log(5.0), 16))
     gs, keep = rt.make_grid(g)
     kap = rt.build_kappa(lines, spec)
-    nbands = surrogate.band_count(spec, args.bands)
+    nbands = surrogate.band_count(spec, args.bands128)
     torch.cuda.synchronize()
     t0 = time.time()
-    P, norms, hist = surrogate.train_bands(lines, spec, p_nodes, 0.01, 0.3, band_pts=args.bands,
-                                           n_per_band=args.band_samples, batch=args.band_batch,
+    P, norms, hist = surrogate.train_bands(lines, spec, p_nodes, 0.01, 0.3, band_pts=args.bands128,
+                                           n_per_band=args.band_samples, batch=args.band_batch128,
                                            steps=int(str(args.band_steps).split(",")[-1]), lr0=args.band_lr,
                                            group=65535, log_every=500, emission_mix=args.band_mix)
     torch.cuda.synchronize()
@@ -1098,7 +1098,7 @@ def run_surrogate128(args):
         return ab
 
     table = lambda t, m, f: rt.trace(gs, kap, spec, t, n_rays=m, n_rays_total=m, flags=f)
-    ens = lambda t, m, f: rt.trace_mlp_bands(gs, args.bands, P, norms, spec, t, n_rays=m, n_rays_total=m, flags=f)
+    ens = lambda t, m, f: rt.trace_mlp_bands(gs, args.bands128, P, norms, spec, t, n_rays=m, n_rays_total=m, flags=f)
     lbl = lambda t, m, f: rt.trace_lbl(gs, lines, spec, t, n_rays=m, n_rays_total=m, flags=f)
     tallies["table"] = timed("table", table, n)
     tallies["ensemble"] = timed("ensemble", ens, n)
@@ -1115,11 +1115,11 @@ def run_surrogate128(args):
     res = {"metric": "ray-cell steps/s, spectral-band ensemble walk vs table and line-by-line walks",
            "value": walks["ensemble"]["ray_cell_steps_per_s"], "unit": "ray-cell steps/s", "higher_is_better": True,
            "config": {"workload": f"box128 learned part: 128^3, 100k Voigt lines, 64 T x 400k nu, {n} rays "
-                                  f"(all three walks on {n_sub}); ensemble of {nbands} networks x {args.bands} "
+                                  f"(all three walks on {n_sub}); ensemble of {nbands} networks x {args.bands128} "
                                   f"wavenumbers, {args.band_samples} samples per band (16 p x 64 T tables)"},
            "training": {"seconds": train_s, "steps": hist[-1][0] + 1 if hist else 0,
                         "loss_first": hist[0][1] if hist else None, "loss_last": hist[-1][1] if hist else None,
-                        "batch_per_band": args.band_batch, "lr0": args.band_lr, "emission_mix": args.band_mix},
+                        "batch_per_band": args.band_batch128, "lr0": args.band_lr, "emission_mix": args.band_mix},
            "walks": walks,
            "ensemble_vs_table": err(tallies["ensemble"], tallies["table"]),
            "subset_vs_lbl": {"table": err(sub["table"], sub["lbl"]), "ensemble": err(sub["ensemble"], sub["lbl"])},
@@ -1143,9 +1143,11 @@ def main():
     ap.add_argument("--epochs", default="1,8,32", help="comma-separated epoch counts (one network each)")
     ap.add_argument("--objective", default="mse", choices=["mse"])
     ap.add_argument("--rays", type=int, default=50_000_000)
-    ap.add_argument("--bands", type=int, default=64, help="wavenumbers per network of the ensemble (0: none)")
+    ap.add_argument("--bands", type=int, default=32, help="wavenumbers per network of the ensemble (0: none)")
     ap.add_argument("--band-steps", default="24000", help="comma-separated training steps (one ensemble each)")
-    ap.add_argument("--band-batch", type=int, default=256)
+    ap.add_argument("--band-batch", type=int, default=128)
+    ap.add_argument("--bands128", type=int, default=64, help="128^3 learned part: wavenumbers per network")
+    ap.add_argument("--band-batch128", type=int, default=256, help="128^3 learned part: batch per network")
     ap.add_argument("--band-lr", type=float, default=3e-3)
     ap.add_argument("--band-mix", type=float, default=0.5,
                     help="fraction of the ensemble's samples drawn in proportion to kappa I_b")
