@@ -271,3 +271,19 @@ def test_adaptive_points_exclude_fixed_points(rt):
         rt.build_kappa(c0.lines, bad)
     with pytest.raises(rt.RtError):
         rt.build_kappa(c0.lines, replace(c0.spec, kappa_min=-1.0))
+
+
+def test_c1_full_size_adaptive_points_sampled_columns(rt, c1_columns):
+    # Adaptive points per line on the full 64 x 100k Voigt table of the 20k-line list (the
+    # configuration `bench.py --workload next` times): 600 random columns and both edges
+    # against the oracle's adaptive table; the evaluation count over the whole table exact.
+    from dataclasses import replace
+    case, cols, _ = c1_columns
+    spec = replace(case.spec, kappa_min=1e-3)
+    ref = okappa.kappa_columns(case.lines, spec, cols)
+    got, ev, st = _gpu_table(rt, case.lines, spec)
+    assert st == 0
+    assert ev == okappa.profile_evals(case.lines, spec)
+    nz = ref > 0
+    assert np.array_equal(got[:, cols] > 0, nz)
+    assert _rel(got[:, cols][nz], ref[nz]).max() <= TOL

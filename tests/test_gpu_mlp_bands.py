@@ -267,3 +267,49 @@ def test_band_samples_follow_the_emission_weights(rt, mix):
             cnt = np.bincount(j[sel], minlength=8)
             m = sel.sum()
             assert np.all(np.abs(cnt - m * p) <= 5 * np.sqrt(m * p * (1 - p)) + 1), (b, k, cnt, m * p)
+
+
+def test_banded_walk_at_the_learned_part_size(rt):
+    # The 64^3 learned-part workload in the benchmark's configuration: 3125 networks of 32
+    # wavenumbers over 100k wavenumbers, 5e7 rays grouped by band.  The visits do not depend
+    # on kappa, so the step count must equal the table walk's on the same rays exactly; the
+    # tally must close its energy balance; and a sample of rays' emission weights must follow
+    # each ray's own band network (recorded weights against the FP64 oracle network).
+    import torch
+    case = synth.config(2)
+    spec, g = case.spec, case.grid
+    band_pts = 32
+    nb = -(-spec.n_nu // band_pts)
+    base = _spread_net(60)
+    P = torch.from_numpy(np.tile(base, nb)).cuda()
+    norms, lo, hi = _band_norms(rt, spec, band_pts)
+    gs, keep = rt.make_grid(g)
+    n = case.n_rays
+    t = rt.Tally(g.ncells)
+    t.zero()
+    rec = rt.Record(2000, g.nx + g.ny + g.nz + 4)
+    rt.trace_mlp_bands(gs, band_pts, P, norms, spec, t, n_rays=n, record=rec)
+    ab, sc, st = t.read()
+    steps_b = int(t.steps.item())
+    kap = torch.full((spec.nT, spec.n_nu), 1e-3, dtype=torch.float32, device="cuda")
+    t2 = rt.Tally(g.ncells)
+    t2.zero()
+    rt.trace(gs, kap, spec, t2, n_rays=n)
+    t2.read()
+    assert steps_b == int(t2.steps.item())
+    assert sc[3] < 1e-5
+    # the recorded rays' weights: 4 pi V kappa I_b dnu ncells n_nu / N with kappa from the ray's band network
+    cell, j = otrace.emission_indices(g.ncells, spec.n_nu, 0, 0, 2000)
+    w_gpu = rec.weight.cpu().numpy().astype(np.float64)
+    T = g.T[cell].astype(np.float64)
+    nu = spec.nu_min + j * spec.dnu
+    raw = np.stack([np.log(nu), T, np.full_like(T, np.float32(spec.p_ref_atm)),
+                    np.full_like(T, np.float32(spec.x_ref))], 1)
+    logk = np.array([_oracle_logk_band(base, lo[jj // band_pts], hi[jj // band_pts], raw[i:i + 1])[0]
+                     for i, jj in enumerate(j)])
+    from oracle import physics as ph
+    V = g.hx * g.hy * g.hz
+    w_ref = (4 * math.pi * V * 100.0 * np.exp(logk) * ph.planck_wavenumber(nu, T) * 100.0 * spec.dnu
+             * g.ncells * spec.n_nu / n)
+    rel = np.abs(w_gpu - w_ref) / w_ref
+    assert np.median(rel) < 1e-2 and rel.max() < 5e-2, (np.median(rel), rel.max())
