@@ -177,6 +177,13 @@ WORKLOADS = {
 WALK_BYTES_PER_STEP = {4: 16, 1: 12}
 PROFILE_SUMMARIES = {4: ("k_kappa_box128_voigt100k.md", "k_walk_box128_voigt100k.md"),
                      1: ("k_kappa_box32_voigt20k.md", "k_walk_box32_voigt20k.md")}
+# what bounds the walk instead of HBM, from those profiles (tables and cells L2-resident)
+WALK_LIMITERS = {
+    4: {"dram_bytes_per_step": 0.095, "l2_hit_pct": 98.9, "alu_pipe_pct": 63.2, "issue_pct": 69.1,
+        "l1_data_pipe_pct": 70.5, "note": "rays grouped by wavenumber; ALU, issue and L1 bind together"},
+    1: {"dram_bytes_per_step": 0.23, "l2_hit_pct": 96.7, "alu_pipe_pct": 57.2, "issue_pct": 67.3,
+        "l1_data_pipe_pct": 66.2, "note": "ungrouped; gathers L2-resident, ALU and L1 bind together"},
+}
 
 
 def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
@@ -386,7 +393,9 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
                             "traffic": _profiled_traffic(prof_w, ["rt_trace.cu", "rt_walk.cuh",
                                                                   "rt_common.cuh"]),
                             "bytes_per_step": bps, "peak_source": "measured HBM copy (MEASURED_PEAKS.json)",
-                            "note": "tables L2-resident; latency- and issue-bound (profiles/)"}
+                            "limiters": {**WALK_LIMITERS[index], "source": "profiles/" + prof_w},
+                            "note": "tables L2-resident: the walk is bound by the ALU pipe, issue and the L1 "
+                                    "data pipe, not by HBM (limiters, from the ncu summary)"}
     return out
 
 
