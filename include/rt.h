@@ -441,7 +441,13 @@ rt_status rt_mlp_make_samples(const float *tables, int32_t n_p, const float *p_n
  * only has to resolve that band's lines, which one network for the whole window
  * cannot.  Parameters: device [n_nets][RT_MLP_NPARAM] (network b at b *
  * RT_MLP_NPARAM); norms: DEVICE array of n_nets rt_mlp_norm (each band's log nu
- * range and output scale).
+ * range and output scale).  The caller owns every buffer; the calls allocate only
+ * stream-ordered scratch (BF16 weight tiles: 96 KB per network for a walk, 192 KB
+ * for training, plus the training step's activations and gradient partials; a
+ * banded walk also 4 bytes per ray for the band-grouped order).  Bad sizes, NULL
+ * buffers or out-of-range arguments return RT_E_INVAL before any launch; a bounded
+ * device wait that gives up sets RT_DEV_TIMEOUT in the status word.  The norms are
+ * read on the device and are not validated.
  */
 
 /* Training samples for an ensemble: n_per_band samples per band b (rows b n_per_band
