@@ -125,3 +125,78 @@ def test_tuning_round_trip_and_validation():
                                    "walk_group": 0}
     finally:
         rt.set_tuning(**before)
+
+
+def test_adaptive_points_spec_rejected_on_host():
+    L = rt.lib()
+    case = synth.config(0)
+    lines, keep = rt.make_lines(case.lines)
+    dummy = ct.c_void_p(16)
+    for km in (-1e-3, math.nan, math.inf):
+        bad = rt.make_spectral(case.spec)
+        bad.kappa_min = km
+        st, msg = _status(lambda: L.rt_build_kappa(ct.byref(lines), ct.byref(bad), dummy, None, None, None))
+        assert st == rt.RT_E_INVAL and "kappa_min" in msg
+    # adaptive windows and fixed points per line exclude each other
+    bad = rt.make_spectral(case.spec)
+    bad.kappa_min, bad.points_per_line = 1e-3, 128
+    st, msg = _status(lambda: L.rt_build_kappa(ct.byref(lines), ct.byref(bad), dummy, None, None, None))
+    assert st == rt.RT_E_INVAL and "exclude" in msg
+
+
+def test_ensemble_entry_points_reject_bad_input_on_host():
+    # every case fails validation before any allocation or launch
+    L = rt.lib()
+    case = synth.config(0)
+    spec = rt.make_spectral(case.spec)
+    d = ct.c_void_p(16)
+    samp = lambda bp=32, lo=0.01, hi=0.3, mix=0.5, n=100, tables=d: L.rt_mlp_make_samples_bands(
+        tables, 2, d, ct.byref(spec), bp, lo, hi, mix, 1, n, d, d, None)
+    assert samp(mix=1.5) == rt.RT_E_INVAL
+    assert samp(mix=math.nan) == rt.RT_E_INVAL
+    assert samp(bp=0) == rt.RT_E_INVAL
+    assert samp(lo=0.0) == rt.RT_E_INVAL
+    assert samp(n=-1) == rt.RT_E_INVAL
+    assert samp(tables=None) == rt.RT_E_INVAL
+    big = rt.make_spectral(case.spec)
+    big.n_nu = 70000
+    st, msg = _status(lambda: L.rt_mlp_make_samples_bands(d, 2, d, ct.byref(big), 1, 0.01, 0.3, 0.5, 1, 100,
+                                                           d, d, None))
+    assert st == rt.RT_E_INVAL and "65535" in msg
+
+    train = lambda nn=2, n=1024, b=256, lr0=1e-3, s0=1, ns=4, tot=4: L.rt_mlp_train_steps_nets(
+        nn, d, d, d, d, d, d, n, b, d, lr0, 1e-5, s0, ns, tot, None, None, None)
+    assert train(nn=0) == rt.RT_E_INVAL
+    assert train(b=2048) == rt.RT_E_INVAL
+    assert train(b=0) == rt.RT_E_INVAL
+    assert train(lr0=math.nan) == rt.RT_E_INVAL
+    assert train(s0=0) == rt.RT_E_INVAL
+    assert train(s0=3, ns=4, tot=4) == rt.RT_E_INVAL
+    assert train(ns=0) == rt.RT_OK            # no step: nothing allocated or launched
+
+    fwd = lambda nn=2, n=100, p=d: L.rt_mlp_forward_nets(nn, p, d, d, n, d, None, None)
+    assert fwd(nn=0) == rt.RT_E_INVAL
+    assert fwd(nn=65536) == rt.RT_E_INVAL
+    assert fwd(n=-1) == rt.RT_E_INVAL
+    assert fwd(p=None) == rt.RT_E_INVAL
+    assert fwd(n=0, p=None) == rt.RT_OK       # no sample: buffers are not read
+
+    g = rt.rt_grid(64, 1, 1, 0, 1 / 64, math.inf, math.inf, 16, None, None)
+    t = rt.rt_tally_buf(16, 16, 16, 16)
+    walk = lambda bp=32, p=d, nm=d, flags=0, n=10, s=spec: L.rt_trace_mlp_bands(
+        ct.byref(g), bp, p, nm, ct.byref(s), 0, n, max(n, 10), 0, 0, flags, ct.byref(t), None, None)
+    assert walk(p=None) == rt.RT_E_INVAL
+    assert walk(nm=None) == rt.RT_E_INVAL
+    assert walk(bp=0) == rt.RT_E_INVAL
+    assert walk(flags=rt.RT_SRC_BEAM) == rt.RT_E_INVAL
+    st, msg = _status(lambda: walk(bp=1, s=big))
+    assert st == rt.RT_E_INVAL and "65535" in msg
+    st, msg = _status(lambda: walk(n=1 << 32))
+    assert st == rt.RT_E_INVAL and "2^32" in msg
+
+
+def test_wait_probe_rejects_bad_input_on_host():
+    L = rt.lib()
+    assert L.rt_wait_probe(1000, 1, None, None) == rt.RT_E_INVAL
+    assert L.rt_wait_probe(0, 1, ct.c_void_p(16), None) == rt.RT_E_INVAL
+    assert L.rt_wait_probe((1 << 24) + 1, 1, ct.c_void_p(16), None) == rt.RT_E_INVAL
