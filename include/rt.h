@@ -396,7 +396,8 @@ rt_status rt_mlp_train_step(float *params, float *adam_m, float *adam_v, float *
  * cosine learning rate
  *   lr(s) = lr1 + (lr0 - lr1) (1 + cos(pi s / max(1, total_steps - 1))) / 2
  * evaluated in binary64 and rounded to binary32.  losses (optional device
- * [n_steps]) receives each step's loss.  Requires 1 <= batch <= n and
+ * [n_steps]) receives each step's loss; grad receives the last step's gradient
+ * (the earlier steps' are not stored).  Requires 1 <= batch <= n and
  * step_first - 1 + n_steps <= total_steps.  Asynchronous.
  */
 rt_status rt_mlp_train_steps(float *params, float *adam_m, float *adam_v, float *grad,
@@ -510,6 +511,13 @@ rt_status rt_trace_lbl(const rt_grid *grid, const rt_lines *lines, const rt_spec
 /* Self-test of the tensor-core path: D = A B^T for 128x128 FP32 row-major A, B
  * (rounded to BF16), D FP32 row-major [128][128].  Asynchronous. */
 rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream);
+
+/* Self-test of the transposed operand path: D = A^T B (D[m][n] = sum_k A[k][m]
+ * B[k][n]) for 128x128 FP32 row-major A, B (rounded to BF16), both written as tiles
+ * with one row per contraction index and read by the tensor core MN-major, as the
+ * training backward pass reads its output-gradient and activation tiles.
+ * Asynchronous. */
+rt_status rt_tc_selftest_mn(const float *A, const float *B, float *D, uint32_t *status, void *stream);
 
 /*
  * rt_alu_probe -- measured ALU ceilings of the current GPU, for the line sum's

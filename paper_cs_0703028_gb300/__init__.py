@@ -91,6 +91,7 @@ _SIGNATURES = {
     "rt_mlp_train_steps": ([_P, _P, _P, _P, _P, _P, ct.c_int64, ct.c_int64, _P, ct.c_double, ct.c_double,
                             ct.c_int32, ct.c_int32, ct.c_int32, _P, _P, _P], ct.c_int),
     "rt_tc_selftest": ([_P, _P, _P, _P, _P], ct.c_int),
+    "rt_tc_selftest_mn": ([_P, _P, _P, _P, _P], ct.c_int),
     "rt_alu_probe": ([_P, _P], ct.c_int),
     "rt_wait_probe": ([ct.c_uint32, ct.c_int32, _P, _P], ct.c_int),
     "rt_trace_mlp": ([_P, _P, _P, _P, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint32,

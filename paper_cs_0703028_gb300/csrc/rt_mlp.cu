@@ -141,13 +141,18 @@ struct FwdSmem {
   uint64_t bar_w, bar_mma;
   uint32_t tmem;
   float red[4];
+  float yh[kH];               // the head's partial sum over the second half of the units
 };
+
+// Two threads per sample row, as in the backward pass: thread t takes row t mod 128
+// and half t / 128 of the units of every layer.
+constexpr int kFwdThreads = 2 * kH;
 
 // Networks of an ensemble along grid.y: network `net` reads its parameters, tiles,
 // samples (n rows at net * in_stride) and activations at net times the per-network
 // strides.
 template <bool TRAIN>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kFwdThreads)
 k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long long tile_stride, Norm N1,
           const Norm *__restrict__ norms, const float *__restrict__ inputs, const float *__restrict__ targets,
           long long n, long long in_stride, float *__restrict__ Z, float *__restrict__ dy,
@@ -167,7 +172,10 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   } else {
     out += net * in_stride;
   }
-  const long long row = (long long)blockIdx.x * kH + tid;
+  const int r = tid & (kH - 1);          // sample row within the tile
+  const int cb = (tid >> 7) * (kH / 2);  // first unit of the thread's half
+  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // the warp's tensor-memory lanes
+  const long long row = (long long)blockIdx.x * kH + r;
   const bool valid = row < n;
 
   if (tid == 0) {
@@ -190,7 +198,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   float u[4];
   normalise(inputs, row, valid, N, u);
 #pragma unroll 1
-  for (int c0 = 0; c0 < kH; c0 += 8) {
+  for (int c0 = cb; c0 < cb + kH / 2; c0 += 8) {
     float h[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -201,7 +209,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     }
     uint4 pk = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
                           pack_bf16x2(h[6], h[7]));
-    *reinterpret_cast<uint4 *>(&S.A[tile_index(tid, c0)]) = pk;
+    *reinterpret_cast<uint4 *>(&S.A[tile_index(r, c0)]) = pk;
   }
   int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
   int mma_pending = -1;  // parity of a product whose completion wait gave up
@@ -211,7 +219,10 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   for (int l = 0; l < 3; ++l) {
     tc::fence_smem_to_async();
     tc::fence_before_sync();
-    if (__syncthreads_or(timeout)) break;
+    if (__syncthreads_or(timeout)) {  // timeout block-uniform from here on
+      timeout = 1;
+      break;
+    }
     if (tid == 0) {
       tc::fence_after_sync();
       tc::mma_128x128x128(tmem, S.A, S.W[l]);
@@ -219,15 +230,16 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     }
     timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)(l & 1), kWaitLimit) ? 0 : 1;
     if (__syncthreads_or(timeout)) {
+      timeout = 1;
       mma_pending = l & 1;
       break;
     }
     tc::fence_after_sync();
     const float *bias = S.sp.b[l];
 #pragma unroll 1
-    for (int c0 = 0; c0 < kH; c0 += 32) {
+    for (int c0 = cb; c0 < cb + kH / 2; c0 += 32) {
       float acc[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+      tc::tmem_ld32(tmem + lanes + (uint32_t)c0, acc);
 #pragma unroll
       for (int i = 0; i < 32; i += 8) {
         float h[8];
@@ -242,7 +254,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
         if (l < 2) {
           uint4 pk = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]),
                                 pack_bf16x2(h[4], h[5]), pack_bf16x2(h[6], h[7]));
-          *reinterpret_cast<uint4 *>(&S.A[tile_index(tid, c0 + i)]) = pk;
+          *reinterpret_cast<uint4 *>(&S.A[tile_index(r, c0 + i)]) = pk;
         }
       }
     }
@@ -255,13 +267,17 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
       tc::mbar_wait(&S.bar_w, 0, kWaitLimit);
       if (mma_pending >= 0) tc::mbar_wait(&S.bar_mma, (uint32_t)mma_pending, kWaitLimit);
     }
-  } else {
+  }
+  if (!timeout && cb != 0) S.yh[r] = y;
+  __syncthreads();
+  if (!timeout && cb == 0) {
+    y += S.yh[r];
     y += S.sp.b5;
     if (TRAIN) {
       const float ts = valid ? (targets[row] - N.mean) / N.scale : 0.0f;
-      const float r = valid ? (y - ts) : 0.0f;
-      if (valid) dy[row] = r / (float)n;
-      float l2 = 0.5f * r * r / (float)n * loss_scale;
+      const float res = valid ? (y - ts) : 0.0f;
+      if (valid) dy[row] = res / (float)n;
+      float l2 = 0.5f * res * res / (float)n * loss_scale;
       for (int o = 16; o > 0; o >>= 1) l2 += __shfl_down_sync(0xffffffffu, l2, o);
       if (lane == 0) S.red[warp] = l2;
     } else if (valid) {
@@ -277,11 +293,14 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   }
 }
 
+// dZ and H are written one row per sample (16-byte stores of 8 units) and serve
+// both products: dZ K-major as the A operand of dH = dZ W, and dZ, H read MN-major
+// (as their transposes) for dW = dZ^T H.  They come first, so that a product that
+// reads past either tile stays inside the block's shared memory.
 struct BwdSmem {
-  uint16_t Wt[kTileElems];   // current layer's transposed weights, rows = in
   uint16_t dZ[kTileElems];   // rows = samples, k = out
-  uint16_t dZt[kTileElems];  // rows = out, k = samples
-  uint16_t Ht[kTileElems];   // rows = in, k = samples
+  uint16_t H[kTileElems];    // rows = samples, k = in
+  uint16_t Wt[kTileElems];   // current layer's transposed weights, rows = in
   float buf[kH][kH + 1];     // FP32 [sample][column] for column sums (padded: no bank conflicts)
   float u[kH][4];
   float dyv[kH];
@@ -293,6 +312,13 @@ __device__ __forceinline__ void put_bf16(uint16_t *tile, int r, int k, float v) 
   tile[tile_index(r, k)] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// elements (r, k0 .. k0 + 7) of a K-major tile (k0 a multiple of 8): one 16-byte store
+__device__ __forceinline__ void put_bf16x8(uint16_t *tile, int r, int k0, const float (&v)[8]) {
+  *reinterpret_cast<uint4 *>(&tile[tile_index(r, k0)]) =
+      make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                 pack_bf16x2(v[6], v[7]));
+}
+
 // column c of buf summed over the 128 samples (thread c), after a barrier
 __device__ __forceinline__ float column_sum(const BwdSmem &S, int c) {
   float s = 0.0f;
@@ -301,7 +327,13 @@ __device__ __forceinline__ float column_sum(const BwdSmem &S, int c) {
   return s;
 }
 
-__global__ void __launch_bounds__(128)
+// Two threads per sample row: thread t takes row t mod 128 (its warp reads that
+// row's tensor-memory lane) and half t / 128 of the 128 units in every epilogue.
+// The column sums (bias gradients) and the first layer's gradient run on the first
+// 128 threads, one column each.
+constexpr int kBwdThreads = 2 * kH;
+
+__global__ void __launch_bounds__(kBwdThreads)
 k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long long tile_stride, Norm N1,
           const Norm *__restrict__ norms, const float *__restrict__ inputs, long long n, long long in_stride,
           const float *__restrict__ Z, const float *__restrict__ dy, float *__restrict__ Gpart,
@@ -319,7 +351,10 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   // the tiles in a fixed order by k_grad_adam)
   float *G = Gpart + (net * gridDim.x + blockIdx.x) * kGradStride;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const long long row = (long long)blockIdx.x * kH + tid;
+  const int r = tid & (kH - 1);          // sample row within the tile
+  const int cb = (tid >> 7) * (kH / 2);  // first unit of the thread's half
+  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // the warp's tensor-memory lanes
+  const long long row = (long long)blockIdx.x * kH + r;
   const bool valid = row < n;
 
   if (tid == 0) {
@@ -336,33 +371,35 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     tc::mbar_arrive_expect_tx(&S.bar_w, kTileBytes);
     tc::bulk_g2s(S.Wt, tiles + 5 * kTileElems, kTileBytes, &S.bar_w);
   }
-  float u[4];
-  normalise(inputs, row, valid, N, u);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) S.u[tid][k] = u[k];
   const float dyv = valid ? dy[row] : 0.0f;
-  S.dyv[tid] = dyv;
+  if (tid < kH) {
+    float u[4];
+    normalise(inputs, row, valid, N, u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) S.u[r][k] = u[k];
+    S.dyv[r] = dyv;
+  }
 
   // head: dw5 = sum_s dy h4, db5 = sum_s dy (loads issued 32 at a time)
 #pragma unroll 1
-  for (int c0 = 0; c0 < kH; c0 += 32) {
+  for (int c0 = cb; c0 < cb + kH / 2; c0 += 32) {
     float z4[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) z4[i] = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) S.buf[tid][c0 + i] = dyv * z4[i] * sigmoid_fast(z4[i]);
+    for (int i = 0; i < 32; ++i) S.buf[r][c0 + i] = dyv * z4[i] * sigmoid_fast(z4[i]);
   }
   __syncthreads();
-  G[oW5 + tid] = column_sum(S, tid);
+  if (tid < kH) G[oW5 + tid] = column_sum(S, tid);
   if (tid == 0) {
     float d5 = 0.0f;
-    for (int r = 0; r < kH; ++r) d5 += S.dyv[r];
+    for (int q = 0; q < kH; ++q) d5 += S.dyv[q];
     G[oB5] = d5;
   }
   __syncthreads();
-  // dz4 = dy w5 silu'(z4) -> dZ, dZ^T, buf (for db4); h3 -> H^T (for dW4)
+  // dz4 = dy w5 silu'(z4) -> dZ, buf (for db4); h3 -> H (for dW4)
 #pragma unroll 1
-  for (int c0 = 0; c0 < kH; c0 += 16) {
+  for (int c0 = cb; c0 < cb + kH / 2; c0 += 16) {
     float z4[16], z3[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -370,18 +407,22 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
       z3[i] = valid ? Z[zidx(2, c0 + i, n, row)] : 0.0f;
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int c = c0 + i;
-      const float s4 = sigmoid_fast(z4[i]);
-      const float dz = dyv * __ldg(P + oW5 + c) * (s4 * (1.0f + z4[i] * (1.0f - s4)));
-      S.buf[tid][c] = dz;
-      put_bf16(S.dZ, tid, c, dz);
-      put_bf16(S.dZt, c, tid, dz);
-      put_bf16(S.Ht, c, tid, z3[i] * sigmoid_fast(z3[i]));
+    for (int i = 0; i < 16; i += 8) {
+      float dz[8], h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + i + q;
+        const float s4 = sigmoid_fast(z4[i + q]);
+        dz[q] = dyv * __ldg(P + oW5 + c) * (s4 * (1.0f + z4[i + q] * (1.0f - s4)));
+        S.buf[r][c] = dz[q];
+        h[q] = z3[i + q] * sigmoid_fast(z3[i + q]);
+      }
+      put_bf16x8(S.dZ, r, c0 + i, dz);
+      put_bf16x8(S.H, r, c0 + i, h);
     }
   }
   __syncthreads();
-  G[oB4 + tid] = column_sum(S, tid);
+  if (tid < kH) G[oB4 + tid] = column_sum(S, tid);
 
   int timeout = 0;
   bool aborted = false;
@@ -401,7 +442,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     }
     if (tid == 0) {
       tc::fence_after_sync();
-      tc::mma_128x128x128(tmem, S.dZt, S.Ht);        // dW_l[out][in]
+      tc::mma_128x128x128_mn(tmem, S.dZ, S.H);       // dW_l[out][in] = dZ^T H
       tc::mma_128x128x128(tmem + kH, S.dZ, S.Wt);    // dH_{l-1}[sample][in]
       tc::mma_commit(&S.bar_mma);
     }
@@ -419,7 +460,7 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     float *gW = G + (l == 4 ? oW4 : (l == 3 ? oW3 : oW2));
     const long long zl = (long long)(l - 2);  // block of z_{l-1}
 #pragma unroll 1
-    for (int c0 = 0; c0 < kH; c0 += 32) {
+    for (int c0 = cb; c0 < cb + kH / 2; c0 += 32) {
       // this chunk's pre-activations first, so that their loads overlap the
       // tensor-memory reads below
       float z[32], zp[32];
@@ -429,47 +470,54 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
         zp[i] = (valid && l > 2) ? Z[zidx(zl - 1, c0 + i, n, row)] : 0.0f;
       }
       float acc[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+      tc::tmem_ld32(tmem + lanes + (uint32_t)c0, acc);
 #pragma unroll
       for (int i = 0; i < 32; i += 4)
-        *reinterpret_cast<float4 *>(gW + tid * kH + c0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kH + c0), acc);
+        *reinterpret_cast<float4 *>(gW + r * kH + c0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+      tc::tmem_ld32(tmem + lanes + (uint32_t)(kH + c0), acc);
+      uint32_t pd[4], ph[4];  // BF16 pairs of dz and h, stored 8 units at a time
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const int c = c0 + i;
         const float s = sigmoid_fast(z[i]);
         const float dz = acc[i] * (s * (1.0f + z[i] * (1.0f - s)));
-        S.buf[tid][c] = dz;
+        S.buf[r][c] = dz;
         if (l > 2) {
-          put_bf16(S.dZ, tid, c, dz);
-          put_bf16(S.dZt, c, tid, dz);
-          put_bf16(S.Ht, c, tid, zp[i] * sigmoid_fast(zp[i]));
+          const uint32_t bd = __bfloat16_as_ushort(__float2bfloat16_rn(dz));
+          const uint32_t bh = __bfloat16_as_ushort(__float2bfloat16_rn(zp[i] * sigmoid_fast(zp[i])));
+          const int w = (i >> 1) & 3;
+          pd[w] = (i & 1) ? (pd[w] | (bd << 16)) : bd;
+          ph[w] = (i & 1) ? (ph[w] | (bh << 16)) : bh;
+          if ((i & 7) == 7) {
+            *reinterpret_cast<uint4 *>(&S.dZ[tile_index(r, c - 7)]) = make_uint4(pd[0], pd[1], pd[2], pd[3]);
+            *reinterpret_cast<uint4 *>(&S.H[tile_index(r, c - 7)]) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+          }
         }
       }
     }
     tc::fence_before_sync();
     __syncthreads();
     const int ob = (l == 4 ? oB3 : (l == 3 ? oB2 : oB1));
-    G[ob + tid] = column_sum(S, tid);
-    if (l == 2) {  // first layer: dW1[c][k] = sum_s dz1[s][c] u[s][k]
+    if (tid < kH) G[ob + tid] = column_sum(S, tid);
+    if (l == 2 && tid < kH) {  // first layer: dW1[c][k] = sum_s dz1[s][c] u[s][k]
       float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
-      for (int r = 0; r < kH; ++r) {
-        const float d = S.buf[r][tid];
+      for (int q = 0; q < kH; ++q) {
+        const float d = S.buf[q][tid];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] = fmaf(d, S.u[r][k], g[k]);
+        for (int k = 0; k < 4; ++k) g[k] = fmaf(d, S.u[q][k], g[k]);
       }
       *reinterpret_cast<float4 *>(G + oW1 + tid * 4) = make_float4(g[0], g[1], g[2], g[3]);
     }
     __syncthreads();  // buf is rewritten by the next layer
   }
-  if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
-  if (aborted && tid == 0) {  // let what is still in flight land (bounded) before leaving
+  if (aborted && tid == 0) {  // some thread's wait gave up; let what is still in flight land (bounded)
+    status_or(status, RT_DEV_TIMEOUT);
     if (w_pending >= 0) tc::mbar_wait(&S.bar_w, (uint32_t)w_pending, kWaitLimit);
     if (mma_pending >= 0) tc::mbar_wait(&S.bar_mma, (uint32_t)mma_pending, kWaitLimit);
   }
   if (aborted)  // block-uniform: the partial holds no gradient of this tile
-    for (int i = tid; i < kNParam; i += kH) G[i] = 0.0f;
+    for (int i = tid; i < kNParam; i += kBwdThreads) G[i] = 0.0f;
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -481,54 +529,106 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
 // gradient = sum of the tiles' partials, in tile order (deterministic), and
 // unless `adam` is 0 the Adam update of the FP32 masters with it (Kingma and Ba);
 // with `tiles` given, an updated weight of W2..W4 is also written to its two BF16
-// tile positions (the layout k_mlp_prep writes), ready for the next step
-__global__ void k_grad_adam(const float *__restrict__ part, int nparts, float *__restrict__ grad, int adam,
-                            float *__restrict__ P, float *__restrict__ m, float *__restrict__ v, float lr,
-                            float b1, float b2, float eps, float c1, float c2, uint16_t *__restrict__ tiles) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kNParam) return;
+// tile positions (the layout k_mlp_prep writes), ready for the next step.  The
+// gradient itself is stored only when grad is not NULL (within a run of steps,
+// only the last step's).  Each thread takes PER parameters kAdamThreads apart,
+// all their loads issued before the first update (PER = 4 for an ensemble of at
+// least kAdamWide networks, else 1, so that a single network still fills the GPU).
+constexpr int kAdamThreads = 256, kAdamWide = 64;
+
+__device__ __forceinline__ void adam_tile_write(uint16_t *__restrict__ tiles, int i, float w) {
+  const int mat = (i >= oW2 && i < oW2 + kTileElems) ? 0
+                  : (i >= oW3 && i < oW3 + kTileElems) ? 1
+                  : (i >= oW4 && i < oW4 + kTileElems) ? 2 : -1;
+  if (mat >= 0) {
+    const int e = i - (mat == 0 ? oW2 : (mat == 1 ? oW3 : oW4));
+    const int r = e / kH, k = e % kH;  // row (output unit), column (input unit)
+    const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+    tiles[mat * kTileElems + tile_index(r, k)] = h;
+    tiles[(mat + 3) * kTileElems + tile_index(k, r)] = h;
+  }
+}
+
+template <int PER>
+__global__ void __launch_bounds__(kAdamThreads)
+k_grad_adam(const float *__restrict__ part, int nparts, float *__restrict__ grad, int adam,
+            float *__restrict__ P, float *__restrict__ m, float *__restrict__ v, float lr, float b1, float b2,
+            float eps, float c1, float c2, uint16_t *__restrict__ tiles) {
+  const int i0 = blockIdx.x * (kAdamThreads * PER) + threadIdx.x;
   const long long net = blockIdx.y;  // network of an ensemble: its partials, parameters, moments, tiles
   part += net * nparts * kGradStride;
-  grad += net * kNParam;
+  if (grad) grad += net * kNParam;
   P += net * kNParam;
   if (adam) {
     m += net * kNParam;
     v += net * kNParam;
   }
   if (tiles) tiles += net * 6 * kTileElems;
-  float gi = 0.0f;
-  for (int t = 0; t < nparts; ++t) gi += part[(long long)t * kGradStride + i];
-  grad[i] = gi;
-  if (!adam) return;
-  const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
-  const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
-  m[i] = mi;
-  v[i] = vi;
-  const float pi = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-  P[i] = pi;
-  if (tiles) {
-    const int mat = (i >= oW2 && i < oW2 + kTileElems) ? 0
-                    : (i >= oW3 && i < oW3 + kTileElems) ? 1
-                    : (i >= oW4 && i < oW4 + kTileElems) ? 2 : -1;
-    if (mat >= 0) {
-      const int e = i - (mat == 0 ? oW2 : (mat == 1 ? oW3 : oW4));
-      const int r = e / kH, k = e % kH;  // row (output unit), column (input unit)
-      const uint16_t h = __bfloat16_as_ushort(__float2bfloat16_rn(pi));
-      tiles[mat * kTileElems + tile_index(r, k)] = h;
-      tiles[(mat + 3) * kTileElems + tile_index(k, r)] = h;
+  if (PER == 1) {  // one parameter per thread (few networks, many tile partials each)
+    const int i = i0;
+    if (i >= kNParam) return;
+    float gi = 0.0f;
+    for (int t = 0; t < nparts; ++t) gi += part[(long long)t * kGradStride + i];
+    if (grad) grad[i] = gi;
+    if (!adam) return;
+    const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    P[i] = pi;
+    if (tiles) adam_tile_write(tiles, i, pi);
+    return;
+  }
+  // out-of-range slots read the last parameter (a valid address, no branch in the
+  // loads) and store nothing
+  int ix[PER];
+  float g[PER], pv[PER], mv[PER], vv[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    ix[q] = min(i0 + q * kAdamThreads, kNParam - 1);
+    g[q] = part[ix[q]];
+    if (adam) {
+      pv[q] = P[ix[q]];
+      mv[q] = m[ix[q]];
+      vv[q] = v[ix[q]];
     }
+  }
+#pragma unroll 4
+  for (int t = 1; t < nparts; ++t) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) g[q] += part[(long long)t * kGradStride + ix[q]];
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = i0 + q * kAdamThreads;
+    if (i >= kNParam) continue;
+    if (grad) grad[i] = g[q];
+    if (!adam) continue;
+    const float mi = fmaf(b1, mv[q], (1.0f - b1) * g[q]);
+    const float vi = fmaf(b2, vv[q], (1.0f - b2) * g[q] * g[q]);
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = pv[q] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    P[i] = pi;
+    if (tiles) adam_tile_write(tiles, i, pi);
   }
 }
 
 // Self-test of the tensor-core path: D = A B^T for 128 x 128 x 128, A and B
-// given as FP32 row-major [128][128] (rounded to bf16).
+// given as FP32 row-major [128][128] (rounded to bf16); with MN, D = A^T B with
+// both tiles read MN-major (the backward pass's weight-gradient product).  The MN
+// form keeps each tile 64 KB apart from the next member, so that a product reading
+// past its 32 KB tile stays inside the block's shared memory.
+template <bool MN>
 __global__ void __launch_bounds__(128)
 k_tc_selftest(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ D,
               uint32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  constexpr int kGap = MN ? 2 * kTileElems : kTileElems;
   uint16_t *sA = reinterpret_cast<uint16_t *>(smem_raw);
-  uint16_t *sB = sA + kTileElems;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + kTileElems);
+  uint16_t *sB = sA + kGap;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sB + kGap);
   uint32_t *holder = reinterpret_cast<uint32_t *>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -546,7 +646,8 @@ k_tc_selftest(const float *__restrict__ A, const float *__restrict__ B, float *_
   tc::fence_after_sync();
   const uint32_t tmem = *holder;
   if (tid == 0) {
-    tc::mma_128x128x128(tmem, sA, sB);
+    if (MN) tc::mma_128x128x128_mn(tmem, sA, sB);
+    else tc::mma_128x128x128(tmem, sA, sB);
     tc::mma_commit(bar);
   }
   const int ok = tc::mbar_wait(bar, 0, kWaitLimit) ? 1 : 0;
@@ -852,7 +953,10 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
       }
     }
     // every tile is done with this item (and with the band's weights) before the next
-    if (__syncthreads_or(timeout)) break;
+    if (__syncthreads_or(timeout)) {  // any tile's wait gave up: the block stops, flag uniform
+      timeout = 1;
+      break;
+    }
   }
   if (timeout && tid == 0) status_or(status, RT_DEV_TIMEOUT);
   if (weights_late && tid == 0) tc::mbar_wait(&S.bar_w, wphase ^ 1u, kWaitLimit);  // bounded: let the copy land
@@ -1029,11 +1133,12 @@ rt_status validate_train(float *params, float *m, float *v, float *grad, const f
 // `chained`: the scratch's BF16 tiles already hold the parameters and the loss slot
 // is zero (a run of steps), and the Adam kernel refreshes the tiles for the next
 // step.  n_nets networks (norms: device [n_nets], or N1 by value for one network)
-// each take n samples of inputs / targets at row net * in_stride.
+// each take n samples of inputs / targets at row net * in_stride.  `write_grad`:
+// the step stores its gradient into grad (always with RT_MLP_GRAD_ONLY).
 rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const float *inputs,
                          const float *targets, int64_t n, int64_t in_stride, int n_nets, const Norm &N1,
                          const Norm *norms, float lr, int32_t step, int32_t flags, float *loss, uint32_t *status,
-                         char *scr, bool chained, cudaStream_t st) {
+                         char *scr, bool chained, bool write_grad, cudaStream_t st) {
   const unsigned grid = (unsigned)((n + kH - 1) / kH);
   const size_t nn = (size_t)n_nets;
   uint16_t *tiles = reinterpret_cast<uint16_t *>(scr);
@@ -1047,19 +1152,26 @@ rt_status mlp_train_core(float *params, float *m, float *v, float *grad, const f
     if (s != RT_OK) return s;
   }
   const long long ts = 6LL * kTileElems;
-  k_mlp_fwd<true><<<dim3(grid, n_nets), kH, sizeof(FwdSmem), st>>>(
+  k_mlp_fwd<true><<<dim3(grid, n_nets), kFwdThreads, sizeof(FwdSmem), st>>>(
       params, tiles, ts, N1, norms, inputs, targets, n, in_stride, Z, dy, loss, 1.0f / (float)n_nets, nullptr,
       status);
   RT_CUDA_TRY(cudaGetLastError());
-  k_mlp_bwd<<<dim3(grid, n_nets), kH, sizeof(BwdSmem), st>>>(params, tiles, ts, N1, norms, inputs, n, in_stride,
-                                                             Z, dy, gpart, status);
+  k_mlp_bwd<<<dim3(grid, n_nets), kBwdThreads, sizeof(BwdSmem), st>>>(params, tiles, ts, N1, norms, inputs, n,
+                                                                      in_stride, Z, dy, gpart, status);
   RT_CUDA_TRY(cudaGetLastError());
   const bool adam = !(flags & RT_MLP_GRAD_ONLY);
   const float c1 = adam ? (float)(1.0 - std::pow(0.9, step)) : 1.0f;
   const float c2 = adam ? (float)(1.0 - std::pow(0.999, step)) : 1.0f;
-  k_grad_adam<<<dim3((kNParam + 255) / 256, n_nets), 256, 0, st>>>(gpart, (int)grid, grad, adam ? 1 : 0, params,
-                                                                    m, v, lr, 0.9f, 0.999f, 1e-8f, c1, c2,
-                                                                    chained ? tiles : nullptr);
+  float *g_out = write_grad ? grad : nullptr;
+  uint16_t *t_out = chained ? tiles : nullptr;
+  if (n_nets >= kAdamWide) {
+    constexpr int per_block = kAdamThreads * 4;
+    k_grad_adam<4><<<dim3((kNParam + per_block - 1) / per_block, n_nets), kAdamThreads, 0, st>>>(
+        gpart, (int)grid, g_out, adam ? 1 : 0, params, m, v, lr, 0.9f, 0.999f, 1e-8f, c1, c2, t_out);
+  } else {
+    k_grad_adam<1><<<dim3((kNParam + kAdamThreads - 1) / kAdamThreads, n_nets), kAdamThreads, 0, st>>>(
+        gpart, (int)grid, g_out, adam ? 1 : 0, params, m, v, lr, 0.9f, 0.999f, 1e-8f, c1, c2, t_out);
+  }
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -1075,7 +1187,7 @@ rt_status mlp_train_impl(float *params, float *m, float *v, float *grad, const f
   s = scr.alloc(train_scratch_bytes(n, 1), st);
   if (s != RT_OK) return s;
   return mlp_train_core(params, m, v, grad, inputs, targets, n, n, 1, to_norm(nm), nullptr, lr, step, flags,
-                        loss, status, scr.as<char>(), false, st);
+                        loss, status, scr.as<char>(), false, true, st);
 }
 
 // n_steps steps of n_nets networks (one network: nm is a host norm; an ensemble: nm
@@ -1120,7 +1232,7 @@ rt_status mlp_train_steps_impl(float *params, float *m, float *v, float *grad, c
     // every network's batch b: rows b * batch .. of its own n rows
     r = mlp_train_core(params, m, v, grad, inputs + 4 * b * batch, targets + b * batch, batch, n, n_nets, N1,
                        norms, (float)lr, (int32_t)(s + 1), 0, losses ? losses + i : loss1, status, scr.as<char>(),
-                       true, st);
+                       true, i == n_steps - 1, st);
     if (r != RT_OK) return r;
   }
   return RT_OK;
@@ -1148,21 +1260,26 @@ rt_status mlp_forward_impl(int n_nets, const float *params, const rt_mlp_norm *n
   const unsigned grid = (unsigned)((n + kH - 1) / kH);
   const Norm N1 = norm_on_device ? Norm{} : to_norm(nm);
   const Norm *norms = norm_on_device ? reinterpret_cast<const Norm *>(nm) : nullptr;
-  k_mlp_fwd<false><<<dim3(grid, n_nets), kH, sizeof(FwdSmem), st>>>(
+  k_mlp_fwd<false><<<dim3(grid, n_nets), kFwdThreads, sizeof(FwdSmem), st>>>(
       params, scr.as<uint16_t>(), 3LL * kTileElems, N1, norms, inputs, nullptr, n, n, nullptr, nullptr, nullptr,
       1.0f, out, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
 
-rt_status tc_selftest_impl(const float *A, const float *B, float *D, uint32_t *status, cudaStream_t st) {
+rt_status tc_selftest_impl(const float *A, const float *B, float *D, bool mn, uint32_t *status,
+                           cudaStream_t st) {
   if (!A || !B || !D) return fail(RT_E_INVAL, "rt_tc_selftest: NULL buffer");
-  const size_t bytes = 2 * (size_t)kTileBytes + 64;
+  const size_t bytes = (mn ? 4 : 2) * (size_t)kTileBytes + 64;
   static std::once_flag once;
   static rt_status attr = RT_OK;
-  std::call_once(once, [bytes] { attr = set_smem((const void *)k_tc_selftest, bytes); });
+  std::call_once(once, [] {
+    attr = set_smem((const void *)k_tc_selftest<false>, 2 * (size_t)kTileBytes + 64);
+    if (attr == RT_OK) attr = set_smem((const void *)k_tc_selftest<true>, 4 * (size_t)kTileBytes + 64);
+  });
   if (attr != RT_OK) return attr;
-  k_tc_selftest<<<1, kH, bytes, st>>>(A, B, D, status);
+  if (mn) k_tc_selftest<true><<<1, kH, bytes, st>>>(A, B, D, status);
+  else k_tc_selftest<false><<<1, kH, bytes, st>>>(A, B, D, status);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }
@@ -1363,7 +1480,11 @@ rt_status rt_mlp_forward_nets(int32_t n_nets, const float *params, const rt_mlp_
 }
 
 rt_status rt_tc_selftest(const float *A, const float *B, float *D, uint32_t *status, void *stream) {
-  return rt::tc_selftest_impl(A, B, D, status, (cudaStream_t)stream);
+  return rt::tc_selftest_impl(A, B, D, false, status, (cudaStream_t)stream);
+}
+
+rt_status rt_tc_selftest_mn(const float *A, const float *B, float *D, uint32_t *status, void *stream) {
+  return rt::tc_selftest_impl(A, B, D, true, status, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -137,5 +137,22 @@ __device__ __forceinline__ void mma_128x128x128(uint32_t d_tmem, const void *A, 
              idesc, s > 0 ? 1u : 0u);
 }
 
+// The same product with both operands read MN-major: A and B are tiles written
+// K-major as above with 128 rows = the contraction index (X[k][m] at row k, column
+// m), and D[m][n] = sum_k A[k][m] B[k][n].  Read MN-major (instruction-descriptor
+// transpose bits 15 and 16), a core matrix is 8 contraction rows of 16 bytes, 8
+// consecutive m (or n) each; core matrices adjacent in m are 128 bytes apart (SBO)
+// and groups of 8 contraction rows 2048 bytes apart (LBO), so K-slice s starts
+// 4096 * s bytes after the tile.  This reads a K-major tile as its transpose
+// without a second, transposed copy.
+__device__ __forceinline__ void mma_128x128x128_mn(uint32_t d_tmem, const void *A, const void *B) {
+  constexpr uint32_t idesc = idesc_bf16_f32(128, 128) | (1u << 15) | (1u << 16);
+  const uint32_t a0 = smem_addr(A), b0 = smem_addr(B);
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    mma_bf16(d_tmem, smem_desc(a0 + 4096u * s, 2048u, 128u), smem_desc(b0 + 4096u * s, 2048u, 128u),
+             idesc, s > 0 ? 1u : 0u);
+}
+
 }  // namespace tc
 }  // namespace rt

@@ -49,6 +49,23 @@ def test_tensor_core_selftest(rt):
     assert np.allclose(D.cpu().numpy(), ref, rtol=1e-5, atol=1e-4)
 
 
+def test_tensor_core_selftest_transposed_operands(rt):
+    # both tiles written one row per contraction index and read MN-major: D = A^T B
+    import torch
+    rng = np.random.default_rng(1)
+    A = rng.normal(0, 1, (128, 128)).astype(np.float32)
+    B = rng.normal(0, 1, (128, 128)).astype(np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    D = torch.zeros((128, 128), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert rt.lib().rt_tc_selftest_mn(ct.c_void_p(dA.data_ptr()), ct.c_void_p(dB.data_ptr()),
+                                      ct.c_void_p(D.data_ptr()), ct.c_void_p(st.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = _bf16(A).T @ _bf16(B)
+    assert np.allclose(D.cpu().numpy(), ref, rtol=1e-5, atol=1e-4)
+
+
 def _inputs(n, seed):
     rng = np.random.default_rng(seed)
     return (LO + (HI - LO) * rng.uniform(0, 1, (n, 4))).astype(np.float32)
@@ -154,3 +171,5 @@ def test_multi_step_training_equals_single_steps(rt):
     c.steps(x, t, batch, lr0, lr1, 1, total, total)
     torch.cuda.synchronize()
     assert torch.equal(a.params, c.params)
+    # grad holds the last step's gradient after a run of steps, as after single steps
+    assert torch.equal(a.grad, bt.grad) and torch.equal(a.grad, c.grad)
