@@ -134,11 +134,14 @@ __device__ __forceinline__ float layer1(const SmallParams &S, int c, const float
   return fmaf(w.w, u[3], fmaf(w.z, u[2], fmaf(w.y, u[1], fmaf(w.x, u[0], S.b1[c]))));
 }
 
+// Two weight buffers: W2 and W3 are copied at the start, W4 into the first buffer
+// once the product with W2 has completed.  About 101 KB in all, so that two blocks
+// share an SM.
 struct FwdSmem {
-  uint16_t W[3][kTileElems];  // W2..W4, rows = out
+  uint16_t W[2][kTileElems];  // layer l's weights (rows = out) in buffer l mod 2
   uint16_t A[kTileElems];     // current layer input, rows = samples
   SmallParams sp;
-  uint64_t bar_w, bar_mma;
+  uint64_t bar_w[2], bar_mma;
   uint32_t tmem;
   float red[4];
   float yh[kH];               // the head's partial sum over the second half of the units
@@ -152,7 +155,7 @@ constexpr int kFwdThreads = 2 * kH;
 // samples (n rows at net * in_stride) and activations at net times the per-network
 // strides.
 template <bool TRAIN>
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, 2)
 k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long long tile_stride, Norm N1,
           const Norm *__restrict__ norms, const float *__restrict__ inputs, const float *__restrict__ targets,
           long long n, long long in_stride, float *__restrict__ Z, float *__restrict__ dy,
@@ -179,7 +182,8 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   const bool valid = row < n;
 
   if (tid == 0) {
-    tc::mbar_init(&S.bar_w, 1);
+    tc::mbar_init(&S.bar_w[0], 1);
+    tc::mbar_init(&S.bar_w[1], 1);
     tc::mbar_init(&S.bar_mma, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -189,9 +193,13 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = S.tmem;
+  bool w4_issued = false;  // thread 0: the copy of W4 is in flight or done
   if (tid == 0) {
-    tc::mbar_arrive_expect_tx(&S.bar_w, 3 * kTileBytes);
-    tc::bulk_g2s(&S.W[0][0], tiles, 3 * kTileBytes, &S.bar_w);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_arrive_expect_tx(&S.bar_w[b], kTileBytes);
+      tc::bulk_g2s(&S.W[b][0], tiles + b * kTileElems, kTileBytes, &S.bar_w[b]);
+    }
   }
 
   // layer 1 on the CUDA cores
@@ -211,12 +219,13 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
                           pack_bf16x2(h[6], h[7]));
     *reinterpret_cast<uint4 *>(&S.A[tile_index(r, c0)]) = pk;
   }
-  int timeout = tc::mbar_wait(&S.bar_w, 0, kWaitLimit) ? 0 : 1;
+  int timeout = 0;
   int mma_pending = -1;  // parity of a product whose completion wait gave up
 
   float y = 0.0f;
 #pragma unroll 1
   for (int l = 0; l < 3; ++l) {
+    timeout = tc::mbar_wait(&S.bar_w[l & 1], (uint32_t)(l >> 1), kWaitLimit) ? 0 : 1;
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     if (__syncthreads_or(timeout)) {  // timeout block-uniform from here on
@@ -225,7 +234,7 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     }
     if (tid == 0) {
       tc::fence_after_sync();
-      tc::mma_128x128x128(tmem, S.A, S.W[l]);
+      tc::mma_128x128x128(tmem, S.A, S.W[l & 1]);
       tc::mma_commit(&S.bar_mma);
     }
     timeout = tc::mbar_wait(&S.bar_mma, (uint32_t)(l & 1), kWaitLimit) ? 0 : 1;
@@ -235,6 +244,11 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
       break;
     }
     tc::fence_after_sync();
+    if (l == 0 && tid == 0) {  // W4 into the buffer the finished product read
+      tc::mbar_arrive_expect_tx(&S.bar_w[0], kTileBytes);
+      tc::bulk_g2s(&S.W[0][0], tiles + 2 * kTileElems, kTileBytes, &S.bar_w[0]);
+      w4_issued = true;
+    }
     const float *bias = S.sp.b[l];
 #pragma unroll 1
     for (int c0 = cb; c0 < cb + kH / 2; c0 += 32) {
@@ -262,9 +276,11 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   if (timeout) {
     if (tid == 0) {
       status_or(status, RT_DEV_TIMEOUT);
-      // the weight copy or a product may still be in flight: let it land (bounded)
+      // a weight copy or a product may still be in flight: let it land (bounded)
       // before the block releases its shared and tensor memory
-      tc::mbar_wait(&S.bar_w, 0, kWaitLimit);
+      tc::mbar_wait(&S.bar_w[0], 0, kWaitLimit);
+      tc::mbar_wait(&S.bar_w[1], 0, kWaitLimit);
+      if (w4_issued) tc::mbar_wait(&S.bar_w[0], 1, kWaitLimit);
       if (mma_pending >= 0) tc::mbar_wait(&S.bar_mma, (uint32_t)mma_pending, kWaitLimit);
     }
   }
@@ -295,15 +311,15 @@ k_mlp_fwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
 
 // dZ and H are written one row per sample (16-byte stores of 8 units) and serve
 // both products: dZ K-major as the A operand of dH = dZ W, and dZ, H read MN-major
-// (as their transposes) for dW = dZ^T H.  They come first, so that a product that
-// reads past either tile stays inside the block's shared memory.
+// (as their transposes) for dW = dZ^T H.  Column sums over the tile's samples (bias
+// and first-layer gradients) are reduced by warp shuffles into per-row-quarter
+// partials; about 110 KB in all, so that two blocks share an SM.
 struct BwdSmem {
   uint16_t dZ[kTileElems];   // rows = samples, k = out
   uint16_t H[kTileElems];    // rows = samples, k = in
   uint16_t Wt[kTileElems];   // current layer's transposed weights, rows = in
-  float buf[kH][kH + 1];     // FP32 [sample][column] for column sums (padded: no bank conflicts)
-  float u[kH][4];
-  float dyv[kH];
+  float colred[5][4][kH];    // [bias, dW1 k = 0..3][row quarter][unit] partial sums
+  float dyred[4];            // per row quarter: sum of dy
   uint64_t bar_w, bar_mma;
   uint32_t tmem;
 };
@@ -313,27 +329,36 @@ __device__ __forceinline__ void put_bf16(uint16_t *tile, int r, int k, float v) 
 }
 
 // elements (r, k0 .. k0 + 7) of a K-major tile (k0 a multiple of 8): one 16-byte store
-__device__ __forceinline__ void put_bf16x8(uint16_t *tile, int r, int k0, const float (&v)[8]) {
+__device__ __forceinline__ void put_bf16x8(uint16_t *tile, int r, int k0, const float *v) {
   *reinterpret_cast<uint4 *>(&tile[tile_index(r, k0)]) =
       make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
                  pack_bf16x2(v[6], v[7]));
 }
 
-// column c of buf summed over the 128 samples (thread c), after a barrier
-__device__ __forceinline__ float column_sum(const BwdSmem &S, int c) {
-  float s = 0.0f;
-#pragma unroll 8
-  for (int r = 0; r < kH; ++r) s += S.buf[r][c];
-  return s;
+// v: this lane's values of 16 consecutive columns (its row).  Returns, in every
+// lane, the sum over the warp's 32 rows of column (lane & 15): four halving
+// exchange steps leave each lane one column summed over its 16-lane half, the last
+// step adds the two halves.  A fixed tree, so the sum is deterministic.  v is clobbered.
+__device__ __forceinline__ float warp_column_sum16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int o = 8, h = 8; o >= 1; o >>= 1, h >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = upper ? v[i] : v[i + h];
+      const float keep = upper ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 // Two threads per sample row: thread t takes row t mod 128 (its warp reads that
-// row's tensor-memory lane) and half t / 128 of the 128 units in every epilogue.
-// The column sums (bias gradients) and the first layer's gradient run on the first
-// 128 threads, one column each.
+// row's tensor-memory lane) and half t / 128 of the 128 units, in chunks of 16.
 constexpr int kBwdThreads = 2 * kH;
+constexpr int kBwdChunk = 16;
 
-__global__ void __launch_bounds__(kBwdThreads)
+__global__ void __launch_bounds__(kBwdThreads, 2)
 k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long long tile_stride, Norm N1,
           const Norm *__restrict__ norms, const float *__restrict__ inputs, long long n, long long in_stride,
           const float *__restrict__ Z, const float *__restrict__ dy, float *__restrict__ Gpart,
@@ -350,10 +375,11 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
   // this tile's gradient partial (every parameter written exactly once; summed over
   // the tiles in a fixed order by k_grad_adam)
   float *G = Gpart + (net * gridDim.x + blockIdx.x) * kGradStride;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int r = tid & (kH - 1);          // sample row within the tile
+  const int q4 = warp & 3;               // row quarter = the warp's tensor-memory lanes
   const int cb = (tid >> 7) * (kH / 2);  // first unit of the thread's half
-  const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;  // the warp's tensor-memory lanes
+  const uint32_t lanes = (uint32_t)(q4 * 32) << 16;
   const long long row = (long long)blockIdx.x * kH + r;
   const bool valid = row < n;
 
@@ -371,58 +397,52 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     tc::mbar_arrive_expect_tx(&S.bar_w, kTileBytes);
     tc::bulk_g2s(S.Wt, tiles + 5 * kTileElems, kTileBytes, &S.bar_w);
   }
+  float u[4];
+  normalise(inputs, row, valid, N, u);
   const float dyv = valid ? dy[row] : 0.0f;
-  if (tid < kH) {
-    float u[4];
-    normalise(inputs, row, valid, N, u);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) S.u[r][k] = u[k];
-    S.dyv[r] = dyv;
+  if (tid < kH) {  // db5 = sum_s dy, per row quarter
+    float d = dyv;
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    if (lane == 0) S.dyred[q4] = d;
   }
 
-  // head: dw5 = sum_s dy h4, db5 = sum_s dy (loads issued 32 at a time)
+  // head: dw5 = sum_s dy h4
 #pragma unroll 1
-  for (int c0 = cb; c0 < cb + kH / 2; c0 += 32) {
-    float z4[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) z4[i] = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) S.buf[r][c0 + i] = dyv * z4[i] * sigmoid_fast(z4[i]);
-  }
-  __syncthreads();
-  if (tid < kH) G[oW5 + tid] = column_sum(S, tid);
-  if (tid == 0) {
-    float d5 = 0.0f;
-    for (int q = 0; q < kH; ++q) d5 += S.dyv[q];
-    G[oB5] = d5;
-  }
-  __syncthreads();
-  // dz4 = dy w5 silu'(z4) -> dZ, buf (for db4); h3 -> H (for dW4)
-#pragma unroll 1
-  for (int c0 = cb; c0 < cb + kH / 2; c0 += 16) {
-    float z4[16], z3[16];
+  for (int c0 = cb; c0 < cb + kH / 2; c0 += kBwdChunk) {
+    float v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      z4[i] = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
-      z3[i] = valid ? Z[zidx(2, c0 + i, n, row)] : 0.0f;
+      const float z4 = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
+      v[i] = dyv * z4 * sigmoid_fast(z4);
     }
-#pragma unroll
-    for (int i = 0; i < 16; i += 8) {
-      float dz[8], h[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int c = c0 + i + q;
-        const float s4 = sigmoid_fast(z4[i + q]);
-        dz[q] = dyv * __ldg(P + oW5 + c) * (s4 * (1.0f + z4[i + q] * (1.0f - s4)));
-        S.buf[r][c] = dz[q];
-        h[q] = z3[i + q] * sigmoid_fast(z3[i + q]);
-      }
-      put_bf16x8(S.dZ, r, c0 + i, dz);
-      put_bf16x8(S.H, r, c0 + i, h);
-    }
+    const float cs = warp_column_sum16(v, lane);
+    if (lane < 16) S.colred[0][q4][c0 + lane] = cs;
   }
   __syncthreads();
-  if (tid < kH) G[oB4 + tid] = column_sum(S, tid);
+  if (tid < kH) G[oW5 + tid] = S.colred[0][0][tid] + S.colred[0][1][tid] + S.colred[0][2][tid] + S.colred[0][3][tid];
+  if (tid == 0) G[oB5] = S.dyred[0] + S.dyred[1] + S.dyred[2] + S.dyred[3];
+  __syncthreads();
+  // dz4 = dy w5 silu'(z4) -> dZ and db4; h3 -> H (for dW4)
+#pragma unroll 1
+  for (int c0 = cb; c0 < cb + kH / 2; c0 += kBwdChunk) {
+    float dz[16], h[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float z4 = valid ? Z[zidx(3, c0 + i, n, row)] : 0.0f;
+      const float z3 = valid ? Z[zidx(2, c0 + i, n, row)] : 0.0f;
+      const float s4 = sigmoid_fast(z4);
+      dz[i] = dyv * __ldg(P + oW5 + c0 + i) * (s4 * (1.0f + z4 * (1.0f - s4)));
+      h[i] = z3 * sigmoid_fast(z3);
+    }
+    put_bf16x8(S.dZ, r, c0, dz);
+    put_bf16x8(S.dZ, r, c0 + 8, dz + 8);
+    put_bf16x8(S.H, r, c0, h);
+    put_bf16x8(S.H, r, c0 + 8, h + 8);
+    const float cs = warp_column_sum16(dz, lane);
+    if (lane < 16) S.colred[0][q4][c0 + lane] = cs;
+  }
+  __syncthreads();
+  if (tid < kH) G[oB4 + tid] = S.colred[0][0][tid] + S.colred[0][1][tid] + S.colred[0][2][tid] + S.colred[0][3][tid];
 
   int timeout = 0;
   bool aborted = false;
@@ -460,64 +480,72 @@ k_mlp_bwd(const float *__restrict__ P, const uint16_t *__restrict__ tiles, long 
     float *gW = G + (l == 4 ? oW4 : (l == 3 ? oW3 : oW2));
     const long long zl = (long long)(l - 2);  // block of z_{l-1}
 #pragma unroll 1
-    for (int c0 = cb; c0 < cb + kH / 2; c0 += 32) {
+    for (int c0 = cb; c0 < cb + kH / 2; c0 += kBwdChunk) {
       // this chunk's pre-activations first, so that their loads overlap the
       // tensor-memory reads below
-      float z[32], zp[32];
+      float z[16], zp[16];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < 16; ++i) {
         z[i] = valid ? Z[zidx(zl, c0 + i, n, row)] : 0.0f;
         zp[i] = (valid && l > 2) ? Z[zidx(zl - 1, c0 + i, n, row)] : 0.0f;
       }
-      float acc[32];
-      tc::tmem_ld32(tmem + lanes + (uint32_t)c0, acc);
+      float acc[16];
+      tc::tmem_ld16(tmem + lanes + (uint32_t)c0, acc);
 #pragma unroll
-      for (int i = 0; i < 32; i += 4)
+      for (int i = 0; i < 16; i += 4)
         *reinterpret_cast<float4 *>(gW + r * kH + c0 + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
-      tc::tmem_ld32(tmem + lanes + (uint32_t)(kH + c0), acc);
-      uint32_t pd[4], ph[4];  // BF16 pairs of dz and h, stored 8 units at a time
+      tc::tmem_ld16(tmem + lanes + (uint32_t)(kH + c0), acc);
+      float dz[16];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int c = c0 + i;
+      for (int i = 0; i < 16; ++i) {
         const float s = sigmoid_fast(z[i]);
-        const float dz = acc[i] * (s * (1.0f + z[i] * (1.0f - s)));
-        S.buf[r][c] = dz;
-        if (l > 2) {
-          const uint32_t bd = __bfloat16_as_ushort(__float2bfloat16_rn(dz));
-          const uint32_t bh = __bfloat16_as_ushort(__float2bfloat16_rn(zp[i] * sigmoid_fast(zp[i])));
-          const int w = (i >> 1) & 3;
-          pd[w] = (i & 1) ? (pd[w] | (bd << 16)) : bd;
-          ph[w] = (i & 1) ? (ph[w] | (bh << 16)) : bh;
-          if ((i & 7) == 7) {
-            *reinterpret_cast<uint4 *>(&S.dZ[tile_index(r, c - 7)]) = make_uint4(pd[0], pd[1], pd[2], pd[3]);
-            *reinterpret_cast<uint4 *>(&S.H[tile_index(r, c - 7)]) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-          }
+        dz[i] = acc[i] * (s * (1.0f + z[i] * (1.0f - s)));
+      }
+      if (l > 2) {
+        float h[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = zp[i] * sigmoid_fast(zp[i]);
+        put_bf16x8(S.dZ, r, c0, dz);
+        put_bf16x8(S.dZ, r, c0 + 8, dz + 8);
+        put_bf16x8(S.H, r, c0, h);
+        put_bf16x8(S.H, r, c0 + 8, h + 8);
+      }
+      float v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = dz[i];
+      float cs = warp_column_sum16(v, lane);
+      if (lane < 16) S.colred[0][q4][c0 + lane] = cs;
+      if (l == 2) {  // first layer: dW1[c][k] = sum_s dz1[s][c] u[s][k]
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = dz[i] * u[k];
+          cs = warp_column_sum16(v, lane);
+          if (lane < 16) S.colred[1 + k][q4][c0 + lane] = cs;
         }
       }
     }
     tc::fence_before_sync();
     __syncthreads();
     const int ob = (l == 4 ? oB3 : (l == 3 ? oB2 : oB1));
-    if (tid < kH) G[ob + tid] = column_sum(S, tid);
-    if (l == 2 && tid < kH) {  // first layer: dW1[c][k] = sum_s dz1[s][c] u[s][k]
-      float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 4
-      for (int q = 0; q < kH; ++q) {
-        const float d = S.buf[q][tid];
+    if (tid < kH) G[ob + tid] = S.colred[0][0][tid] + S.colred[0][1][tid] + S.colred[0][2][tid] + S.colred[0][3][tid];
+    if (l == 2 && tid < kH) {
+      float g[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[k] = fmaf(d, S.u[q][k], g[k]);
-      }
+      for (int k = 0; k < 4; ++k)
+        g[k] = S.colred[1 + k][0][tid] + S.colred[1 + k][1][tid] + S.colred[1 + k][2][tid] + S.colred[1 + k][3][tid];
       *reinterpret_cast<float4 *>(G + oW1 + tid * 4) = make_float4(g[0], g[1], g[2], g[3]);
     }
-    __syncthreads();  // buf is rewritten by the next layer
   }
   if (aborted && tid == 0) {  // some thread's wait gave up; let what is still in flight land (bounded)
     status_or(status, RT_DEV_TIMEOUT);
     if (w_pending >= 0) tc::mbar_wait(&S.bar_w, (uint32_t)w_pending, kWaitLimit);
     if (mma_pending >= 0) tc::mbar_wait(&S.bar_mma, (uint32_t)mma_pending, kWaitLimit);
   }
-  if (aborted)  // block-uniform: the partial holds no gradient of this tile
+  if (aborted) {  // block-uniform: the partial holds no gradient of this tile
+    __syncthreads();  // the other threads' partial writes are done before the zeros
     for (int i = tid; i < kNParam; i += kBwdThreads) G[i] = 0.0f;
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -1125,6 +1153,12 @@ rt_status validate_train(float *params, float *m, float *v, float *grad, const f
   std::call_once(once, [] {
     attr = set_smem((const void *)k_mlp_fwd<true>, sizeof(FwdSmem));
     if (attr == RT_OK) attr = set_smem((const void *)k_mlp_bwd, sizeof(BwdSmem));
+    if (attr == RT_OK) {  // two backward blocks per SM: the largest shared-memory split
+      const cudaError_t e = cudaFuncSetAttribute((const void *)k_mlp_bwd,
+                                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) attr = fail(RT_E_CUDA, "k_mlp_bwd carveout: %s", cudaGetErrorString(e));
+    }
   });
   return attr;
 }
