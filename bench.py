@@ -179,10 +179,10 @@ PROFILE_SUMMARIES = {4: ("k_kappa_box128_voigt100k.md", "k_walk_box128_voigt100k
                      1: ("k_kappa_box32_voigt20k.md", "k_walk_box32_voigt20k.md")}
 # what bounds the walk instead of HBM, from those profiles (tables and cells L2-resident)
 WALK_LIMITERS = {
-    4: {"dram_bytes_per_step": 0.095, "l2_hit_pct": 98.9, "alu_pipe_pct": 63.2, "issue_pct": 69.1,
-        "l1_data_pipe_pct": 70.5, "note": "rays grouped by wavenumber; ALU, issue and L1 bind together"},
-    1: {"dram_bytes_per_step": 0.23, "l2_hit_pct": 96.7, "alu_pipe_pct": 57.2, "issue_pct": 67.3,
-        "l1_data_pipe_pct": 66.2, "note": "ungrouped; gathers L2-resident, ALU and L1 bind together"},
+    4: {"dram_bytes_per_step": 1.0, "l2_hit_pct": 44.8, "alu_pipe_pct": 74.3, "issue_pct": 69.5,
+        "l1_data_pipe_pct": 15.9, "note": "ungrouped; dark rays take only the DDA step; ALU and issue bind"},
+    1: {"dram_bytes_per_step": 0.21, "l2_hit_pct": 82.9, "alu_pipe_pct": 64.5, "issue_pct": 71.9,
+        "l1_data_pipe_pct": 22.6, "note": "ungrouped; dark rays take only the DDA step; ALU and issue bind"},
 }
 
 
@@ -394,8 +394,8 @@ def hot_path_line(index, args, world, rank, local, e2e=True, tau_cut=True):
                                                                   "rt_common.cuh"]),
                             "bytes_per_step": bps, "peak_source": "measured HBM copy (MEASURED_PEAKS.json)",
                             "limiters": {**WALK_LIMITERS[index], "source": "profiles/" + prof_w},
-                            "note": "tables L2-resident: the walk is bound by the ALU pipe, issue and the L1 "
-                                    "data pipe, not by HBM (limiters, from the ncu summary)"}
+                            "note": "the walk is bound by the ALU pipe and issue (the DDA's compares and "
+                                    "selects), not by HBM (limiters, from the ncu summary)"}
     return out
 
 

@@ -284,24 +284,29 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
   if (inside) pf(cnext);
 
   const float ds = __fsub_rn(tn, R.t);
-  // the segment's optical depth; an unbounded segment (a ray that never reaches a
-  // wall, ds = inf) is held at 1e30, which leaves a transmission of exactly 0 and
-  // a deposit of w trans0, as an infinite depth would, without infinities in the sum
-  const float a = kap > 0.0f ? fminf(__fmul_rn(__fmul_rn(kap, 100.0f), ds), 1e30f) : 0.0f;
   const float trans0 = R.trans;
-  // compensated optical depth
-  {
-    const float y = __fsub_rn(a, R.tc);
-    const float sum = __fadd_rn(R.tau, y);
-    R.tc = __fsub_rn(__fsub_rn(sum, R.tau), y);
-    R.tau = sum;
-  }
-  // deposit and transmission exp(-tau); once the transmission has underflowed to
-  // zero it stays zero (tau only grows), so a dark ray skips both exponentials
-  if (trans0 != 0.0f) {
-    const float dep = R.w * trans0 * one_minus_exp_neg(a);
-    if (writes && dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
-    R.trans = __expf(__fsub_rn(R.tc, R.tau));
+  // Once the transmission has underflowed to zero it stays zero (tau only grows): a
+  // dark ray deposits nothing and its optical depth matters only to the optical-depth
+  // cut, so without the cut it skips the depth sum and both exponentials (its visits,
+  // deposits and escaped weight are those of the full update).
+  if (trans0 != 0.0f || W.tau_cut) {
+    // the segment's optical depth; an unbounded segment (a ray that never reaches a
+    // wall, ds = inf) is held at 1e30, which leaves a transmission of exactly 0 and
+    // a deposit of w trans0, as an infinite depth would, without infinities in the sum
+    const float a = kap > 0.0f ? fminf(__fmul_rn(__fmul_rn(kap, 100.0f), ds), 1e30f) : 0.0f;
+    // compensated optical depth
+    {
+      const float y = __fsub_rn(a, R.tc);
+      const float sum = __fadd_rn(R.tau, y);
+      R.tc = __fsub_rn(__fsub_rn(sum, R.tau), y);
+      R.tau = sum;
+    }
+    // deposit and transmission exp(-tau)
+    if (trans0 != 0.0f) {
+      const float dep = R.w * trans0 * one_minus_exp_neg(a);
+      if (writes && dep != 0.0f) atomicAdd(absorbed + R.cell, (double)dep);
+      R.trans = __expf(__fsub_rn(R.tc, R.tau));
+    }
   }
   if (REC && writes && R.row >= 0 && R.nv < W.rec_max) {
     rec.cells[(long long)R.row * W.rec_max + R.nv] = R.cell;
