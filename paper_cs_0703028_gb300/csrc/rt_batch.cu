@@ -110,10 +110,13 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
 #pragma unroll
       for (int u = 0; u < kBatchUnroll; ++u) {  // steps per pass of the loop
         if (!done) {
-          const float kap = TAB == 2 ? cell_kappa_row(cd, krow) : (TAB == 1 ? cell_kappa_row1(cd, krow1, W.nT) : cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j));
+          // a dark ray (transmission zero, no optical-depth cut) needs neither its cell's
+          // kappa nor the next cell's data
+          const bool lit = R.trans != 0.0f || W.tau_cut;
+          const float kap = !lit ? 0.0f : (TAB == 2 ? cell_kappa_row(cd, krow) : (TAB == 1 ? cell_kappa_row1(cd, krow1, W.nT) : cell_kappa_l<TAB>(cd, tab, W.nT, W.n_nu, R.j)));
           float4 cdn = cd;
           done = ray_step<false, false, true>(W, kap, D.absorbed, D.status, rec, R, true,
-                                              [&](int c) { cdn = __ldg(cells + c); }, s_axes[warp]);
+                                              [&](int c) { if (lit) cdn = __ldg(cells + c); }, s_axes[warp]);
           cd = cdn;
         }
       }
