@@ -179,10 +179,10 @@ PROFILE_SUMMARIES = {4: ("k_kappa_box128_voigt100k.md", "k_walk_box128_voigt100k
                      1: ("k_kappa_box32_voigt20k.md", "k_walk_box32_voigt20k.md")}
 # what bounds the walk instead of HBM, from those profiles (tables and cells L2-resident)
 WALK_LIMITERS = {
-    4: {"dram_bytes_per_step": 1.0, "l2_hit_pct": 44.8, "alu_pipe_pct": 74.3, "issue_pct": 69.5,
-        "l1_data_pipe_pct": 15.9, "note": "ungrouped; dark rays take only the DDA step; ALU and issue bind"},
-    1: {"dram_bytes_per_step": 0.21, "l2_hit_pct": 82.9, "alu_pipe_pct": 64.5, "issue_pct": 71.9,
-        "l1_data_pipe_pct": 22.6, "note": "ungrouped; dark rays take only the DDA step; ALU and issue bind"},
+    4: {"dram_bytes_per_step": 1.0, "l2_hit_pct": 44.9, "alu_pipe_pct": 72.4, "issue_pct": 69.7,
+        "l1_data_pipe_pct": 19.6, "note": "ungrouped; dark rays take only the DDA step; ALU and issue bind"},
+    1: {"dram_bytes_per_step": 0.21, "l2_hit_pct": 83.1, "alu_pipe_pct": 60.5, "issue_pct": 68.5,
+        "l1_data_pipe_pct": 21.0, "note": "ungrouped; dark rays take only the DDA step; ALU and issue bind"},
 }
 
 

@@ -104,9 +104,18 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
         }
         next += __popc(idle);
       }
-      if (!__any_sync(0xffffffffu, active)) break;
+      const unsigned am = __ballot_sync(0xffffffffu, active);
+      if (!am) break;
       if (!active) continue;
       bool done = false;
+      if (__all_sync(am, R.trans == 0.0f && !W.tau_cut)) {
+        // every active lane dark: DDA-only steps
+#pragma unroll
+        for (int u = 0; u < kBatchUnroll; ++u)
+          if (!done)
+            done = ray_step<false, false, true, true>(W, 0.0f, D.absorbed, D.status, rec, R, true, NoPrefetch(),
+                                                      s_axes[warp]);
+      } else {
 #pragma unroll
       for (int u = 0; u < kBatchUnroll; ++u) {  // steps per pass of the loop
         if (!done) {
@@ -119,6 +128,7 @@ k_walk_batch(const EnclDev *__restrict__ E, const long long *__restrict__ item_o
                                               [&](int c) { if (lit) cdn = __ldg(cells + c); }, s_axes[warp]);
           cd = cdn;
         }
+      }
       }
       if (done) {
         em += (double)R.w;

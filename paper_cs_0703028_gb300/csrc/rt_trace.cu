@@ -197,11 +197,18 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, const ui
       }
       next += __popc(idle);
     }
-    if (!__any_sync(0xffffffffu, active)) break;
+    const unsigned am = __ballot_sync(0xffffffffu, active);
+    if (!am) break;
     if (!active) continue;
+    bool done = false;
+    if (__all_sync(am, R.trans == 0.0f && !W.tau_cut)) {
+      // every active lane dark: kWalkUnroll DDA-only steps
+#pragma unroll
+      for (int u = 0; u < kWalkUnroll; ++u)
+        if (!done) done = ray_step<REC, true, true, true>(W, 0.0f, absorbed, status, rec, R, true, NoPrefetch(), s_axes);
+    } else {
     // kWalkUnroll steps per pass of the loop; each step loads the table value of
     // its cell and the next cell's data, both in flight while its arithmetic runs
-    bool done = false;
 #pragma unroll
     for (int u = 0; u < kWalkUnroll; ++u) {
       if (!done) {
@@ -214,6 +221,7 @@ k_walk(const float4 *__restrict__ cells, const float *__restrict__ tab, const ui
                                          [&](int c) { if (lit) cdn = __ldg(cells + c); }, s_axes);
         cd = cdn;
       }
+    }
     }
     if (done) {
       const float out = R.w * R.trans;

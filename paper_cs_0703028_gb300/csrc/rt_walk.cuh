@@ -256,7 +256,10 @@ struct NoPrefetch {
 // AXES: the chosen axis's {n, cell stride, h bits} come from one 16-byte load of
 // axes[axis] (a per-block shared-memory copy of the grid) instead of selects
 // among constant-bank values.
-template <bool REC = true, bool EARLY_EXIT = true, bool AXES = false, typename Prefetch = NoPrefetch>
+// DARK: the caller knows the ray is dark and no optical-depth cut is requested, so
+// the step is the DDA alone (same visits as the full step; kap is not read).
+template <bool REC = true, bool EARLY_EXIT = true, bool AXES = false, bool DARK = false,
+          typename Prefetch = NoPrefetch>
 __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double *__restrict__ absorbed,
                                          uint32_t *status, const RecordPtrs &rec, Ray &R,
                                          bool writes = true, Prefetch pf = Prefetch(),
@@ -289,7 +292,7 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
   // dark ray deposits nothing and its optical depth matters only to the optical-depth
   // cut, so without the cut it skips the depth sum and both exponentials (its visits,
   // deposits and escaped weight are those of the full update).
-  if (trans0 != 0.0f || W.tau_cut) {
+  if (!DARK && (trans0 != 0.0f || W.tau_cut)) {
     // the segment's optical depth; an unbounded segment (a ray that never reaches a
     // wall, ds = inf) is held at 1e30, which leaves a transmission of exactly 0 and
     // a deposit of w trans0, as an infinite depth would, without infinities in the sum
@@ -313,7 +316,7 @@ __device__ __forceinline__ bool ray_step(const WalkParams &W, float kap, double 
     rec.ds[(long long)R.row * W.rec_max + R.nv] = ds;
   }
   ++R.nv;
-  const bool cut = W.tau_cut && R.tau > 100.0f;
+  const bool cut = !DARK && W.tau_cut && R.tau > 100.0f;
   const bool capped = R.nv >= W.step_cap;
   if (EARLY_EXIT) {
     if (tn == INFINITY || cut) return true;
