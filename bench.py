@@ -649,16 +649,20 @@ def run_surrogate(args):
     n_lbl = max(1, n // 50)
     walks, tallies = {}, {}
 
-    def timed_walk(name, fn, n_rays):
-        t = rt.Tally(g.ncells)
+    def timed_walk(name, fn, n_rays, counters=1):
+        # counters = 2: a surrogate walk called with RT_COUNT_EVALS, steps[1] = its network
+        # evaluations (128 queries each)
+        t = rt.Tally(g.ncells, counters=counters)
         t.zero()
         fn(t)
         t.zero()
         ms = _ev_time(lambda: fn(t))
         ab, sc, _ = t.read()
-        steps = int(t.steps.item())
+        steps = int(t.steps[0].item())
         walks[name] = {"ray_cell_steps_per_s": steps / (ms * 1e-3), "ms": ms, "steps": steps,
                        "rays": n_rays, "energy_residual": float(sc[3])}
+        if counters > 1:
+            walks[name]["network_evals"] = int(t.steps[1].item())
         return ab
 
     with ClockWindow(0) as clk:
@@ -678,7 +682,8 @@ def run_surrogate(args):
         train_s = time.time() - t0
         name = f"mlp_e{ep}"
         with ClockWindow(0) as clk_m:
-            ab = timed_walk(name, lambda t: rt.trace_mlp(gs, params, norm, spec, t, n_rays=n, n_rays_total=n), n)
+            ab = timed_walk(name, lambda t: rt.trace_mlp(gs, params, norm, spec, t, n_rays=n, n_rays_total=n,
+                                                         flags=rt.RT_COUNT_EVALS), n, counters=2)
         walks[name]["clocks"] = clk_m.result
         err = np.abs(ab[big] - ref[big]) / ref[big]
         row = {"epochs": ep, "steps": len(hist) and hist[-1][0] + 1, "train_s": train_s,
@@ -711,7 +716,8 @@ def run_surrogate(args):
             name = f"bands{args.bands}_s{st_n}"
             with ClockWindow(0) as clk_b:
                 ab = timed_walk(name, lambda t: rt.trace_mlp_bands(gs, args.bands, P_e, norms_e, spec, t, n_rays=n,
-                                                                   n_rays_total=n), n)
+                                                                   n_rays_total=n, flags=rt.RT_COUNT_EVALS),
+                                n, counters=2)
             walks[name]["clocks"] = clk_b.result
             err = np.abs(ab[big] - ref[big]) / ref[big]
             # the worst cells: their temperature, share of the largest tally, error
@@ -765,7 +771,9 @@ def run_surrogate(args):
     del xs, ys, tr, tl
     peak = _peaks().get("bf16_tflops", 1978.3)
     eval_flops = 3 * 2 * 128 * 128
-    walk_tf = walks[best_name]["ray_cell_steps_per_s"] * eval_flops / 1e12
+    # the network evaluations the walk ran (128 queries each; a dark ray's steps need none)
+    wb = walks[best_name]
+    walk_tf = wb["network_evals"] * 128 * eval_flops / (wb["ms"] * 1e-3) / 1e12
     last = curve[-1]
     train_tf = args.samples * last["epochs"] * 3 * eval_flops / last["train_s"] / 1e12
     res = {"metric": "ray-cell steps/s, surrogate walk vs on-the-fly line-by-line walk",

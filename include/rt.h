@@ -66,6 +66,9 @@ enum { RT_MEM_HOST = 0, RT_MEM_DEVICE = 1 };
 #define RT_SRC_EMIT   0        /* thermal emission sampled over cells and wavenumbers */
 #define RT_SRC_BEAM   1        /* collimated unit beams: ray r enters face x=0 at nu_(r mod n_nu) */
 #define RT_TAU_CUT    (1 << 4) /* stop a ray once its optical depth exceeds 100 (lost < 4e-44) */
+#define RT_COUNT_EVALS (1 << 5) /* rt_trace_mlp, rt_trace_mlp_bands only: tally->steps holds two
+                                   counters and steps[1] also accumulates the number of network
+                                   evaluations (one per 128-ray tile and walk step) */
 
 /*
  * Spectral line list (Section 3, Eq. S: S(T_ref), nu, E_eta; Eq. tau: lines of one
@@ -145,7 +148,8 @@ typedef struct {
  *                     [2] power absorbed by the cold black walls, [3] relative
  *                     energy residual |emitted - absorbed - walls| / emitted
  *                     (set by rt_tally)
- *   steps[1]          number of ray-cell steps processed
+ *   steps[1]          number of ray-cell steps processed (steps[2] with RT_COUNT_EVALS:
+ *                     [1] the surrogate walk's network evaluations)
  *   status[1]         sticky RT_DEV_* bits
  */
 typedef struct {
@@ -415,7 +419,10 @@ rt_status rt_mlp_train_steps(float *params, float *adam_m, float *adam_v, float 
  * are those of rt_trace; the emission weight uses the network's kappa of the
  * emitting cell.  Rays are processed in 128-ray tiles, several tiles per block
  * sharing the resident weights; each tile's live rays' queries are evaluated
- * together on the tensor cores at every step.
+ * together on the tensor cores at every step.  A ray whose transmission has
+ * underflowed to zero (and no RT_TAU_CUT) needs no further kappa: it takes its
+ * remaining steps at once, without network evaluations, and its lane takes a new
+ * ray (the visits, deposits and escaped weight are unchanged).
  */
 rt_status rt_trace_mlp(const rt_grid *grid, const float *params, const rt_mlp_norm *norm,
                        const rt_spectral *spec, uint64_t ray_begin, uint64_t n_rays,

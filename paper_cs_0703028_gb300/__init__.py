@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_E_INVAL", 2: "RT_E_NOMEM", 3: "RT_E_CUDA", 4:
                 5: "RT_E_TIMEOUT", 6: "RT_E_UNSORTED", 7: "RT_E_NONFINITE"}
 PROFILE = {"lorentz": 0, "voigt": 1}
 RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
-RT_SRC_EMIT, RT_SRC_BEAM, RT_TAU_CUT = 0, 1, 1 << 4
+RT_SRC_EMIT, RT_SRC_BEAM, RT_TAU_CUT, RT_COUNT_EVALS = 0, 1, 1 << 4, 1 << 5
 
 
 class RtError(RuntimeError):
@@ -221,19 +221,23 @@ class Tally:
     that traced disjoint ray ranges combine their tallies with one all-reduce
     (``shard.combine_tally``)."""
 
-    def __init__(self, ncells: int, device="cuda"):
+    def __init__(self, ncells: int, device="cuda", counters: int = 1):
         import torch
         self.ncells = int(ncells)
         self.flat = torch.zeros(self.ncells + 4, dtype=torch.float64, device=device)
         self.absorbed = self.flat[:self.ncells]
         self.scalars = self.flat[self.ncells:]
-        self.steps = torch.zeros(1, dtype=torch.int64, device=device)
+        # [ray-cell steps] or, counters = 2 for a surrogate walk with RT_COUNT_EVALS,
+        # [ray-cell steps, network evaluations]
+        self.steps = torch.zeros(int(counters), dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.buf = rt_tally_buf(self.absorbed.data_ptr(), self.scalars.data_ptr(),
                                 self.steps.data_ptr(), self.status.data_ptr())
 
     def zero(self, stream=None):
         _check(lib().rt_tally_zero(ct.byref(self.buf), self.ncells, _stream_ptr(stream)), "rt_tally_zero")
+        if self.steps.numel() > 1:  # the evaluation counter (rt_tally_zero clears steps[0])
+            self.steps[1:].zero_()
 
     def read(self, stream=None, absorbed=True, check=True):
         """rt_tally: returns (absorbed float64 numpy or None, scalars[4], status)."""

@@ -872,7 +872,8 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
            const Norm *__restrict__ norms, BandPlan B, const float *__restrict__ T,
            const float *__restrict__ Pf, const float *__restrict__ Xf, float p_ref, float x_ref, WalkParams W,
            double *__restrict__ absorbed, double *__restrict__ scalars,
-           unsigned long long *__restrict__ steps_out, uint32_t *status, RecordPtrs rec) {
+           unsigned long long *__restrict__ steps_out, unsigned long long *__restrict__ evals_out,
+           uint32_t *status, RecordPtrs rec) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   WalkMlpSmem &S = *reinterpret_cast<WalkMlpSmem *>(smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -894,6 +895,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
   int cur_band = -1, timeout = 0;
   bool weights_late = false;
   const int tile = tid >> 7;
+  unsigned long long n_evals = 0;  // this tile's network evaluations (counted by its thread 0)
   Norm N = N1;
 #pragma unroll 1
   for (;;) {  // work items: one band's network, at most B.chunk of its rays
@@ -963,10 +965,17 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
         timeout = 1;
         break;
       }
+      n_evals += (tid & 127) == 0 ? 1 : 0;
       if (active) {
         const float kap = __expf(logk);
         if (R.w < 0.0f) R.w = emission_weight(W, R.j, Tc, kap);
-        if (ray_step(W, kap, absorbed, status, rec, R)) {
+        bool fin = ray_step(W, kap, absorbed, status, rec, R);
+        // a dark ray (transmission zero, no optical-depth cut) needs no more kappa: it
+        // takes its remaining steps at once, DDA only, and frees its lane for a new ray
+        if (!fin && R.trans == 0.0f && !W.tau_cut)
+          while (!(fin = ray_step<true, true, false, true>(W, 0.0f, absorbed, status, rec, R))) {
+          }
+        if (fin) {
           const float out = R.w * R.trans;
           em += (double)R.w;
           esc += (double)out;
@@ -998,6 +1007,7 @@ k_walk_mlp(const float *__restrict__ P, const uint16_t *__restrict__ tiles, Norm
     if (esc != 0.0) atomicAdd(scalars + 2, esc);
     if (nsteps) atomicAdd(steps_out, nsteps);
   }
+  if (evals_out && n_evals) atomicAdd(evals_out, n_evals);  // nonzero only in a tile's thread 0
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -1327,6 +1337,8 @@ rt_status trace_mlp_core(const rt_grid *grid, int band_pts, const float *params,
                          const rt_tally_buf *tally, const rt_record *record, cudaStream_t st) {
   WalkParams W;
   RecordPtrs rp;
+  const bool count_evals = (flags & RT_COUNT_EVALS) != 0;
+  flags &= ~RT_COUNT_EVALS;
   rt_status v = walk_setup(grid, spec, ray_begin, n_rays, n_total, seed, enclosure, flags, tally, record, &W, &rp);
   if (v != RT_OK) return v;
   if ((flags & 0xF) != RT_SRC_EMIT) return fail(RT_E_INVAL, "rt_trace_mlp: only RT_SRC_EMIT");
@@ -1371,7 +1383,7 @@ rt_status trace_mlp_core(const rt_grid *grid, int band_pts, const float *params,
   BandPlan B{order, band_start, item_start, item_next, chunk, n_bands};
   k_walk_mlp<<<blocks, kWalkMlpThreads, sizeof(WalkMlpSmem), st>>>(
       params, tiles, N1, norms, B, grid->T, grid->p_atm, grid->x, (float)spec->p_ref_atm, (float)spec->x_ref, W,
-      tally->absorbed, tally->scalars, tally->steps, tally->status, rp);
+      tally->absorbed, tally->scalars, tally->steps, count_evals ? tally->steps + 1 : nullptr, tally->status, rp);
   RT_CUDA_TRY(cudaGetLastError());
   return RT_OK;
 }

@@ -200,3 +200,14 @@ def test_wait_probe_rejects_bad_input_on_host():
     assert L.rt_wait_probe(1000, 1, None, None) == rt.RT_E_INVAL
     assert L.rt_wait_probe(0, 1, ct.c_void_p(16), None) == rt.RT_E_INVAL
     assert L.rt_wait_probe((1 << 24) + 1, 1, ct.c_void_p(16), None) == rt.RT_E_INVAL
+
+
+def test_table_walk_rejects_the_evaluation_counter_flag():
+    L = rt.lib()
+    case = synth.config(0)
+    spec = rt.make_spectral(case.spec)
+    g = rt.rt_grid(64, 1, 1, 0, 1 / 64, math.inf, math.inf, 16, None, None)
+    t = rt.rt_tally_buf(16, 16, 16, 16)
+    st, msg = _status(lambda: L.rt_trace(ct.byref(g), ct.c_void_p(16), ct.byref(spec), 0, 10, 10, 0, 0,
+                                         rt.RT_COUNT_EVALS, ct.byref(t), None, None))
+    assert st == rt.RT_E_INVAL and "unknown bits" in msg

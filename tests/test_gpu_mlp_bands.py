@@ -313,3 +313,37 @@ def test_banded_walk_at_the_learned_part_size(rt):
              * g.ncells * spec.n_nu / n)
     rel = np.abs(w_gpu - w_ref) / w_ref
     assert np.median(rel) < 1e-2 and rel.max() < 5e-2, (np.median(rel), rel.max())
+
+
+def test_evaluation_count_and_dark_rays(rt):
+    # RT_COUNT_EVALS adds the network evaluations in steps[1] and leaves the walk as it
+    # was; with the optical-depth cut every counted step is a lit step (no dark ray runs
+    # ahead), so the evaluations cover at least the steps of the tile's longest ray; without
+    # the cut a dark ray takes its remaining steps without evaluations
+    import torch
+    spec = synth.Spectral(nu_min=2000.0, dnu=0.02, n_nu=2000, cutoff=25.0, profile="voigt", nT=13,
+                          T_min=800.0, T_max=2000.0, p_ref_atm=1.0, x_ref=0.1)
+    p = _spread_net(51)
+    P = torch.from_numpy(p).cuda()
+    g = synth.gaussian_hotspot_grid(12, 1.0, 800.0, 2000.0, 0.2)
+    gs, keep = rt.make_grid(g)
+    norms = rt.norms_tensor([LO], [HI], [2.0], [1.0])   # large kappa: most rays go dark
+    n = 30000
+
+    def run(flags):
+        t = rt.Tally(g.ncells, counters=2)
+        t.zero()
+        rt.trace_mlp_bands(gs, 5000, P, norms, spec, t, n_rays=n, seed=3, flags=flags)
+        ab, sc, st = t.read()
+        assert st == 0
+        return ab, sc, int(t.steps[0].item()), int(t.steps[1].item())
+
+    a0, s0, n0, e0 = run(0)
+    a1, s1, n1, e1 = run(rt.RT_COUNT_EVALS)
+    assert e0 == 0 and e1 > 0
+    assert n0 == n1
+    assert np.allclose(a0, a1, rtol=1e-12, atol=1e-12 * a0.max())
+    # the evaluations serve fewer ray-steps than were taken: dark rays ran ahead
+    assert e1 * 128 < n1
+    _, _, nc, ec = run(rt.RT_COUNT_EVALS | rt.RT_TAU_CUT)
+    assert ec * 128 >= nc   # with the cut every step is evaluated
