@@ -127,6 +127,12 @@ k_walk_lbl(const int4 *__restrict__ R, const float4 *__restrict__ L0, const floa
       const float kap = kappa_lbl<PROFILE>(R, L0, L1, l0, l1, Ry.j, Tc, pc, xc, K, W.dnu, wc);
       if (Ry.w < 0.0f) Ry.w = (W.mode == RT_SRC_BEAM) ? 1.0f : emission_weight(W, Ry.j, Tc, kap);
       if (ray_step(W, kap, absorbed, status, rec, Ry, lead)) break;
+      if (Ry.trans == 0.0f && !W.tau_cut) {
+        // dark (uniform over the warp's one ray): its remaining steps need no line sum
+        while (!ray_step<true, true, false, true>(W, 0.0f, absorbed, status, rec, Ry, lead)) {
+        }
+        break;
+      }
     }
     const float out = Ry.w * Ry.trans;
     em += (double)Ry.w;
