@@ -63,19 +63,6 @@ __device__ __forceinline__ long long zidx(long long layer, int c, long long n, l
   return (layer * kH + c) * n + row;
 }
 
-// SiLU of two pre-activations, packed as the BF16 pair the next layer reads:
-// z rounded to BF16, then with u = z/2 (exact), SiLU(z) = z (1 + tanh(z/2)) / 2
-// = u tanh(u) + u, one fused multiply-add, in packed BF16 arithmetic (the
-// surrogate walk's inference epilogue; training keeps its SiLU in binary32).
-__device__ __forceinline__ uint32_t silu_bf16x2(float lo, float hi) {
-  uint32_t z, r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(z) : "f"(hi), "f"(lo));
-  asm("{\n .reg .b32 c, u, t;\n mov.b32 c, 0x3F003F00;\n mul.rn.bf16x2 u, %1, c;\n"
-      " tanh.approx.bf16x2 t, u;\n fma.rn.bf16x2 %0, u, t, u;\n}"
-      : "=r"(r) : "r"(z));
-  return r;
-}
-
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
   const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
@@ -849,12 +836,14 @@ __device__ __forceinline__ bool mlp_eval_tile(WalkMlpSmem &S, uint32_t tmem, con
     for (int c0 = 0; c0 < kH; c0 += 32) {
       float z[32];  // pre-activations, biases included
       tc::tmem_ld32(tcol + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, z);
-      if (l < 3) {  // next layer's BF16 input
+      if (l < 3) {  // next layer's BF16 input: binary32 SiLU (as in training), rounded to BF16
 #pragma unroll
         for (int i = 0; i < 32; i += 8)
           *reinterpret_cast<uint4 *>(&S.A[tile][tile_index(r, c0 + i)]) =
-              make_uint4(silu_bf16x2(z[i], z[i + 1]), silu_bf16x2(z[i + 2], z[i + 3]),
-                         silu_bf16x2(z[i + 4], z[i + 5]), silu_bf16x2(z[i + 6], z[i + 7]));
+              make_uint4(pack_bf16x2(z[i] * sigmoid_fast(z[i]), z[i + 1] * sigmoid_fast(z[i + 1])),
+                         pack_bf16x2(z[i + 2] * sigmoid_fast(z[i + 2]), z[i + 3] * sigmoid_fast(z[i + 3])),
+                         pack_bf16x2(z[i + 4] * sigmoid_fast(z[i + 4]), z[i + 5] * sigmoid_fast(z[i + 5])),
+                         pack_bf16x2(z[i + 6] * sigmoid_fast(z[i + 6]), z[i + 7] * sigmoid_fast(z[i + 7])));
       } else {  // last hidden layer: binary32 SiLU into the head
 #pragma unroll
         for (int q = 0; q < 32; ++q) y = fmaf(S.sp.w5[c0 + q], z[q] * sigmoid_fast(z[q]), y);
