@@ -1160,7 +1160,7 @@ def main():
     ap.add_argument("--epochs", default="1,8,32", help="comma-separated epoch counts (one network each)")
     ap.add_argument("--objective", default="mse", choices=["mse"])
     ap.add_argument("--rays", type=int, default=50_000_000)
-    ap.add_argument("--bands", type=int, default=32, help="wavenumbers per network of the ensemble (0: none)")
+    ap.add_argument("--bands", type=int, default=16, help="wavenumbers per network of the ensemble (0: none)")
     ap.add_argument("--band-steps", default="24000", help="comma-separated training steps (one ensemble each)")
     ap.add_argument("--band-batch", type=int, default=128)
     ap.add_argument("--bands128", type=int, default=64, help="128^3 learned part: wavenumbers per network")
