@@ -270,7 +270,7 @@ def test_band_samples_follow_the_emission_weights(rt, mix):
 
 
 def test_banded_walk_at_the_learned_part_size(rt):
-    # The 64^3 learned-part workload in the benchmark's configuration: 3125 networks of 32
+    # The 64^3 learned-part workload in the benchmark's configuration: 6250 networks of 16
     # wavenumbers over 100k wavenumbers, 5e7 rays grouped by band.  The visits do not depend
     # on kappa, so the step count must equal the table walk's on the same rays exactly; the
     # tally must close its energy balance; and a sample of rays' emission weights must follow
@@ -278,7 +278,7 @@ def test_banded_walk_at_the_learned_part_size(rt):
     import torch
     case = synth.config(2)
     spec, g = case.spec, case.grid
-    band_pts = 32
+    band_pts = 16
     nb = -(-spec.n_nu // band_pts)
     base = _spread_net(60)
     P = torch.from_numpy(np.tile(base, nb)).cuda()
