@@ -357,10 +357,17 @@ class MlpTrainer:
         self.step_no = int(step_first) - 1 + int(n_steps)
 
 
+def _check_eval_counter(tally, flags):
+    # RT_COUNT_EVALS makes the library write a second steps counter
+    if (int(flags) & RT_COUNT_EVALS) and tally.steps.numel() < 2:
+        raise RtError(RT_E_INVAL, "trace_mlp", "RT_COUNT_EVALS needs a Tally with counters=2")
+
+
 def trace_mlp(grid_struct, params, norm, spec, tally: Tally, n_rays: int, ray_begin: int = 0,
               n_rays_total: int | None = None, seed: int = 0, enclosure: int = 0, flags: int = 0,
               record: Record | None = None, stream=None):
     """Run rt_trace_mlp (asynchronous); accumulates into ``tally``."""
+    _check_eval_counter(tally, flags)
     S = make_spectral(spec)
     st = lib().rt_trace_mlp(ct.byref(grid_struct), _ptr(params), ct.byref(norm), ct.byref(S),
                             int(ray_begin), int(n_rays),
@@ -439,6 +446,7 @@ def trace_mlp_bands(grid_struct, band_pts, params, norms, spec, tally: Tally, n_
                     n_rays_total: int | None = None, seed: int = 0, enclosure: int = 0, flags: int = 0,
                     record: Record | None = None, stream=None):
     """Run rt_trace_mlp_bands (asynchronous); accumulates into ``tally``."""
+    _check_eval_counter(tally, flags)
     S = make_spectral(spec)
     st = lib().rt_trace_mlp_bands(ct.byref(grid_struct), int(band_pts), _ptr(params), _ptr(norms), ct.byref(S),
                                   int(ray_begin), int(n_rays),

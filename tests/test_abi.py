@@ -211,3 +211,12 @@ def test_table_walk_rejects_the_evaluation_counter_flag():
     st, msg = _status(lambda: L.rt_trace(ct.byref(g), ct.c_void_p(16), ct.byref(spec), 0, 10, 10, 0, 0,
                                          rt.RT_COUNT_EVALS, ct.byref(t), None, None))
     assert st == rt.RT_E_INVAL and "unknown bits" in msg
+
+
+def test_evaluation_counter_needs_two_counters():
+    # the binding refuses RT_COUNT_EVALS with a one-counter tally before any call
+    t = rt.Tally(8, device="cpu")
+    with pytest.raises(rt.RtError):
+        rt.trace_mlp_bands(None, 16, None, None, None, t, n_rays=1, flags=rt.RT_COUNT_EVALS)
+    with pytest.raises(rt.RtError):
+        rt.trace_mlp(None, None, None, None, t, n_rays=1, flags=rt.RT_COUNT_EVALS)
